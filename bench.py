@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""MD steps/s and pair-evaluations/s of the vertex- and edge-based force paths, mixed precision and
+plain FP64, on one GB300 (one process per GPU; N > 1 runs independent replicas).
+
+Default workload: Lennard-Jones fluid, N = 1,048,576, rho = 0.85, T = 1.0, rc = 2.5, skin 0.3,
+dt = 0.001, FCC start with +-0.05 sigma jitter (synthetic, seeded).  One step is one velocity-Verlet
+step of the whole path: kick + drift + skin check, cell + Verlet rebuild when due, forces, kick and
+FP64 energy reductions.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MD steps/s & pair-evals/s: vertex vs edge, mixed vs FP64 plain, on 1 GB300"
+WORKLOAD = "lj_fluid_n1048576_rho0.85_T1.0_rc2.5_skin0.3_dt0.001"
+
+
+def make_system(rank: int = 0):
+    from paper_1401_4350_gb300 import systems
+    return systems.make_lj(1_048_576, 0.85, 1.0, seed=1001 + rank)
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.file = None
+        self.uuid = device_uuid
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(",") for l in self.file.read().splitlines() if l.strip()]
+        try:
+            os.unlink(self.file.name)
+        except OSError:
+            pass
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+
+def algorithmic_bytes_force(path: int, precision: int, n: int, full_entries: int, pairs: int) -> float:
+    """Compulsory DRAM bytes of one force launch (lists, per-particle arrays once, outputs once)."""
+    from paper_1401_4350_gb300 import binding as B
+    if precision == B.MD_MIXED:
+        pos_b, out_b = 16, 32          # fixed-point coordinates; force + compensation (float4 x 2)
+    else:
+        pos_b, out_b = 32, 64          # double4 positions; force + virial words (double4 x 2)
+    if path == B.MD_VERTEX:
+        return 4.0 * full_entries + n * (4 + pos_b + out_b)
+    return 8.0 * pairs + 8.0 * (n + 1) + n * (pos_b + 2 * out_b)  # outputs: zeroed once, accumulated once
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+    from paper_1401_4350_gb300 import binding as B
+    from paper_1401_4350_gb300 import build as mdbuild
+    from paper_1401_4350_gb300.sim import Simulation
+
+    if rank == 0:
+        mdbuild.build()
+    if dist is not None:
+        dist.barrier()
+    B.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    system = make_system(rank)
+    n = system.n
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def time_steps(sim, path, k, sampler=None):
+        st0 = sim.status()
+        barrier()
+        if sampler:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k, path, use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        barrier()
+        st1 = sim.status()
+        assert st1[B.MD_STATUS_CODE] == 0, f"device status {st1}"
+        return e0.elapsed_time(e1), st1[B.MD_STATUS_REBUILDS] - st0[B.MD_STATUS_REBUILDS], clocks
+
+    def list_stats(sim):
+        cnt = sim.view("nbr_count", torch.int32, n)
+        full = int(cnt.sum().item())
+        return full, full // 2
+
+    def force_launch_ms(sim, path, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        fn = sim.forces_vertex if path == B.MD_VERTEX else sim.forces_edge
+        fn()
+        torch.cuda.synchronize()
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+
+    results = {}
+    # ---- headline: mixed precision, vertex path (the faster path on this workload) ----
+    headline_path = B.MD_VERTEX
+    sim = Simulation(system, B.MD_MIXED, trace_capacity=0, stream=stream)
+    sim.prepare(headline_path)
+    sim.step(max(args.warmup, 3), headline_path, use_graph=True)
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    ms, rebuilds, clocks = time_steps(sim, headline_path, args.steps, sampler)
+    ms = max_over_ranks(ms)
+    full_entries, pairs = list_stats(sim)
+    force_ms = force_launch_ms(sim, headline_path, min(args.steps, 200))
+    step_ms = ms / args.steps
+    results["vertex_mixed"] = {"steps_per_s": 1e3 / step_ms, "ms_per_step": step_ms, "rebuilds": rebuilds,
+                               "pair_evals_per_s": pairs * 1e3 / step_ms, "force_kernel_ms": force_ms}
+    # ---- end to end through the C ABI with host-resident state ----
+    pos_h = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
+    vel_h = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
+    en_h = torch.empty(B.MD_ENERGY_WORDS, dtype=torch.float64, pin_memory=True)
+    pos_h.copy_(sim.pos)
+    vel_h.copy_(sim.vel)
+    energy_dev = sim.view("energy", torch.float64, B.MD_ENERGY_WORDS)
+    e2e_steps = max(10, min(args.steps // 10, 300))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.pos.copy_(pos_h, non_blocking=True)
+        sim.vel.copy_(vel_h, non_blocking=True)
+        sim.step(1, headline_path, use_graph=True)
+        pos_h.copy_(sim.pos, non_blocking=True)
+        vel_h.copy_(sim.vel, non_blocking=True)
+        en_h.copy_(energy_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    assert np.isfinite(en_h.numpy()[:4]).all()
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 2 * n * 32,
+           "d2h_bytes_per_step": 2 * n * 32 + 8 * B.MD_ENERGY_WORDS}
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- the other decompositions / precisions on the same workload ----
+    if not args.no_variants:
+        for name, path, precision, k in (("edge_mixed", B.MD_EDGE, B.MD_MIXED, min(args.steps, 1000)),
+                                         ("vertex_fp64", B.MD_VERTEX, B.MD_FP64, min(args.steps, 40)),
+                                         ("edge_fp64", B.MD_EDGE, B.MD_FP64, min(args.steps, 40))):
+            v = Simulation(system, precision, stream=stream)
+            v.prepare(path)
+            v.step(3, path, use_graph=True)
+            vms, vreb, _ = time_steps(v, path, k)
+            vms = max_over_ranks(vms)
+            _, vpairs = list_stats(v)
+            fms = force_launch_ms(v, path, min(k, 20))
+            results[name] = {"steps_per_s": 1e3 * k / vms, "ms_per_step": vms / k, "rebuilds": vreb,
+                             "pair_evals_per_s": vpairs * 1e3 * k / vms, "force_kernel_ms": fms, "steps": k}
+            del v
+            torch.cuda.empty_cache()
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alg = algorithmic_bytes_force(headline_path, B.MD_MIXED, n, full_entries, pairs)
+    achieved = alg / (force_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "k_vertex_mixed<1,false,1>",
+                "algorithmic_bytes_per_launch": alg, "force_kernel_ms": force_ms,
+                "force_share_of_step": force_ms / step_ms,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
+    value = world * args.steps / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "precision": "mixed: FP32 pair arithmetic + compensated FP32 sums, FP64 integration and reductions",
+        "pair_evals_per_s": world * pairs * args.steps / (ms * 1e-3),
+        "config": {"workload": WORKLOAD, "n": n, "path": "vertex", "precision": "mixed",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (full list ~0.33 GB + state ~0.2 GB per step)",
+                   "mean_full_list": full_entries / n, "unique_pairs": pairs},
+        "variants": results,
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps + 1 + 11 * rebuilds,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(system)
+    return line
+
+
+def cpu_baseline(system, max_seconds=25.0):
+    """The FP64 oracle as it stands, single-threaded on the host, on a bounded sample of steps."""
+    import oracle
+    oracle.build()
+    m = oracle.Model(oracle.LJ, tuple(system.box), system.rc)
+    t0 = time.perf_counter()
+    oracle.run_nve(system.pos, system.vel, m, system.dt, 1, use_cells=True)
+    t1 = time.perf_counter()
+    per = (t1 - t0) / 2.0  # one step = two force evaluations here (initial + after the drift)
+    k = max(1, min(8, int(max_seconds / max(per, 1e-3)) - 1))
+    t2 = time.perf_counter()
+    oracle.run_nve(system.pos, system.vel, m, system.dt, k, use_cells=True)
+    el = time.perf_counter() - t2
+    return {"value": k / el, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "host_cores_available": len(os.sched_getaffinity(0)),
+            "sample": f"{k} velocity-Verlet steps (+1 initial force evaluation) of the same {system.n}-particle "
+                      f"system, FP64 cell-list C oracle, one thread"}
+
+
+def run_reference(args):
+    """The oracle timed as it stands, bounded: at most ~60 s of host time."""
+    import oracle
+    oracle.build()
+    system = make_system(0)
+    m = oracle.Model(oracle.LJ, tuple(system.box), system.rc)
+    t0 = time.perf_counter()
+    pos, vel, _, _, _ = oracle.run_nve(system.pos, system.vel, m, system.dt, 1, use_cells=True)
+    per = (time.perf_counter() - t0) / 2.0
+    k = max(1, min(args.steps, int(60.0 / max(per, 1e-3)) - 1))
+    t1 = time.perf_counter()
+    oracle.run_nve(pos, vel, m, system.dt, k, use_cells=True)
+    el = time.perf_counter() - t1
+    value = k / el
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1, "steps": k,
+            "requested_steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * el / k, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": system.n, "implementation": "FP64 cell-list C oracle"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{k} steps of the {system.n}-particle workload, one host thread"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    line = run_ours(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

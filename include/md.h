@@ -1,0 +1,258 @@
+/*
+ * md.h -- C ABI of the GB300 short-range pair-force library (libmdgb.so).
+ *
+ * The library evaluates the pair forces (and, for the patchy model, torques)
+ * of a periodic particle system over a Verlet neighbour list in the two
+ * decompositions compared in Rovigatti, Sulc, Reguly, Romano, "A comparison
+ * between parallelization approaches in molecular dynamics simulations on
+ * GPUs" (arXiv:1401.4350):
+ *   - vertex-based: one thread per particle over its full neighbour list,
+ *     every pair computed twice, no write conflicts (Sec. Introduction and
+ *     Sec. Methods, the "vertex-based" approach);
+ *   - edge-based: one thread per potentially non-zero pair of a half list,
+ *     Newton's third law, atomic accumulation only when the pair force is not
+ *     zero (Sec. Methods, the "edge-based" approach, and the caption of Fig. 1);
+ * together with the supporting steps of Sec. Methods: cell binning, Verlet
+ * list build with a skin (rv = rc + rs) and velocity-Verlet integration with
+ * FP64 positions and momenta and FP32 pair forces (the "mixed precision"
+ * scheme), or FP64 throughout.
+ *
+ * Conventions (every entry point):
+ *   - All array pointers are DEVICE pointers owned by the caller.  The library
+ *     never allocates or frees device memory; scratch, cells, neighbour lists,
+ *     derived coordinates and force accumulators live in one caller-provided
+ *     workspace of md_workspace_bytes() bytes whose sub-arrays are described by
+ *     md_workspace_layout().  The workspace must be 256-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *     stream-ordered and asynchronous unless stated otherwise.
+ *   - The return value reports host-side argument validation (MD_ERR_INVALID,
+ *     with a message from md_last_error()) and launch failures (MD_ERR_CUDA).
+ *     Conditions detected on the device (neighbour-list overflow, non-finite
+ *     forces, a bounded wait that ran out) are recorded in the workspace's
+ *     status words and read with md_read_status().
+ *   - Particle arrays are [n][4] with the 4th component unused unless stated.
+ *     md_build_cells reorders every particle array into cell order; `id` maps
+ *     each slot back to the caller's original particle index.
+ *   - No call aborts, traps or throws across the ABI.
+ */
+#ifndef MDGB_MD_H
+#define MDGB_MD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_ABI_VERSION 1
+
+/* Return / status codes. */
+enum {
+  MD_OK = 0,
+  MD_ERR_INVALID = 1,         /* bad argument (host-side check); see md_last_error()      */
+  MD_ERR_CUDA = 2,            /* a CUDA runtime call or launch failed                      */
+  MD_ERR_NEIGH_OVERFLOW = 3,  /* device: a neighbour list exceeded its capacity            */
+  MD_ERR_NONFINITE = 4,       /* device: a non-finite force or position was produced       */
+  MD_ERR_TIMEOUT = 5,         /* device: a bounded wait ran out                            */
+  MD_ERR_UNSUPPORTED = 6      /* the call is valid but this configuration is not built     */
+};
+
+/* Pair models (Sec. Models). */
+enum {
+  MD_LJ = 0,      /* Lennard-Jones, Eq. 1, cut and energy-shifted at rc                        */
+  MD_WCA = 1,     /* Lennard-Jones cut at 2^(1/6) sigma and shifted by +eps (purely repulsive)  */
+  MD_PATCHY = 2   /* WCA core + patch attraction -eps_p exp(-(r_pp/delta)^10 / 2), cf. Eqs. 2-4 */
+};
+
+/* Arithmetic of the pair forces. */
+enum {
+  MD_FP64 = 0,    /* FP64 everywhere                                                          */
+  MD_MIXED = 1    /* FP32 pair arithmetic with compensated FP32 accumulation; FP64 integration,
+                     reductions and periodic wrap (Sec. Methods, mixed precision)              */
+};
+
+/* Decomposition of the force evaluation. */
+enum { MD_VERTEX = 0, MD_EDGE = 1 };
+
+/* Which neighbour lists md_build_verlet writes. */
+enum { MD_LIST_FULL = 1, MD_LIST_HALF = 2, MD_LIST_BOTH = 3 };
+
+#define MD_MAX_PATCH 4
+
+/* Status words (int32) in the workspace, read with md_read_status(). */
+enum {
+  MD_STATUS_CODE = 0,          /* first device-detected error (MD_OK if none); sticky     */
+  MD_STATUS_NEED_NEIGH = 1,    /* largest full-list length seen at the last build          */
+  MD_STATUS_NEED_PAIRS_LO = 2, /* half-list length (pairs) of the last build, low 31 bits  */
+  MD_STATUS_NEED_PAIRS_HI = 3, /* ... and the bits above                                  */
+  MD_STATUS_REBUILDS = 4,      /* number of cell + Verlet rebuilds done by md_step_verlet  */
+  MD_STATUS_STEPS = 5,         /* number of steps done by md_step_verlet                   */
+  MD_STATUS_WORDS = 16
+};
+
+/* Energy words (double) in the workspace: values at the last completed step. */
+enum {
+  MD_ENERGY_U = 0,        /* potential energy                       */
+  MD_ENERGY_KT = 1,       /* translational kinetic energy           */
+  MD_ENERGY_KR = 2,       /* rotational kinetic energy (patchy)     */
+  MD_ENERGY_W = 3,        /* pair virial  sum_pairs r_ij . F_ij      */
+  MD_ENERGY_WORDS = 8
+};
+
+/* Model and run parameters (a plain struct; no pointers). */
+typedef struct md_params {
+  int32_t n;                     /* number of particles, >= 1                                    */
+  int32_t model;                 /* MD_LJ, MD_WCA or MD_PATCHY                                   */
+  int32_t precision;             /* MD_FP64 or MD_MIXED                                          */
+  int32_t max_neigh;             /* full-list capacity per particle (columns), >= 1              */
+  int64_t max_pairs;             /* half-list capacity in pairs, >= 1                            */
+  int32_t n_patch;               /* patchy: patch sites per particle, 1..MD_MAX_PATCH            */
+  int32_t threads_per_particle;  /* vertex path: 1, 2, 4 or 8 threads cooperate on a particle   */
+  int32_t block_size;            /* force-kernel CTA size: 0 (default) or 32..1024, multiple of 32 */
+  int32_t trace_capacity;        /* energy-trace rows kept by md_step_verlet (0 = none)         */
+  double box[3];                 /* periodic box edges; each must exceed 2 rv                    */
+  double rc;                     /* centre-centre cut-off (LJ: 2.5 sigma; WCA: 2^(1/6) sigma)    */
+  double skin;                   /* Verlet skin rs > 0; rv = rc + rs                             */
+  double dt;                     /* time step                                                    */
+  double mass;                   /* particle mass                                                */
+  double inertia;                /* patchy: isotropic moment of inertia                          */
+  double eps, sigma;             /* Lennard-Jones parameters                                     */
+  double eps_p, delta;           /* patchy: patch strength and range                            */
+  double patch[MD_MAX_PATCH][3]; /* patchy: body-frame patch-site offsets from the centre        */
+} md_params;
+
+/* Primary state: FP64 device arrays owned by the caller, [n][4] each. */
+typedef struct md_state {
+  double* pos;     /* x, y, z, - ; wrapped into [0, L) by md_build_cells                     */
+  double* vel;     /* vx, vy, vz, -                                                          */
+  double* quat;    /* patchy: unit quaternion (w, x, y, z) body -> lab; else NULL            */
+  double* angmom;  /* patchy: lab-frame angular momentum Lx, Ly, Lz, -; else NULL            */
+  int32_t* id;     /* [n] original index of the particle held in each slot                   */
+} md_state;
+
+/* Byte offsets of the workspace sub-arrays (all 256-byte aligned). */
+typedef struct md_ws_layout {
+  size_t total;          /* md_workspace_bytes()                                              */
+  int32_t ncell[3];      /* cells per axis (an axis with fewer than 3 cells of edge >= rv is 1) */
+  int32_t force_elem;    /* bytes per force component: 4 (MD_MIXED) or 8 (MD_FP64)            */
+  size_t status;         /* int32[MD_STATUS_WORDS]                                             */
+  size_t energy;         /* double[MD_ENERGY_WORDS]                                            */
+  size_t cell_start;     /* int32[ncells + 1]: first slot of each cell (cell-sorted order)     */
+  size_t fxp;            /* uint32[n][4]: positions as fractions of the box edge times 2^32   */
+  size_t fxp_build;      /* uint32[n][4]: the same at the last Verlet build                   */
+  size_t patch_lab;      /* float[n][MD_MAX_PATCH][4]: lab-frame patch sites (patchy, mixed)  */
+  size_t nbr;            /* int32[max_neigh][n]: full list, column-major (entry k of slot i at k*n+i) */
+  size_t nbr_count;      /* int32[n]: full-list length per slot                               */
+  size_t half_start;     /* int64[n + 1]: half-list row offsets                               */
+  size_t pairs;          /* int32[max_pairs][2]: half list (i, j), i < j, sorted by i          */
+  size_t force;          /* [n][4] (Fx, Fy, Fz, E_i): float (mixed) or double (FP64)         */
+  size_t force_lo;       /* [n][4] (compensation of Fx, Fy, Fz; W_i)                          */
+  size_t torque;         /* [n][4] (tx, ty, tz, -) patchy                                      */
+  size_t torque_lo;      /* [n][4] compensation of the torque (mixed)                         */
+  size_t trace;          /* double[trace_capacity][4]: (step, K, U, W) rows of md_step_verlet */
+  size_t scratch;        /* internal scratch                                                  */
+} md_ws_layout;
+
+/* ABI version the library was built with (MD_ABI_VERSION). */
+int md_abi_version(void);
+
+/* Message describing the last host-side failure on this thread ("" if none). */
+const char* md_last_error(void);
+
+/* Validates p; returns MD_OK or MD_ERR_INVALID (with md_last_error()). */
+int md_check_params(const md_params* p);
+
+/* Workspace size in bytes for p (0 if p is invalid). */
+size_t md_workspace_bytes(const md_params* p);
+
+/* Fills *out with the workspace layout for p.  Returns MD_OK or MD_ERR_INVALID. */
+int md_workspace_layout(const md_params* p, md_ws_layout* out);
+
+/* Clears the workspace status, energy and trace words and the displacement
+ * bookkeeping (stream-ordered).  Call once after allocating the workspace. */
+int md_init_workspace(const md_params* p, void* ws, void* stream);
+
+/*
+ * md_build_cells -- cell binning with a counting sort (Sec. Methods: cell
+ * filling one particle per thread; particles reordered for cache hits).
+ * Wraps every position into [0, L), assigns each particle the cell of edge
+ * L/ncell >= rv that holds it, and reorders pos, vel, quat, angmom and id into
+ * cell order (within a cell: increasing previous slot), then writes
+ * cell_start and the fixed-point coordinates fxp.  Deterministic.
+ */
+int md_build_cells(const md_params* p, md_state* s, void* ws, void* stream);
+
+/*
+ * md_build_verlet -- Verlet lists L_i of every j with |x_j - x_i|^2 < rv^2,
+ * rv = rc + skin (Sec. Methods), minimum image, from the cells of the last
+ * md_build_cells.  which = MD_LIST_FULL (column-major list used by the vertex
+ * path), MD_LIST_HALF (pairs i < j used by the edge path) or MD_LIST_BOTH.
+ * The membership decision is exact in FP64 (candidates are filtered in FP32
+ * and those within a relative band of 1e-5 of rv^2 are re-decided with the
+ * FP64 distance d = x_j - x_i, d -= L rint(d / L), r^2 = dx^2 + dy^2 + dz^2
+ * summed in that order without contraction).  Rows keep increasing slot order.
+ * A list longer than its capacity sets MD_ERR_NEIGH_OVERFLOW in the status and
+ * the needed size in MD_STATUS_NEED_NEIGH / MD_STATUS_NEED_PAIRS_*; the lists
+ * are then truncated and must be rebuilt with larger capacities.
+ * Also records the positions of this build for the skin criterion.
+ */
+int md_build_verlet(const md_params* p, md_state* s, void* ws, int32_t which, void* stream);
+
+/*
+ * md_forces_vertex -- vertex-based force evaluation (Sec. Methods): one thread
+ * (or threads_per_particle threads) per particle loops over its full list,
+ * computes every pair, and writes the particle's total force, torque, energy
+ * (half of each pair energy) and virial once.  Needs MD_LIST_FULL.
+ */
+int md_forces_vertex(const md_params* p, md_state* s, void* ws, void* stream);
+
+/*
+ * md_forces_edge -- edge-based force evaluation (Sec. Methods, Fig. 1): one
+ * thread per pair of the half list computes F_ij and, only when it is not
+ * zero, adds it to i and -F_ij to j (Newton's third law) with atomics; the
+ * contributions to a run of pairs with the same i are first summed within the
+ * warp.  Needs MD_LIST_HALF.  The accumulation order is not deterministic.
+ */
+int md_forces_edge(const md_params* p, md_state* s, void* ws, void* stream);
+
+/*
+ * md_step_verlet -- nsteps of NVE velocity Verlet on the caller's stream,
+ * without host synchronisation: half kick with the current forces, drift,
+ * rebuild of cells and lists when the largest displacement since the last
+ * build exceeds skin/2, forces by `path` (MD_VERTEX or MD_EDGE), half kick.
+ * Patchy particles also get the half kicks of the angular momentum and the
+ * exact rotation q <- exp(omega dt / 2) (x) q, omega = L / inertia.
+ * Precondition: cells, lists and forces are current for the state (e.g. after
+ * md_prepare).  Each step's kinetic, potential energy and virial are reduced
+ * in FP64 into the energy words and, when trace_capacity > 0, appended to the
+ * trace.  use_graph != 0 replays a CUDA graph per step whose rebuild is a
+ * conditional node (the graph is built on the first call for this
+ * (p, s, ws, path) and cached); use_graph = 0 launches the kernels directly and
+ * the rebuild kernels return early when no rebuild is due.
+ */
+int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, int32_t path, int32_t use_graph,
+                   void* stream);
+
+/* md_build_cells + md_build_verlet(lists for `path`) + the forces of `path`. */
+int md_prepare(const md_params* p, md_state* s, void* ws, int32_t path, void* stream);
+
+/*
+ * Copies the current forces into FP64 device arrays in slot order:
+ * force_out [n][4] = (Fx, Fy, Fz, E_i), torque_out [n][4] = (tx, ty, tz, W_i)
+ * (torque_out may be NULL).  Mixed-precision values are the FP64 sums of the
+ * FP32 accumulator and its compensation term.
+ */
+int md_get_forces(const md_params* p, const void* ws, double* force_out, double* torque_out, void* stream);
+
+/* Synchronises `stream` and copies the MD_STATUS_WORDS status words to host_out. */
+int md_read_status(const md_params* p, const void* ws, int32_t* host_out, void* stream);
+
+/* Releases the CUDA graphs cached by md_step_verlet for this workspace (ws may be NULL: all). */
+int md_release_graphs(const void* ws);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDGB_MD_H */

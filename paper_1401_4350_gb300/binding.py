@@ -1,0 +1,190 @@
+"""Thin Python binding of libmdgb.so (the C ABI of include/md.h).
+
+Argument marshalling only: every step of the force path runs in the library's CUDA kernels.
+Device memory comes from torch tensors (their data pointers are passed through), streams are
+torch CUDA streams.  Importing this module does not need a GPU; loading the library does not
+either, but every compute call does.  A missing library raises at load time: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+LIB_PATH = os.path.join(PKG, "libmdgb.so")
+HEADER = os.path.join(ROOT, "include", "md.h")
+
+MD_OK, MD_ERR_INVALID, MD_ERR_CUDA, MD_ERR_NEIGH_OVERFLOW, MD_ERR_NONFINITE, MD_ERR_TIMEOUT, MD_ERR_UNSUPPORTED = range(7)
+MD_LJ, MD_WCA, MD_PATCHY = 0, 1, 2
+MD_FP64, MD_MIXED = 0, 1
+MD_VERTEX, MD_EDGE = 0, 1
+MD_LIST_FULL, MD_LIST_HALF, MD_LIST_BOTH = 1, 2, 3
+MD_MAX_PATCH = 4
+MD_STATUS_CODE, MD_STATUS_NEED_NEIGH, MD_STATUS_NEED_PAIRS_LO, MD_STATUS_NEED_PAIRS_HI = 0, 1, 2, 3
+MD_STATUS_REBUILDS, MD_STATUS_STEPS, MD_STATUS_WORDS = 4, 5, 16
+MD_ENERGY_U, MD_ENERGY_KT, MD_ENERGY_KR, MD_ENERGY_W, MD_ENERGY_WORDS = 0, 1, 2, 3, 8
+
+
+class md_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("model", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_neigh", ctypes.c_int32), ("max_pairs", ctypes.c_int64), ("n_patch", ctypes.c_int32),
+                ("threads_per_particle", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("trace_capacity", ctypes.c_int32), ("box", ctypes.c_double * 3), ("rc", ctypes.c_double),
+                ("skin", ctypes.c_double), ("dt", ctypes.c_double), ("mass", ctypes.c_double),
+                ("inertia", ctypes.c_double), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("eps_p", ctypes.c_double), ("delta", ctypes.c_double),
+                ("patch", (ctypes.c_double * 3) * MD_MAX_PATCH)]
+
+
+class md_state(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("angmom", ctypes.c_void_p), ("id", ctypes.c_void_p)]
+
+
+class md_ws_layout(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_size_t), ("ncell", ctypes.c_int32 * 3), ("force_elem", ctypes.c_int32)] + [
+        (name, ctypes.c_size_t) for name in
+        ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr", "nbr_count", "half_start",
+         "pairs", "force", "force_lo", "torque", "torque_lo", "trace", "scratch")]
+
+
+class MDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libmdgb error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.POINTER(md_params)
+_S = ctypes.POINTER(md_state)
+_V = ctypes.c_void_p
+
+
+def header_functions():
+    """Names of the functions declared in include/md.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(md_[a-z_0-9]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libmdgb.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with `python -m paper_1401_4350_gb300.build`")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "md_abi_version": ([], ctypes.c_int),
+        "md_last_error": ([], ctypes.c_char_p),
+        "md_check_params": ([_P], ctypes.c_int),
+        "md_workspace_bytes": ([_P], ctypes.c_size_t),
+        "md_workspace_layout": ([_P, ctypes.POINTER(md_ws_layout)], ctypes.c_int),
+        "md_init_workspace": ([_P, _V, _V], ctypes.c_int),
+        "md_build_cells": ([_P, _S, _V, _V], ctypes.c_int),
+        "md_build_verlet": ([_P, _S, _V, ctypes.c_int32, _V], ctypes.c_int),
+        "md_forces_vertex": ([_P, _S, _V, _V], ctypes.c_int),
+        "md_forces_edge": ([_P, _S, _V, _V], ctypes.c_int),
+        "md_step_verlet": ([_P, _S, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _V], ctypes.c_int),
+        "md_prepare": ([_P, _S, _V, ctypes.c_int32, _V], ctypes.c_int),
+        "md_get_forces": ([_P, _V, _V, _V, _V], ctypes.c_int),
+        "md_read_status": ([_P, _V, ctypes.POINTER(ctypes.c_int32), _V], ctypes.c_int),
+        "md_release_graphs": ([_V], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().md_last_error().decode()
+
+
+def _check(rc):
+    if rc != MD_OK:
+        raise MDError(rc, last_error())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+# ---- the C ABI, one wrapper per entry point ---------------------------------------------------
+
+def md_abi_version() -> int:
+    return load().md_abi_version()
+
+
+def md_check_params(p: md_params) -> int:
+    return load().md_check_params(ctypes.byref(p))
+
+
+def md_workspace_bytes(p: md_params) -> int:
+    return load().md_workspace_bytes(ctypes.byref(p))
+
+
+def md_workspace_layout(p: md_params) -> md_ws_layout:
+    out = md_ws_layout()
+    _check(load().md_workspace_layout(ctypes.byref(p), ctypes.byref(out)))
+    return out
+
+
+def md_init_workspace(p, ws, stream=None):
+    return _check(load().md_init_workspace(ctypes.byref(p), _ptr(ws), _stream(stream)))
+
+
+def md_build_cells(p, s, ws, stream=None):
+    return _check(load().md_build_cells(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
+
+
+def md_build_verlet(p, s, ws, which=MD_LIST_BOTH, stream=None):
+    return _check(load().md_build_verlet(ctypes.byref(p), ctypes.byref(s), _ptr(ws), which, _stream(stream)))
+
+
+def md_forces_vertex(p, s, ws, stream=None):
+    return _check(load().md_forces_vertex(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
+
+
+def md_forces_edge(p, s, ws, stream=None):
+    return _check(load().md_forces_edge(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
+
+
+def md_step_verlet(p, s, ws, nsteps, path=MD_VERTEX, use_graph=True, stream=None):
+    return _check(load().md_step_verlet(ctypes.byref(p), ctypes.byref(s), _ptr(ws), int(nsteps), int(path),
+                                        int(bool(use_graph)), _stream(stream)))
+
+
+def md_prepare(p, s, ws, path=MD_VERTEX, stream=None):
+    return _check(load().md_prepare(ctypes.byref(p), ctypes.byref(s), _ptr(ws), int(path), _stream(stream)))
+
+
+def md_get_forces(p, ws, force_out, torque_out=None, stream=None):
+    return _check(load().md_get_forces(ctypes.byref(p), _ptr(ws), _ptr(force_out), _ptr(torque_out),
+                                       _stream(stream)))
+
+
+def md_read_status(p, ws, stream=None):
+    out = (ctypes.c_int32 * MD_STATUS_WORDS)()
+    _check(load().md_read_status(ctypes.byref(p), _ptr(ws), out, _stream(stream)))
+    return list(out)
+
+
+def md_release_graphs(ws=None):
+    return load().md_release_graphs(_ptr(ws) if ws is not None else None)

@@ -1,0 +1,566 @@
+// md_api.cu -- the C ABI declared in include/md.h: argument validation, workspace layout, kernel
+// arguments, and the orchestration of a velocity-Verlet step (direct launches, or a cached CUDA
+// graph whose cell + Verlet rebuild is an IF conditional node decided on the device).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "md_internal.cuh"
+
+namespace mdgb {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return MD_ERR_CUDA;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Cells per axis: the largest k with L / k >= rv (1 + 1e-6); fewer than 3 cells means one cell
+// along that axis (every particle is a candidate along it and the minimum image picks the image).
+static int cells_axis(double L, double rv) {
+  double k = floor(L / (rv * (1.0 + 1e-6)));
+  if (k > 1024.0) k = 1024.0;
+  int c = (int)k;
+  while (c >= 3 && L / c < rv * (1.0 + 1e-6)) c--;
+  return c >= 3 ? c : 1;
+}
+
+static void cell_dims(const md_params* p, int nc[3]) {
+  const double rv = p->rc + p->skin;
+  for (int c = 0; c < 3; c++) nc[c] = cells_axis(p->box[c], rv);
+  // cap the grid at about 4 cells per particle (bigger cells are always valid)
+  const long long cap = 4LL * p->n + 27;
+  while ((long long)nc[0] * nc[1] * nc[2] > cap) {
+    int m = 0;
+    for (int c = 1; c < 3; c++)
+      if (nc[c] > nc[m]) m = c;
+    nc[m] = (nc[m] - 1 >= 3) ? nc[m] - 1 : 1;
+  }
+}
+
+static int check(const md_params* p) {
+  if (!p) { set_error("params is NULL"); return MD_ERR_INVALID; }
+  if (p->n < 1) { set_error("n must be >= 1 (got %d)", p->n); return MD_ERR_INVALID; }
+  if (p->model < MD_LJ || p->model > MD_PATCHY) { set_error("unknown model %d", p->model); return MD_ERR_INVALID; }
+  if (p->precision != MD_FP64 && p->precision != MD_MIXED) { set_error("unknown precision %d", p->precision); return MD_ERR_INVALID; }
+  if (p->max_neigh < 1) { set_error("max_neigh must be >= 1"); return MD_ERR_INVALID; }
+  if (p->max_pairs < 1) { set_error("max_pairs must be >= 1"); return MD_ERR_INVALID; }
+  if (!(p->rc > 0.0) || !(p->skin > 0.0)) { set_error("rc and skin must be > 0"); return MD_ERR_INVALID; }
+  if (!(p->dt > 0.0) || !(p->mass > 0.0)) { set_error("dt and mass must be > 0"); return MD_ERR_INVALID; }
+  if (!(p->sigma > 0.0)) { set_error("sigma must be > 0"); return MD_ERR_INVALID; }
+  const double rv = p->rc + p->skin;
+  for (int c = 0; c < 3; c++)
+    if (!(p->box[c] > 2.0 * rv)) {
+      set_error("box edge %d (%g) must exceed 2 rv = %g (minimum image)", c, p->box[c], 2.0 * rv);
+      return MD_ERR_INVALID;
+    }
+  if (p->threads_per_particle != 1 && p->threads_per_particle != 2 && p->threads_per_particle != 4 &&
+      p->threads_per_particle != 8) {
+    set_error("threads_per_particle must be 1, 2, 4 or 8");
+    return MD_ERR_INVALID;
+  }
+  if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || p->block_size % 32)) {
+    set_error("block_size must be 0 or a multiple of 32 in [32, 256]");
+    return MD_ERR_INVALID;
+  }
+  if (p->trace_capacity < 0) { set_error("trace_capacity must be >= 0"); return MD_ERR_INVALID; }
+  if (p->model == MD_PATCHY) {
+    if (p->n_patch < 1 || p->n_patch > MD_MAX_PATCH) { set_error("n_patch must be in 1..%d", MD_MAX_PATCH); return MD_ERR_INVALID; }
+    if (!(p->inertia > 0.0) || !(p->delta > 0.0)) { set_error("inertia and delta must be > 0"); return MD_ERR_INVALID; }
+  }
+  if ((double)p->n * (double)p->max_neigh > 9.0e18) { set_error("n * max_neigh too large"); return MD_ERR_INVALID; }
+  return MD_OK;
+}
+
+struct Layout {
+  md_ws_layout pub;
+  size_t scr_words, block_partials, cell_of, rank, perm, count_tmp, block_sums, tmp_d4, tmp_i;
+  int partial_capacity;
+};
+
+static void make_layout(const md_params* p, Layout* L) {
+  memset(L, 0, sizeof(*L));
+  int nc[3];
+  cell_dims(p, nc);
+  const size_t n = (size_t)p->n;
+  const size_t ncell = (size_t)nc[0] * nc[1] * nc[2];
+  const size_t fe = p->precision == MD_MIXED ? 4 : 8;
+  const bool patchy = p->model == MD_PATCHY;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + (bytes ? bytes : 1));
+    return o;
+  };
+  md_ws_layout& P = L->pub;
+  for (int c = 0; c < 3; c++) P.ncell[c] = nc[c];
+  P.force_elem = (int32_t)fe;
+  P.status = take(sizeof(int32_t) * MD_STATUS_WORDS);
+  P.energy = take(sizeof(double) * MD_ENERGY_WORDS);
+  P.cell_start = take(sizeof(int32_t) * (ncell + 1));
+  P.fxp = take(16 * n);
+  P.fxp_build = take(16 * n);
+  P.patch_lab = take(patchy ? fe * 4 * MD_MAX_PATCH * n : 0);
+  P.nbr = take(sizeof(int32_t) * n * (size_t)p->max_neigh);
+  P.nbr_count = take(sizeof(int32_t) * n);
+  P.half_start = take(sizeof(int64_t) * (n + 1));
+  P.pairs = take(8 * (size_t)p->max_pairs);
+  P.force = take(fe * 4 * n);
+  P.force_lo = take(fe * 4 * n);
+  P.torque = take(patchy ? fe * 4 * n : 0);
+  P.torque_lo = take(patchy ? fe * 4 * n : 0);
+  P.trace = take(sizeof(double) * 4 * (size_t)p->trace_capacity);
+  P.scratch = off;
+  L->scr_words = take(sizeof(uint32_t) * SCR_WORDS);
+  const int nblk = (int)((n + 255) / 256);
+  L->partial_capacity = nblk;
+  L->block_partials = take(sizeof(double) * 4 * (size_t)nblk);
+  L->cell_of = take(sizeof(int32_t) * n);
+  L->rank = take(sizeof(int32_t) * n);
+  L->perm = take(sizeof(int32_t) * n);
+  const size_t mcount = (ncell > n ? ncell : n) + 1;
+  L->count_tmp = take(sizeof(int32_t) * mcount);
+  L->block_sums = take(sizeof(int64_t) * (mcount / kScanTile + 4));
+  L->tmp_d4 = take(32 * n * (patchy ? 4 : 2));
+  L->tmp_i = take(sizeof(int32_t) * n);
+  P.total = off;
+}
+
+static float f32(double x) { return (float)x; }
+
+static KArgs make_args(const md_params* p, const md_state* s, void* ws, const Layout& L) {
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  char* w = (char*)ws;
+  a.n = p->n;
+  a.model = p->model;
+  a.precision = p->precision;
+  a.max_neigh = p->max_neigh;
+  a.max_pairs = p->max_pairs;
+  a.n_patch = p->model == MD_PATCHY ? p->n_patch : 0;
+  a.tpp = p->threads_per_particle;
+  a.trace_capacity = p->trace_capacity;
+  for (int c = 0; c < 3; c++) {
+    a.ncell[c] = L.pub.ncell[c];
+    a.box[c] = p->box[c];
+    a.inv_box[c] = 1.0 / p->box[c];
+    a.fxp_scale[c] = 4294967296.0 / p->box[c];
+    a.fxp_unit_d[c] = p->box[c] / 4294967296.0;
+    a.fxp_unit[c] = f32(a.fxp_unit_d[c]);
+  }
+  a.ncell_total = L.pub.ncell[0] * L.pub.ncell[1] * L.pub.ncell[2];
+  const double rv = p->rc + p->skin;
+  a.rc2_d = p->rc * p->rc;
+  a.rc2_f = f32(a.rc2_d);
+  a.rv2_d = rv * rv;
+  a.rv2_lo = f32(a.rv2_d * (1.0 - 1e-5));
+  a.rv2_hi = f32(a.rv2_d * (1.0 + 1e-5));
+  a.disp_thr2 = f32(0.25 * p->skin * p->skin * (1.0 - 1e-4));
+  const double riso = p->model == MD_LJ ? p->rc : pow(2.0, 1.0 / 6.0) * p->sigma;
+  a.rwca2_d = riso * riso;
+  a.rwca2_f = f32(a.rwca2_d);
+  a.rwca2_lo_f = f32(a.rwca2_d * (1.0 - 1e-5));
+  a.rwca2_hi_f = f32(a.rwca2_d * (1.0 + 1e-5));
+  a.rwca2_lo_d = a.rwca2_d * (1.0 - 1e-13);
+  a.rwca2_hi_d = a.rwca2_d * (1.0 + 1e-13);
+  const double sr2 = p->sigma * p->sigma / a.rwca2_d, sr6 = sr2 * sr2 * sr2;
+  a.sig2_d = p->sigma * p->sigma;
+  a.lj_c4_d = 4.0 * p->eps;
+  a.lj_c24_d = 24.0 * p->eps;
+  a.lj_shift_d = 4.0 * p->eps * (sr6 * sr6 - sr6);
+  a.sig2_f = f32(a.sig2_d);
+  a.lj_c4_f = f32(a.lj_c4_d);
+  a.lj_c24_f = f32(a.lj_c24_d);
+  a.lj_shift_f = f32(a.lj_shift_d);
+  if (p->model == MD_PATCHY) {
+    a.inv_delta2_d = 1.0 / (p->delta * p->delta);
+    a.eps_p_d = p->eps_p;
+    a.pgain_d = 5.0 * p->eps_p / (p->delta * p->delta);
+    a.inv_delta2_f = f32(a.inv_delta2_d);
+    a.eps_p_f = f32(a.eps_p_d);
+    a.pgain_f = f32(a.pgain_d);
+    a.half_log2e_f = f32(-0.5 / log(2.0));
+    double R = 0.0;
+    for (int k = 0; k < p->n_patch; k++) {
+      const double r = sqrt(p->patch[k][0] * p->patch[k][0] + p->patch[k][1] * p->patch[k][1] +
+                            p->patch[k][2] * p->patch[k][2]);
+      if (r > R) R = r;
+      for (int c = 0; c < 3; c++) a.patch_body[k][c] = p->patch[k][c];
+    }
+    // every patch term is exactly zero once (r_ab / delta)^10 exceeds 177.4 (FP32: exp2 argument
+    // below -128, flushed) or 1600 (FP64: exp argument below -800, underflow)
+    const double reach_f = 2.0 * R + p->delta * pow(128.0 * 2.0 * log(2.0), 0.1);
+    const double reach_d = 2.0 * R + p->delta * pow(1600.0, 0.1);
+    a.patch_reach2_f = f32(reach_f * reach_f);
+    a.patch_reach2_d = reach_d * reach_d;
+  }
+  a.dt = p->dt;
+  a.mass = p->mass;
+  a.inv_mass = 1.0 / p->mass;
+  a.half_dt_over_m = 0.5 * p->dt / p->mass;
+  a.dt_over_m = p->dt / p->mass;
+  a.inertia = p->inertia;
+  a.inv_inertia = p->inertia > 0.0 ? 1.0 / p->inertia : 0.0;
+  a.dt_over_m_f = f32(a.dt_over_m);
+  a.half_dt_over_m_f = f32(a.half_dt_over_m);
+  a.dt_f = f32(p->dt);
+  a.inv_inertia_f = f32(a.inv_inertia);
+  a.half_mass_f = f32(0.5 * p->mass);
+  if (s) {
+    a.pos = (double4_32a*)s->pos;
+    a.vel = (double4_32a*)s->vel;
+    a.quat = (double4_32a*)s->quat;
+    a.angmom = (double4_32a*)s->angmom;
+    a.id = s->id;
+  }
+  a.status = (int32_t*)(w + L.pub.status);
+  a.energy = (double*)(w + L.pub.energy);
+  a.cell_start = (int32_t*)(w + L.pub.cell_start);
+  a.fxp = (uint4*)(w + L.pub.fxp);
+  a.fxp_build = (uint4*)(w + L.pub.fxp_build);
+  a.patch_lab = (void*)(w + L.pub.patch_lab);
+  a.nbr = (int32_t*)(w + L.pub.nbr);
+  a.nbr_count = (int32_t*)(w + L.pub.nbr_count);
+  a.half_start = (int64_t*)(w + L.pub.half_start);
+  a.pairs = (int2*)(w + L.pub.pairs);
+  a.force = (void*)(w + L.pub.force);
+  a.force_lo = (void*)(w + L.pub.force_lo);
+  a.torque = (void*)(w + L.pub.torque);
+  a.torque_lo = (void*)(w + L.pub.torque_lo);
+  a.trace = (double*)(w + L.pub.trace);
+  a.scr_words = (uint32_t*)(w + L.scr_words);
+  a.block_partials = (double*)(w + L.block_partials);
+  a.cell_of = (int32_t*)(w + L.cell_of);
+  a.rank = (int32_t*)(w + L.rank);
+  a.perm = (int32_t*)(w + L.perm);
+  a.count_tmp = (int32_t*)(w + L.count_tmp);
+  a.block_sums = (int64_t*)(w + L.block_sums);
+  a.tmp_d4 = (double4_32a*)(w + L.tmp_d4);
+  a.tmp_i = (int32_t*)(w + L.tmp_i);
+  a.partial_capacity = L.partial_capacity;
+  return a;
+}
+
+static int check_state(const md_params* p, const md_state* s, const void* ws) {
+  if (!s || !s->pos || !s->vel || !s->id) { set_error("state arrays pos, vel and id are required"); return MD_ERR_INVALID; }
+  if (p->model == MD_PATCHY && (!s->quat || !s->angmom)) { set_error("patchy model needs quat and angmom"); return MD_ERR_INVALID; }
+  if (!ws) { set_error("workspace is NULL"); return MD_ERR_INVALID; }
+  if (((uintptr_t)ws) & 255) { set_error("workspace must be 256-byte aligned"); return MD_ERR_INVALID; }
+  if (((uintptr_t)s->pos | (uintptr_t)s->vel) & 31) { set_error("pos and vel must be 32-byte aligned"); return MD_ERR_INVALID; }
+  return MD_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Graph cache for md_step_verlet
+// ------------------------------------------------------------------------------------------------
+
+struct GraphEntry {
+  md_params params;
+  md_state state;
+  const void* ws;
+  int path;
+  int device;
+  cudaGraph_t g[2];
+  cudaGraphExec_t exec[2];  // 0: first step, 1: following steps
+};
+
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;
+
+static void destroy_entry(GraphEntry& e) {
+  for (int k = 0; k < 2; k++) {
+    if (e.exec[k]) cudaGraphExecDestroy(e.exec[k]);
+    if (e.g[k]) cudaGraphDestroy(e.g[k]);
+    e.exec[k] = nullptr;
+    e.g[k] = nullptr;
+  }
+}
+
+static int list_kind(int path) { return path == MD_EDGE ? MD_LIST_BOTH : MD_LIST_FULL; }
+
+static int build_step_graph(const KArgs& a, int mode, int path, int block, cudaGraph_t* g_out, cudaGraphExec_t* exec_out) {
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  int rc = MD_OK;
+  do {
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) { rc = cuda_fail(e, "cudaGraphCreate"); break; }
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) {
+      rc = cuda_fail(e, "cudaGraphConditionalHandleCreate");
+      break;
+    }
+    if ((e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      rc = cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+      break;
+    }
+    cudaError_t le = launch_integrate(a, mode, 1, (unsigned long long)h, cs);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    cudaGraphNode_t cnode = nullptr;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess && le == cudaSuccess) e = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess && le == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess && le == cudaSuccess) le = launch_forces(a, path, block, cs);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+    if (le != cudaSuccess) { rc = cuda_fail(le, "kernel launch during capture"); break; }
+    if (e != cudaSuccess) { rc = cuda_fail(e, "conditional node"); break; }
+    if (ee != cudaSuccess) { rc = cuda_fail(ee, "cudaStreamEndCapture"); break; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      rc = cuda_fail(e, "capture of the rebuild body");
+      break;
+    }
+    le = launch_build_cells(a, nullptr, cs);
+    if (le == cudaSuccess) le = launch_build_verlet(a, list_kind(path), nullptr, cs);
+    ee = cudaStreamEndCapture(cs, &captured);
+    if (le != cudaSuccess) { rc = cuda_fail(le, "rebuild launch during capture"); break; }
+    if (ee != cudaSuccess) { rc = cuda_fail(ee, "cudaStreamEndCapture (rebuild body)"); break; }
+    if ((e = cudaGraphInstantiate(exec_out, g, 0)) != cudaSuccess) { rc = cuda_fail(e, "cudaGraphInstantiate"); break; }
+    *g_out = g;
+    g = nullptr;
+  } while (0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  return rc;
+}
+
+static int get_graphs(const md_params* p, const md_state* s, const void* ws, int path, const KArgs& a,
+                      cudaGraphExec_t* first, cudaGraphExec_t* mid) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (auto& e : g_graphs) {
+    if (e.ws == ws && e.path == path && e.device == dev && memcmp(&e.params, p, sizeof(*p)) == 0 &&
+        memcmp(&e.state, s, sizeof(*s)) == 0) {
+      *first = e.exec[0];
+      *mid = e.exec[1];
+      return MD_OK;
+    }
+  }
+  // a workspace has at most one cached set of graphs
+  for (size_t k = 0; k < g_graphs.size(); k++) {
+    if (g_graphs[k].ws == ws) {
+      destroy_entry(g_graphs[k]);
+      g_graphs.erase(g_graphs.begin() + k);
+      break;
+    }
+  }
+  GraphEntry e;
+  memset(&e, 0, sizeof(e));
+  e.params = *p;
+  e.state = *s;
+  e.ws = ws;
+  e.path = path;
+  e.device = dev;
+  for (int m = 0; m < 2; m++) {
+    int rc = build_step_graph(a, m, path, p->block_size, &e.g[m], &e.exec[m]);
+    if (rc != MD_OK) {
+      destroy_entry(e);
+      return rc;
+    }
+  }
+  g_graphs.push_back(e);
+  *first = e.exec[0];
+  *mid = e.exec[1];
+  return MD_OK;
+}
+
+}  // namespace mdgb
+
+using namespace mdgb;
+
+extern "C" {
+
+int md_abi_version(void) { return MD_ABI_VERSION; }
+
+const char* md_last_error(void) { return g_err; }
+
+int md_check_params(const md_params* p) {
+  g_err[0] = 0;
+  return check(p);
+}
+
+size_t md_workspace_bytes(const md_params* p) {
+  if (check(p) != MD_OK) return 0;
+  Layout L;
+  make_layout(p, &L);
+  return L.pub.total;
+}
+
+int md_workspace_layout(const md_params* p, md_ws_layout* out) {
+  int rc = check(p);
+  if (rc != MD_OK) return rc;
+  if (!out) { set_error("out is NULL"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  *out = L.pub;
+  return MD_OK;
+}
+
+int md_init_workspace(const md_params* p, void* ws, void* stream) {
+  int rc = check(p);
+  if (rc != MD_OK) return rc;
+  if (!ws || (((uintptr_t)ws) & 255)) { set_error("workspace must be non-NULL and 256-byte aligned"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, nullptr, ws, L);
+  cudaError_t e = launch_init_ws(a, (cudaStream_t)stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_init_workspace");
+}
+
+int md_build_cells(const md_params* p, md_state* s, void* ws, void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc != MD_OK) return rc;
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, ws, L);
+  cudaError_t e = launch_build_cells(a, nullptr, (cudaStream_t)stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_build_cells");
+}
+
+int md_build_verlet(const md_params* p, md_state* s, void* ws, int32_t which, void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc != MD_OK) return rc;
+  if (which < MD_LIST_FULL || which > MD_LIST_BOTH) { set_error("which must be 1, 2 or 3"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, ws, L);
+  cudaError_t e = launch_build_verlet(a, which, nullptr, (cudaStream_t)stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_build_verlet");
+}
+
+static int forces_entry(const md_params* p, md_state* s, void* ws, int path, void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc != MD_OK) return rc;
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, ws, L);
+  cudaError_t e = launch_forces(a, path, p->block_size, (cudaStream_t)stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, path == MD_VERTEX ? "md_forces_vertex" : "md_forces_edge");
+}
+
+int md_forces_vertex(const md_params* p, md_state* s, void* ws, void* stream) {
+  return forces_entry(p, s, ws, MD_VERTEX, stream);
+}
+
+int md_forces_edge(const md_params* p, md_state* s, void* ws, void* stream) {
+  return forces_entry(p, s, ws, MD_EDGE, stream);
+}
+
+int md_prepare(const md_params* p, md_state* s, void* ws, int32_t path, void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc != MD_OK) return rc;
+  if (path != MD_VERTEX && path != MD_EDGE) { set_error("path must be MD_VERTEX or MD_EDGE"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, ws, L);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_build_cells(a, nullptr, st);
+  if (e == cudaSuccess) e = launch_build_verlet(a, list_kind(path), nullptr, st);
+  if (e == cudaSuccess) e = launch_forces(a, path, p->block_size, st);
+  if (e == cudaSuccess) e = launch_integrate(a, 3, 0, 0ULL, st);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_prepare");
+}
+
+int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, int32_t path, int32_t use_graph,
+                   void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc != MD_OK) return rc;
+  if (path != MD_VERTEX && path != MD_EDGE) { set_error("path must be MD_VERTEX or MD_EDGE"); return MD_ERR_INVALID; }
+  if (nsteps < 0) { set_error("nsteps must be >= 0"); return MD_ERR_INVALID; }
+  if (nsteps == 0) return MD_OK;
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, ws, L);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (use_graph) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs != cudaStreamCaptureStatusNone) {
+      set_error("use_graph = 1 while the stream is being captured: call with use_graph = 0 inside a capture");
+      return MD_ERR_INVALID;
+    }
+    cudaGraphExec_t first = nullptr, mid = nullptr;
+    rc = get_graphs(p, s, ws, path, a, &first, &mid);
+    if (rc != MD_OK) return rc;
+    e = cudaGraphLaunch(first, st);
+    for (int k = 1; k < nsteps && e == cudaSuccess; k++) e = cudaGraphLaunch(mid, st);
+  } else {
+    const uint32_t* gate = a.scr_words + SCR_GATE;
+    for (int k = 0; k < nsteps && e == cudaSuccess; k++) {
+      e = launch_integrate(a, k == 0 ? 0 : 1, 0, 0ULL, st);
+      if (e == cudaSuccess) e = launch_build_cells(a, gate, st);
+      if (e == cudaSuccess) e = launch_build_verlet(a, list_kind(path), gate, st);
+      if (e == cudaSuccess) e = launch_forces(a, path, p->block_size, st);
+    }
+  }
+  if (e == cudaSuccess) e = launch_integrate(a, 2, 0, 0ULL, st);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_step_verlet");
+}
+
+int md_get_forces(const md_params* p, const void* ws, double* force_out, double* torque_out, void* stream) {
+  int rc = check(p);
+  if (rc != MD_OK) return rc;
+  if (!ws || !force_out) { set_error("ws and force_out are required"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, nullptr, (void*)ws, L);
+  cudaError_t e = launch_get_forces(a, force_out, torque_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_get_forces");
+}
+
+int md_read_status(const md_params* p, const void* ws, int32_t* host_out, void* stream) {
+  int rc = check(p);
+  if (rc != MD_OK) return rc;
+  if (!ws || !host_out) { set_error("ws and host_out are required"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(host_out, (const char*)ws + L.pub.status, sizeof(int32_t) * MD_STATUS_WORDS, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_read_status");
+}
+
+int md_release_graphs(const void* ws) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (size_t k = 0; k < g_graphs.size();) {
+    if (ws == nullptr || g_graphs[k].ws == ws) {
+      destroy_entry(g_graphs[k]);
+      g_graphs.erase(g_graphs.begin() + k);
+    } else {
+      k++;
+    }
+  }
+  return MD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// md_cells.cu -- cell binning with a counting sort (Sec. Methods: "cell filling" one particle per
+// thread; particle data reordered in global memory for cache hits, here in cell order) and the
+// exclusive scans used by the cell and Verlet builds.
+#include "md_internal.cuh"
+
+namespace mdgb {
+
+// ------------------------------------------------------------------------------------------------
+// Exclusive scan of int32 counts into T[m + 1] (out[m] = total), three passes over tiles of
+// kScanTile elements.  Every kernel returns at once when the gate is closed.
+// ------------------------------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* warp_tot, T& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < nw ? warp_tot[lane] : T(0);
+    T winc = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T o = __shfl_up_sync(0xffffffffu, winc, d);
+      if (lane >= d) winc += o;
+    }
+    if (lane < nw) warp_tot[lane] = winc - w;
+    if (lane == 31) warp_tot[32] = winc;
+  }
+  __syncthreads();
+  T res = warp_tot[wid] + inc - v;
+  total = warp_tot[32];
+  __syncthreads();
+  return res;
+}
+
+template <typename T>
+__global__ void k_scan_tiles(const int32_t* __restrict__ cnt, T* __restrict__ out, int64_t* __restrict__ tile_tot,
+                             int m, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  __shared__ T warp_tot[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t idx = base + k;
+    v[k] = idx < m ? (T)cnt[idx] : T(0);
+    s += v[k];
+  }
+  T total;
+  T pre = block_exclusive_scan<T>(s, warp_tot, total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t idx = base + k;
+    if (idx < m) out[idx] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) tile_tot[blockIdx.x] = (int64_t)total;
+}
+
+// One block scans the tile totals in chunks (exclusive, in place) and writes out[m] = grand total.
+template <typename T>
+__global__ void k_scan_tile_totals(int64_t* __restrict__ tile_tot, int ntiles, T* __restrict__ out, int m,
+                                   const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  __shared__ int64_t warp_tot[33];
+  int64_t carry = 0;
+  for (int base = 0; base < ntiles; base += blockDim.x) {
+    int idx = base + threadIdx.x;
+    int64_t v = idx < ntiles ? tile_tot[idx] : 0;
+    int64_t total;
+    int64_t pre = block_exclusive_scan<int64_t>(v, warp_tot, total);
+    if (idx < ntiles) tile_tot[idx] = carry + pre;
+    carry += total;
+  }
+  if (threadIdx.x == 0) out[m] = (T)carry;
+}
+
+template <typename T>
+__global__ void k_scan_add(T* __restrict__ out, const int64_t* __restrict__ tile_tot, int m, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  const T off = (T)tile_tot[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    int64_t idx = base + k;
+    if (idx < m) out[idx] += off;
+  }
+}
+
+template <typename T>
+cudaError_t launch_scan(const int32_t* cnt, T* out, int64_t* tile_tot, int m, const uint32_t* gate, cudaStream_t st) {
+  int ntiles = (m + kScanTile - 1) / kScanTile;
+  if (ntiles < 1) ntiles = 1;
+  k_scan_tiles<T><<<ntiles, kScanThreads, 0, st>>>(cnt, out, tile_tot, m, gate);
+  k_scan_tile_totals<T><<<1, 1024, 0, st>>>(tile_tot, ntiles, out, m, gate);
+  k_scan_add<T><<<ntiles, 256, 0, st>>>(out, tile_tot, m, gate);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_scan<int32_t>(const int32_t*, int32_t*, int64_t*, int, const uint32_t*, cudaStream_t);
+template cudaError_t launch_scan<int64_t>(const int32_t*, int64_t*, int64_t*, int, const uint32_t*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------------
+// Cell build
+// ------------------------------------------------------------------------------------------------
+
+__global__ void k_zero_i32(int32_t* __restrict__ p, int m, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) p[k] = 0;
+}
+
+__device__ __forceinline__ double wrap_coord(double x, double L, double invL) {
+  double y = x - L * floor(x * invL);
+  if (y >= L) y -= L;
+  if (y < 0.0) y += L;
+  if (y >= L) y = 0.0;
+  return y;
+}
+
+// Wrap each position into [0, L), find its cell, take a rank inside the cell.
+__global__ void k_cells_assign(KArgs a, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  double4_32a p = a.pos[i];
+  p.x = wrap_coord(p.x, a.box[0], a.inv_box[0]);
+  p.y = wrap_coord(p.y, a.box[1], a.inv_box[1]);
+  p.z = wrap_coord(p.z, a.box[2], a.inv_box[2]);
+  a.pos[i] = p;
+  uint4 f = fixed3(p, a);
+  int cx = fixed_cell(f.x, a.ncell[0]), cy = fixed_cell(f.y, a.ncell[1]), cz = fixed_cell(f.z, a.ncell[2]);
+  int c = (cz * a.ncell[1] + cy) * a.ncell[0] + cx;
+  a.cell_of[i] = c;
+  a.rank[i] = atomicAdd(a.count_tmp + c, 1);
+}
+
+__global__ void k_cells_scatter(KArgs a, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  a.perm[a.cell_start[a.cell_of[i]] + a.rank[i]] = i;
+}
+
+// Deterministic order inside each cell: increasing previous slot (insertion sort; cells are small).
+__global__ void k_cells_sort(KArgs a, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.ncell_total) return;
+  int b = a.cell_start[c], e = a.cell_start[c + 1];
+  for (int k = b + 1; k < e; k++) {
+    int v = a.perm[k];
+    int m = k - 1;
+    while (m >= b && a.perm[m] > v) {
+      a.perm[m + 1] = a.perm[m];
+      m--;
+    }
+    a.perm[m + 1] = v;
+  }
+}
+
+__global__ void k_cells_gather(KArgs a, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  int o = a.perm[s];
+  const size_t n = (size_t)a.n;
+  a.tmp_d4[s] = a.pos[o];
+  a.tmp_d4[n + s] = a.vel[o];
+  if (a.model == MD_PATCHY) {
+    a.tmp_d4[2 * n + s] = a.quat[o];
+    a.tmp_d4[3 * n + s] = a.angmom[o];
+  }
+  a.tmp_i[s] = a.id[o];
+}
+
+__global__ void k_cells_copyback(KArgs a, const uint32_t* gate) {
+  if (gate_closed(gate)) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  const size_t n = (size_t)a.n;
+  double4_32a p = a.tmp_d4[s];
+  a.pos[s] = p;
+  a.vel[s] = a.tmp_d4[n + s];
+  if (a.model == MD_PATCHY) {
+    double4_32a q = a.tmp_d4[2 * n + s];
+    a.quat[s] = q;
+    a.angmom[s] = a.tmp_d4[3 * n + s];
+    write_patch_lab(a, s, q);
+  }
+  a.id[s] = a.tmp_i[s];
+  a.fxp[s] = fixed3(p, a);
+}
+
+cudaError_t launch_build_cells(const KArgs& a, const uint32_t* gate, cudaStream_t st) {
+  const int B = 256;
+  const int gn = (a.n + B - 1) / B;
+  k_zero_i32<<<(a.ncell_total + B - 1) / B, B, 0, st>>>(a.count_tmp, a.ncell_total, gate);
+  k_cells_assign<<<gn, B, 0, st>>>(a, gate);
+  cudaError_t e = launch_scan<int32_t>(a.count_tmp, a.cell_start, a.block_sums, a.ncell_total, gate, st);
+  if (e != cudaSuccess) return e;
+  k_cells_scatter<<<gn, B, 0, st>>>(a, gate);
+  k_cells_sort<<<(a.ncell_total + 127) / 128, 128, 0, st>>>(a, gate);
+  k_cells_gather<<<gn, B, 0, st>>>(a, gate);
+  k_cells_copyback<<<gn, B, 0, st>>>(a, gate);
+  return cudaGetLastError();
+}
+
+}  // namespace mdgb

@@ -1,0 +1,605 @@
+// md_forces.cu -- the two force decompositions of Sec. Methods.
+//
+// Vertex-based: one thread (or tpp cooperating threads) per particle walks its full Verlet list,
+// evaluates every pair (each pair is therefore evaluated twice, once from each side) and writes
+// the particle's force, torque, energy and virial once: no write conflicts.
+//
+// Edge-based: one thread per pair (i, j), i < j, of the half list evaluates F_ij once (Newton's
+// third law) and adds it to both particles with atomics, but only when the pair contributes
+// anything (the caption of Fig. 1: zero interactions cause no memory writes).  Pairs of the half
+// list are grouped by i, so a warp first sums the contributions of each run of equal i with a
+// segmented shuffle reduction and issues one atomic per run; the j side is one atomic per pair.
+//
+// Pair arithmetic.  MD_FP64: positions in FP64, minimum image d -= L rint(d / L).  MD_MIXED:
+// positions as 32-bit fixed-point fractions of the box, so that the difference of two
+// coordinates taken in 32-bit integer arithmetic is the minimum image (wrap-around is the
+// periodic boundary) and converts to FP32 with a relative error of 2^-24 of the separation.
+// Per-particle sums are FP32 with a Kahan compensation term (vertex) or FP32 atomics whose
+// rounding error is recovered with TwoSum from the returned old value and accumulated in a
+// second array (edge).
+#include "md_internal.cuh"
+
+namespace mdgb {
+
+// ------------------------------------------------------------------------------------------------
+// Pair terms
+// ------------------------------------------------------------------------------------------------
+
+// Lennard-Jones (Sec. Models, Eq. 1), cut and energy-shifted at the isotropic cut-off:
+// F_i = fs * d with d = x_j - x_i, V = 4 eps (sr12 - sr6) - V(rc).
+__device__ __forceinline__ void lj_terms(const KArgs& a, float r2, float& fs, float& pe) {
+  const float r2i = frcp_approx(r2);
+  const float sr2 = a.sig2_f * r2i;
+  const float sr6 = sr2 * sr2 * sr2;
+  fs = -a.lj_c24_f * sr6 * (2.f * sr6 - 1.f) * r2i;
+  pe = a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f;
+}
+
+__device__ __forceinline__ void lj_terms(const KArgs& a, double r2, double& fs, double& pe) {
+  const double r2i = __drcp_rn(r2);
+  const double sr2 = a.sig2_d * r2i;
+  const double sr6 = sr2 * sr2 * sr2;
+  fs = -a.lj_c24_d * sr6 * (2.0 * sr6 - 1.0) * r2i;
+  pe = a.lj_c4_d * sr6 * (sr6 - 1.0) - a.lj_shift_d;
+}
+
+template <typename R>
+struct Vec3 {
+  R x, y, z;
+};
+
+__device__ __forceinline__ Vec3<float> sep_mixed(const uint4& si, const uint4& sj, const KArgs& a) {
+  return {(float)(int)(sj.x - si.x) * a.fxp_unit[0], (float)(int)(sj.y - si.y) * a.fxp_unit[1],
+          (float)(int)(sj.z - si.z) * a.fxp_unit[2]};
+}
+
+__device__ __forceinline__ Vec3<double> sep_fp64(const double4_32a& pi, const double4_32a& pj, const KArgs& a) {
+  double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+  dx -= a.box[0] * rint(dx * a.inv_box[0]);
+  dy -= a.box[1] * rint(dy * a.inv_box[1]);
+  dz -= a.box[2] * rint(dz * a.inv_box[2]);
+  return {dx, dy, dz};
+}
+
+__device__ __forceinline__ float exp_neg_half(const KArgs& a, float q5) { return fexp2_approx(a.half_log2e_f * q5); }
+__device__ __forceinline__ double exp_neg_half(const KArgs& a, double q5) { return exp(-0.5 * q5); }
+
+template <typename R> __device__ __forceinline__ R rc2_of(const KArgs& a);
+template <> __device__ __forceinline__ float rc2_of<float>(const KArgs& a) { return a.rc2_f; }
+template <> __device__ __forceinline__ double rc2_of<double>(const KArgs& a) { return a.rc2_d; }
+template <typename R> __device__ __forceinline__ R rwca2_of(const KArgs& a);
+template <> __device__ __forceinline__ float rwca2_of<float>(const KArgs& a) { return a.rwca2_f; }
+template <> __device__ __forceinline__ double rwca2_of<double>(const KArgs& a) { return a.rwca2_d; }
+
+// Patch sites of a particle (lab frame).
+template <typename R, int NP>
+struct Patches {
+  Vec3<R> p[NP];
+};
+
+template <int NP>
+__device__ __forceinline__ Patches<float, NP> load_patches(const KArgs& a, int i, float) {
+  Patches<float, NP> P;
+  const float4* src = (const float4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    float4 v = __ldg(src + k);
+    P.p[k] = {v.x, v.y, v.z};
+  }
+  return P;
+}
+
+template <int NP>
+__device__ __forceinline__ Patches<double, NP> load_patches(const KArgs& a, int i, double) {
+  Patches<double, NP> P;
+  const double4_32a* src = (const double4_32a*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    double4_32a v = src[k];
+    P.p[k] = {v.x, v.y, v.z};
+  }
+  return P;
+}
+
+template <typename R> __device__ __forceinline__ R pgain_of(const KArgs& a);
+template <> __device__ __forceinline__ float pgain_of<float>(const KArgs& a) { return a.pgain_f; }
+template <> __device__ __forceinline__ double pgain_of<double>(const KArgs& a) { return a.pgain_d; }
+template <typename R> __device__ __forceinline__ R epsp_of(const KArgs& a);
+template <> __device__ __forceinline__ float epsp_of<float>(const KArgs& a) { return a.eps_p_f; }
+template <> __device__ __forceinline__ double epsp_of<double>(const KArgs& a) { return a.eps_p_d; }
+template <typename R> __device__ __forceinline__ R invd2_of(const KArgs& a);
+template <> __device__ __forceinline__ float invd2_of<float>(const KArgs& a) { return a.inv_delta2_f; }
+template <> __device__ __forceinline__ double invd2_of<double>(const KArgs& a) { return a.inv_delta2_d; }
+template <typename R> __device__ __forceinline__ R reach2_of(const KArgs& a);
+template <> __device__ __forceinline__ float reach2_of<float>(const KArgs& a) { return a.patch_reach2_f; }
+template <> __device__ __forceinline__ double reach2_of<double>(const KArgs& a) { return a.patch_reach2_d; }
+
+// Everything one pair contributes.  F: force on i (on j: -F); e: pair energy; w: -(d . F);
+// ti, tj: torques on i and j.
+template <typename R>
+struct PairOut {
+  Vec3<R> F, ti, tj;
+  R e, w;
+};
+
+template <typename R> __device__ __forceinline__ R rwca2_lo_of(const KArgs& a);
+template <> __device__ __forceinline__ float rwca2_lo_of<float>(const KArgs& a) { return a.rwca2_lo_f; }
+template <> __device__ __forceinline__ double rwca2_lo_of<double>(const KArgs& a) { return a.rwca2_lo_d; }
+template <typename R> __device__ __forceinline__ R rwca2_hi_of(const KArgs& a);
+template <> __device__ __forceinline__ float rwca2_hi_of<float>(const KArgs& a) { return a.rwca2_hi_f; }
+template <> __device__ __forceinline__ double rwca2_hi_of<double>(const KArgs& a) { return a.rwca2_hi_d; }
+
+// Cut-off test of the isotropic part.  The Lennard-Jones force is not shifted, so it jumps at rc:
+// pairs within a narrow band of rc^2 are decided with the exact FP64 distance of the FP64
+// positions, which makes the decision the same as the definition's in either precision.
+template <typename R>
+__device__ __forceinline__ bool iso_inside(const KArgs& a, R r2, int i, int j) {
+  bool in = r2 < rwca2_lo_of<R>(a);
+  if (!in && r2 < rwca2_hi_of<R>(a)) in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
+  return in;
+}
+
+// Isotropic pair (LJ or WCA) at separation d, r2 = |d|^2.
+template <typename R>
+__device__ __forceinline__ PairOut<R> iso_pair(const KArgs& a, const Vec3<R>& d, R r2, int i, int j) {
+  PairOut<R> o;
+  R fs, pe;
+  lj_terms(a, r2, fs, pe);
+  const bool in = iso_inside<R>(a, r2, i, j);
+  fs = in ? fs : R(0);
+  pe = in ? pe : R(0);
+  o.F = {fs * d.x, fs * d.y, fs * d.z};
+  o.e = pe;
+  o.w = -fs * r2;
+  o.ti = o.tj = {R(0), R(0), R(0)};
+  return o;
+}
+
+// Patchy pair: WCA core + sum over patch pairs of -eps_p exp(-(r_ab/delta)^10 / 2), applied when the
+// centre distance is below rc.  Patch terms are skipped when the centre distance is beyond the
+// reach at which every term has underflowed to zero in this precision (exact).
+template <typename R, int NP, bool WANT_TJ>
+__device__ __forceinline__ PairOut<R> patchy_pair(const KArgs& a, const Vec3<R>& d, R r2, const Patches<R, NP>& Pi,
+                                                  int i, int j) {
+  PairOut<R> o;
+  o.F = o.ti = o.tj = {R(0), R(0), R(0)};
+  o.e = o.w = R(0);
+  if (!(r2 < rc2_of<R>(a))) return o;
+  if (iso_inside<R>(a, r2, i, j)) {
+    R fs, pe;
+    lj_terms(a, r2, fs, pe);
+    o.F = {fs * d.x, fs * d.y, fs * d.z};
+    o.e = pe;
+  }
+  if (r2 < reach2_of<R>(a)) {
+    const Patches<R, NP> Pj = load_patches<NP>(a, j, R(0));
+    const R invd2 = invd2_of<R>(a), gain = pgain_of<R>(a), epsp = epsp_of<R>(a);
+    Vec3<R> Fb[NP];
+#pragma unroll
+    for (int b = 0; b < NP; b++) Fb[b] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int pa = 0; pa < NP; pa++) {
+      Vec3<R> Fa = {R(0), R(0), R(0)};
+      const Vec3<R> base = {d.x - Pi.p[pa].x, d.y - Pi.p[pa].y, d.z - Pi.p[pa].z};
+#pragma unroll
+      for (int b = 0; b < NP; b++) {
+        const Vec3<R> s = {base.x + Pj.p[b].x, base.y + Pj.p[b].y, base.z + Pj.p[b].z};
+        const R q = (s.x * s.x + s.y * s.y + s.z * s.z) * invd2;
+        const R q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
+        const R ex = exp_neg_half(a, q5);
+        o.e -= epsp * ex;
+        const R g = gain * q4 * ex;  // force on site a: g * s
+        Fa.x += g * s.x; Fa.y += g * s.y; Fa.z += g * s.z;
+        if (WANT_TJ) { Fb[b].x -= g * s.x; Fb[b].y -= g * s.y; Fb[b].z -= g * s.z; }
+      }
+      o.F.x += Fa.x; o.F.y += Fa.y; o.F.z += Fa.z;
+      const Vec3<R>& p = Pi.p[pa];
+      o.ti.x += p.y * Fa.z - p.z * Fa.y;
+      o.ti.y += p.z * Fa.x - p.x * Fa.z;
+      o.ti.z += p.x * Fa.y - p.y * Fa.x;
+    }
+    if (WANT_TJ) {
+#pragma unroll
+      for (int b = 0; b < NP; b++) {
+        const Vec3<R>& p = Pj.p[b];
+        o.tj.x += p.y * Fb[b].z - p.z * Fb[b].y;
+        o.tj.y += p.z * Fb[b].x - p.x * Fb[b].z;
+        o.tj.z += p.x * Fb[b].y - p.y * Fb[b].x;
+      }
+    }
+  }
+  o.w = -(d.x * o.F.x + d.y * o.F.y + d.z * o.F.z);
+  return o;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Vertex-based kernels
+// ------------------------------------------------------------------------------------------------
+
+struct Comp3 {
+  float s[3], lo[3];
+};
+
+__device__ __forceinline__ void comp_add(Comp3& c, const Vec3<float>& v) {
+  // lo holds minus the Kahan compensation: the sum is s + lo
+  float cx = -c.lo[0], cy = -c.lo[1], cz = -c.lo[2];
+  kahan_add(c.s[0], cx, v.x);
+  kahan_add(c.s[1], cy, v.y);
+  kahan_add(c.s[2], cz, v.z);
+  c.lo[0] = -cx; c.lo[1] = -cy; c.lo[2] = -cz;
+}
+
+// Combine two compensated sums (s1 + lo1) + (s2 + lo2) without losing the rounding of s1 + s2.
+__device__ __forceinline__ void comp_merge(float& s, float& lo, float s2, float lo2) {
+  const float t = __fadd_rn(s, s2);
+  const float err = two_sum_err(s, s2, t);
+  lo = __fadd_rn(__fadd_rn(lo, lo2), err);
+  s = t;
+}
+
+template <int TPP>
+__device__ __forceinline__ void group_reduce(Comp3& F, Comp3& T, float& e, float& w) {
+  if (TPP == 1) return;
+#pragma unroll
+  for (int off = TPP / 2; off > 0; off >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      float s2 = __shfl_xor_sync(0xffffffffu, F.s[c], off);
+      float l2 = __shfl_xor_sync(0xffffffffu, F.lo[c], off);
+      comp_merge(F.s[c], F.lo[c], s2, l2);
+      s2 = __shfl_xor_sync(0xffffffffu, T.s[c], off);
+      l2 = __shfl_xor_sync(0xffffffffu, T.lo[c], off);
+      comp_merge(T.s[c], T.lo[c], s2, l2);
+    }
+    e += __shfl_xor_sync(0xffffffffu, e, off);
+    w += __shfl_xor_sync(0xffffffffu, w, off);
+  }
+}
+
+// Mixed precision vertex kernel.  MODEL_PATCHY selects the patchy pair, NP its patch count.
+template <int TPP, bool PATCHY, int NP>
+__global__ void __launch_bounds__(256) k_vertex_mixed(KArgs a) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / TPP, l = gt % TPP;
+  const bool valid = i < a.n;
+  Comp3 F = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  Comp3 T = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float e = 0.f, w = 0.f;
+  if (valid) {
+    const uint4 si = __ldg(a.fxp + i);
+    const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
+    const int* nb = a.nbr + i;
+    const size_t n = (size_t)a.n;
+    Patches<float, (PATCHY ? NP : 1)> Pi;
+    if (PATCHY) Pi = load_patches<(PATCHY ? NP : 1)>(a, i, 0.f);
+#pragma unroll 4
+    for (int k = l; k < cnt; k += TPP) {
+      const int j = __ldcs(nb + (size_t)k * n);
+      const uint4 sj = __ldg(a.fxp + j);
+      const Vec3<float> d = sep_mixed(si, sj, a);
+      const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+      if (PATCHY) {
+        const PairOut<float> o = patchy_pair<float, (PATCHY ? NP : 1), false>(a, d, r2, Pi, i, j);
+        comp_add(F, o.F);
+        comp_add(T, o.ti);
+        e += o.e;
+        w += o.w;
+      } else {
+        const PairOut<float> o = iso_pair<float>(a, d, r2, i, j);
+        comp_add(F, o.F);
+        e += o.e;
+        w += o.w;
+      }
+    }
+  }
+  group_reduce<TPP>(F, T, e, w);
+  if (valid && l == 0) {
+    float4* fo = (float4*)a.force;
+    float4* flo = (float4*)a.force_lo;
+    fo[i] = make_float4(F.s[0], F.s[1], F.s[2], 0.5f * e);
+    flo[i] = make_float4(F.lo[0], F.lo[1], F.lo[2], 0.5f * w);
+    if (PATCHY) {
+      ((float4*)a.torque)[i] = make_float4(T.s[0], T.s[1], T.s[2], 0.f);
+      ((float4*)a.torque_lo)[i] = make_float4(T.lo[0], T.lo[1], T.lo[2], 0.f);
+    }
+  }
+}
+
+template <int TPP>
+__device__ __forceinline__ void group_reduce_d(double* v, int nv) {
+  if (TPP == 1) return;
+  for (int off = TPP / 2; off > 0; off >>= 1)
+    for (int c = 0; c < nv; c++) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+}
+
+template <int TPP, bool PATCHY, int NP>
+__global__ void __launch_bounds__(256) k_vertex_fp64(KArgs a) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / TPP, l = gt % TPP;
+  const bool valid = i < a.n;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // F(3), T(3), e, w
+  if (valid) {
+    const double4_32a pi = a.pos[i];
+    const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
+    const int* nb = a.nbr + i;
+    const size_t n = (size_t)a.n;
+    Patches<double, (PATCHY ? NP : 1)> Pi;
+    if (PATCHY) Pi = load_patches<(PATCHY ? NP : 1)>(a, i, 0.0);
+    for (int k = l; k < cnt; k += TPP) {
+      const int j = __ldcs(nb + (size_t)k * n);
+      const Vec3<double> d = sep_fp64(pi, a.pos[j], a);
+      const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+      PairOut<double> o;
+      if (PATCHY) o = patchy_pair<double, (PATCHY ? NP : 1), false>(a, d, r2, Pi, i, j);
+      else o = iso_pair<double>(a, d, r2, i, j);
+      acc[0] += o.F.x; acc[1] += o.F.y; acc[2] += o.F.z;
+      acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z;
+      acc[6] += o.e; acc[7] += o.w;
+    }
+  }
+  group_reduce_d<TPP>(acc, 8);
+  if (valid && l == 0) {
+    ((double4_32a*)a.force)[i] = make_double4_32a(acc[0], acc[1], acc[2], 0.5 * acc[6]);
+    ((double4_32a*)a.force_lo)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.5 * acc[7]);
+    if (PATCHY) {
+      ((double4_32a*)a.torque)[i] = make_double4_32a(acc[3], acc[4], acc[5], 0.0);
+      ((double4_32a*)a.torque_lo)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Edge-based kernels
+// ------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float4 atom_add_v4(float4* addr, float4 v) {
+  float4 old;
+  asm volatile("atom.global.add.v4.f32 {%0,%1,%2,%3}, [%4], {%5,%6,%7,%8};"
+               : "=f"(old.x), "=f"(old.y), "=f"(old.z), "=f"(old.w)
+               : "l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+// hi += (v.xyz, v.w); the rounding errors of the three force components go to lo.xyz, and `extra`
+// is added to lo.w (the per-particle virial).
+__device__ __forceinline__ void comp_atomic(float4* hi, float4* lo, float4 v, float extra) {
+  const float4 old = atom_add_v4(hi, v);
+  float4 err;
+  err.x = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
+  err.y = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
+  err.z = two_sum_err(old.z, v.z, __fadd_rn(old.z, v.z));
+  err.w = extra;
+  if (err.x != 0.f || err.y != 0.f || err.z != 0.f || err.w != 0.f) red_add_v4(lo, err);
+}
+
+// Segmented suffix sum over lanes with equal key: after the call the first lane of each run holds
+// the run total.  `end` is the first lane of the next run (or 32).
+__device__ __forceinline__ float seg_sum(float v, int lane, int end) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    float o = __shfl_down_sync(0xffffffffu, v, d);
+    if (lane + d < end) v += o;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double seg_sum(double v, int lane, int end) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    double o = __shfl_down_sync(0xffffffffu, v, d);
+    if (lane + d < end) v += o;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void run_bounds(int key, int lane, bool& head, int& end) {
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  head = (lane == 0) || (prev != key);
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned above = heads & ~((2u << lane) - 1u);
+  end = above ? (__ffs(above) - 1) : 32;
+}
+
+template <bool PATCHY, int NP>
+__global__ void __launch_bounds__(256) k_edge_mixed(KArgs a) {
+  const int64_t E = min(a.half_start[a.n], a.max_pairs);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float4* fhi = (float4*)a.force;
+  float4* flo = (float4*)a.force_lo;
+  float4* thi = (float4*)a.torque;
+  float4* tlo = (float4*)a.torque_lo;
+  for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
+    const int64_t e = base + lane;
+    const bool valid = e < E;
+    const int2 p = valid ? __ldcs(a.pairs + e) : make_int2(-1, -1);
+    PairOut<float> o;
+    o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
+    o.e = o.w = 0.f;
+    if (valid) {
+      const uint4 si = __ldg(a.fxp + p.x), sj = __ldg(a.fxp + p.y);
+      const Vec3<float> d = sep_mixed(si, sj, a);
+      const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+      if (PATCHY) {
+        if (r2 < a.rc2_f) {
+          const Patches<float, (PATCHY ? NP : 1)> Pi = load_patches<(PATCHY ? NP : 1)>(a, p.x, 0.f);
+          o = patchy_pair<float, (PATCHY ? NP : 1), true>(a, d, r2, Pi, p.x, p.y);
+        }
+      } else {
+        o = iso_pair<float>(a, d, r2, p.x, p.y);
+      }
+    }
+    const float eh = 0.5f * o.e, wh = 0.5f * o.w;
+    const bool nz = o.F.x != 0.f || o.F.y != 0.f || o.F.z != 0.f || eh != 0.f || wh != 0.f ||
+                    (PATCHY && (o.ti.x != 0.f || o.ti.y != 0.f || o.ti.z != 0.f || o.tj.x != 0.f ||
+                                o.tj.y != 0.f || o.tj.z != 0.f));
+    // j side: one atomic per contributing pair
+    if (nz) {
+      comp_atomic(fhi + p.y, flo + p.y, make_float4(-o.F.x, -o.F.y, -o.F.z, eh), wh);
+      if (PATCHY) comp_atomic(thi + p.y, tlo + p.y, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f), 0.f);
+    }
+    // i side: one atomic per run of equal i within the warp
+    bool head;
+    int end;
+    run_bounds(p.x, lane, head, end);
+    const unsigned any_nz = __ballot_sync(0xffffffffu, nz);
+    if (any_nz) {
+      const float fx = seg_sum(o.F.x, lane, end), fy = seg_sum(o.F.y, lane, end), fz = seg_sum(o.F.z, lane, end);
+      const float es = seg_sum(eh, lane, end), ws = seg_sum(wh, lane, end);
+      float tx = 0.f, ty = 0.f, tz = 0.f;
+      if (PATCHY) { tx = seg_sum(o.ti.x, lane, end); ty = seg_sum(o.ti.y, lane, end); tz = seg_sum(o.ti.z, lane, end); }
+      // a run contributes iff one of its lanes does
+      const unsigned run_mask = (end == 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
+      if (head && p.x >= 0 && (any_nz & run_mask)) {
+        comp_atomic(fhi + p.x, flo + p.x, make_float4(fx, fy, fz, es), ws);
+        if (PATCHY) comp_atomic(thi + p.x, tlo + p.x, make_float4(tx, ty, tz, 0.f), 0.f);
+      }
+    }
+  }
+}
+
+template <bool PATCHY, int NP>
+__global__ void __launch_bounds__(256) k_edge_fp64(KArgs a) {
+  const int64_t E = min(a.half_start[a.n], a.max_pairs);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double* f = (double*)a.force;
+  double* flo = (double*)a.force_lo;
+  double* t = (double*)a.torque;
+  for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
+    const int64_t e = base + lane;
+    const bool valid = e < E;
+    const int2 p = valid ? __ldcs(a.pairs + e) : make_int2(-1, -1);
+    PairOut<double> o;
+    o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
+    o.e = o.w = 0.0;
+    if (valid) {
+      const Vec3<double> d = sep_fp64(a.pos[p.x], a.pos[p.y], a);
+      const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+      if (PATCHY) {
+        if (r2 < a.rc2_d) {
+          const Patches<double, (PATCHY ? NP : 1)> Pi = load_patches<(PATCHY ? NP : 1)>(a, p.x, 0.0);
+          o = patchy_pair<double, (PATCHY ? NP : 1), true>(a, d, r2, Pi, p.x, p.y);
+        }
+      } else {
+        o = iso_pair<double>(a, d, r2, p.x, p.y);
+      }
+    }
+    const double eh = 0.5 * o.e, wh = 0.5 * o.w;
+    const bool nz = o.F.x != 0.0 || o.F.y != 0.0 || o.F.z != 0.0 || eh != 0.0 || wh != 0.0 ||
+                    (PATCHY && (o.ti.x != 0.0 || o.ti.y != 0.0 || o.ti.z != 0.0 || o.tj.x != 0.0 ||
+                                o.tj.y != 0.0 || o.tj.z != 0.0));
+    if (nz) {
+      double* fj = f + 4 * (size_t)p.y;
+      atomicAdd(fj + 0, -o.F.x); atomicAdd(fj + 1, -o.F.y); atomicAdd(fj + 2, -o.F.z); atomicAdd(fj + 3, eh);
+      atomicAdd(flo + 4 * (size_t)p.y + 3, wh);
+      if (PATCHY) {
+        double* tj = t + 4 * (size_t)p.y;
+        atomicAdd(tj + 0, o.tj.x); atomicAdd(tj + 1, o.tj.y); atomicAdd(tj + 2, o.tj.z);
+      }
+    }
+    bool head;
+    int end;
+    run_bounds(p.x, lane, head, end);
+    const unsigned any_nz = __ballot_sync(0xffffffffu, nz);
+    if (any_nz) {
+      const double fx = seg_sum(o.F.x, lane, end), fy = seg_sum(o.F.y, lane, end), fz = seg_sum(o.F.z, lane, end);
+      const double es = seg_sum(eh, lane, end), ws = seg_sum(wh, lane, end);
+      double tx = 0.0, ty = 0.0, tz = 0.0;
+      if (PATCHY) { tx = seg_sum(o.ti.x, lane, end); ty = seg_sum(o.ti.y, lane, end); tz = seg_sum(o.ti.z, lane, end); }
+      const unsigned run_mask = (end == 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
+      if (head && p.x >= 0 && (any_nz & run_mask)) {
+        double* fi = f + 4 * (size_t)p.x;
+        atomicAdd(fi + 0, fx); atomicAdd(fi + 1, fy); atomicAdd(fi + 2, fz); atomicAdd(fi + 3, es);
+        atomicAdd(flo + 4 * (size_t)p.x + 3, ws);
+        if (PATCHY) {
+          double* ti = t + 4 * (size_t)p.x;
+          atomicAdd(ti + 0, tx); atomicAdd(ti + 1, ty); atomicAdd(ti + 2, tz);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Launch
+// ------------------------------------------------------------------------------------------------
+
+static int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+template <bool PATCHY, int NP>
+static void launch_vertex(const KArgs& a, int block, cudaStream_t st) {
+  const int64_t threads = (int64_t)a.n * a.tpp;
+  const int grid = (int)((threads + block - 1) / block);
+  if (a.precision == MD_MIXED) {
+    switch (a.tpp) {
+      case 1: k_vertex_mixed<1, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+      case 2: k_vertex_mixed<2, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+      case 4: k_vertex_mixed<4, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+      default: k_vertex_mixed<8, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+    }
+  } else {
+    switch (a.tpp) {
+      case 1: k_vertex_fp64<1, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+      case 2: k_vertex_fp64<2, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+      case 4: k_vertex_fp64<4, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+      default: k_vertex_fp64<8, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
+    }
+  }
+}
+
+template <bool PATCHY, int NP>
+static void launch_edge(const KArgs& a, int block, cudaStream_t st) {
+  // persistent grid: enough resident warps to cover every SM, pairs taken in warp-sized chunks
+  int64_t want = (a.max_pairs + block - 1) / block;
+  int64_t cap = (int64_t)sm_count() * (2048 / block);
+  const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  if (a.precision == MD_MIXED) k_edge_mixed<PATCHY, NP><<<grid, block, 0, st>>>(a);
+  else k_edge_fp64<PATCHY, NP><<<grid, block, 0, st>>>(a);
+}
+
+cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st) {
+  if (block <= 0) block = (path == MD_VERTEX) ? 128 : 256;
+  if (path == MD_EDGE) {
+    const size_t elem = a.precision == MD_MIXED ? sizeof(float4) : sizeof(double4_32a);
+    cudaMemsetAsync(a.force, 0, elem * (size_t)a.n, st);
+    cudaMemsetAsync(a.force_lo, 0, elem * (size_t)a.n, st);
+    if (a.model == MD_PATCHY) {
+      cudaMemsetAsync(a.torque, 0, elem * (size_t)a.n, st);
+      cudaMemsetAsync(a.torque_lo, 0, elem * (size_t)a.n, st);
+    }
+  }
+  if (a.model != MD_PATCHY) {
+    if (path == MD_VERTEX) launch_vertex<false, 1>(a, block, st);
+    else launch_edge<false, 1>(a, block, st);
+  } else {
+    switch (a.n_patch) {
+      case 1: if (path == MD_VERTEX) launch_vertex<true, 1>(a, block, st); else launch_edge<true, 1>(a, block, st); break;
+      case 2: if (path == MD_VERTEX) launch_vertex<true, 2>(a, block, st); else launch_edge<true, 2>(a, block, st); break;
+      case 3: if (path == MD_VERTEX) launch_vertex<true, 3>(a, block, st); else launch_edge<true, 3>(a, block, st); break;
+      default: if (path == MD_VERTEX) launch_vertex<true, 4>(a, block, st); else launch_edge<true, 4>(a, block, st); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mdgb

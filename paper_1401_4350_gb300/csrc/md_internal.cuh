@@ -1,0 +1,236 @@
+// md_internal.cuh -- internal declarations shared by the CUDA translation units of libmdgb.
+//
+// Data layout in HBM (all arrays in cell-sorted slot order after md_build_cells):
+//   pos/vel/quat/angmom  double4_32a [n]      FP64 state (caller-owned)
+//   fxp                  uint4   [n]      x/L * 2^32 per axis (periodic by integer wrap-around)
+//   fxp_build            uint4   [n]      fxp at the last Verlet build (skin criterion)
+//   patch_lab            float4 or double4_32a [n][MD_MAX_PATCH]  lab-frame patch sites
+//   nbr                  int32   [max_neigh][n] full list, column-major (coalesced per warp)
+//   pairs                int2    [max_pairs]    half list (i, j), i < j, sorted by i
+//   force / force_lo     float4 or double4_32a [n]  (F, E_i) and (compensation of F, W_i)
+//   torque / torque_lo   float4 or double4_32a [n]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/md.h"
+
+namespace mdgb {
+
+constexpr int kScanItems = 4;      // elements per thread in the block scan
+constexpr int kScanThreads = 512;  // threads per scan block
+constexpr int kScanTile = kScanItems * kScanThreads;
+
+// Scratch words at the start of the scratch region (uint32 each).
+enum {
+  SCR_TICKET = 0,     // last-block ticket of the integrate kernels
+  SCR_DISPMAX = 1,    // max squared displacement since the build (float bits)
+  SCR_GATE = 2,       // 1 when a rebuild is due (read by the gated rebuild kernels)
+  SCR_TICKET2 = 3,    // spare ticket
+  SCR_WORDS = 64
+};
+
+// Everything a kernel needs, passed by value.
+struct KArgs {
+  int32_t n;
+  int32_t model;
+  int32_t precision;
+  int32_t max_neigh;
+  int64_t max_pairs;
+  int32_t n_patch;
+  int32_t tpp;
+  int32_t trace_capacity;
+  int32_t ncell[3];
+  int32_t ncell_total;
+  double box[3];
+  double inv_box[3];
+  double fxp_scale[3];   // 2^32 / L
+  float fxp_unit[3];     // L / 2^32 (FP32)
+  double fxp_unit_d[3];  // L / 2^32 (FP64)
+  double rc2_d, rv2_d;
+  float rc2_f;
+  float rv2_lo, rv2_hi;  // FP32 filter band of the Verlet build
+  float disp_thr2;       // (skin/2)^2, slightly reduced: conservative rebuild trigger
+  // Lennard-Jones constants (FP64 and FP32 copies)
+  double sig2_d, lj_c4_d, lj_shift_d, lj_c24_d;  // 4 eps, V(rc_iso), 24 eps
+  float sig2_f, lj_c4_f, lj_shift_f, lj_c24_f;
+  double rwca2_d;  // squared isotropic cut-off (LJ: rc^2; WCA and patchy core: 2^(1/3) sigma^2)
+  float rwca2_f;
+  // pairs whose r^2 falls inside (lo, hi) have their cut-off decided by exact_r2 in FP64
+  float rwca2_lo_f, rwca2_hi_f;
+  double rwca2_lo_d, rwca2_hi_d;
+  // patchy
+  double inv_delta2_d, eps_p_d, pgain_d;  // 1/delta^2, eps_p, 5 eps_p / delta^2
+  float inv_delta2_f, eps_p_f, pgain_f;
+  float half_log2e_f;                     // -0.5 * log2(e): exp(-q5/2) = exp2(half_log2e * q5)
+  double patch_reach2_d;                  // centre distance^2 beyond which every patch term vanishes
+  float patch_reach2_f;
+  double patch_body[MD_MAX_PATCH][3];
+  // integration
+  double dt, inv_mass, half_dt_over_m, dt_over_m, mass, inertia, inv_inertia;
+  float dt_over_m_f, half_dt_over_m_f, dt_f, inv_inertia_f, half_mass_f;
+  // state
+  double4_32a* pos;
+  double4_32a* vel;
+  double4_32a* quat;
+  double4_32a* angmom;
+  int32_t* id;
+  // workspace
+  int32_t* status;
+  double* energy;
+  int32_t* cell_start;
+  uint4* fxp;
+  uint4* fxp_build;
+  void* patch_lab;
+  int32_t* nbr;
+  int32_t* nbr_count;
+  int64_t* half_start;
+  int2* pairs;
+  void* force;
+  void* force_lo;
+  void* torque;
+  void* torque_lo;
+  double* trace;
+  uint32_t* scr_words;   // SCR_WORDS control words
+  double* block_partials;  // [max_blocks][8] FP64 partial sums of the integrate kernels
+  int32_t* cell_of;      // [n] cell id per slot (build)
+  int32_t* rank;         // [n] rank within cell (build)
+  int32_t* perm;         // [n] new slot -> old slot
+  int32_t* count_tmp;    // [max(ncell, n) + 1] counts for scans
+  int64_t* block_sums;   // scan block totals
+  double4_32a* tmp_d4;       // [4][n] gather buffers
+  int32_t* tmp_i;        // [n]
+  int32_t partial_capacity;
+};
+
+// Host-side helpers implemented in md_api.cu
+void set_error(const char* fmt, ...);
+
+// Launch wrappers (return cudaGetLastError() after the launch).
+cudaError_t launch_build_cells(const KArgs& a, const uint32_t* gate, cudaStream_t st);
+cudaError_t launch_build_verlet(const KArgs& a, int which, const uint32_t* gate, cudaStream_t st);
+cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st);
+// mode: 0 = first half step (kick + drift), 1 = middle (kick, energies, kick, drift), 2 = last (kick,
+// energies), 3 = energies only, 4 = derived arrays only (fxp, patch_lab).
+cudaError_t launch_integrate(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle,
+                             cudaStream_t st);
+cudaError_t launch_get_forces(const KArgs& a, double* fout, double* tout, cudaStream_t st);
+cudaError_t launch_init_ws(const KArgs& a, cudaStream_t st);
+int integrate_blocks(const KArgs& a);
+
+// ------------------------------------------------------------------------------------------------
+// Device helpers
+// ------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void record_error(int32_t* status, int code) {
+  atomicCAS(status + MD_STATUS_CODE, MD_OK, code);
+}
+
+// round(x * scale) mod 2^32 with one DFMA: adding 1.5 * 2^52 leaves the integer in the low mantissa bits.
+__device__ __forceinline__ uint32_t to_fixed(double x, double scale) {
+  double t = fma(x, scale, 6755399441055744.0);
+  return (uint32_t)(unsigned long long)__double_as_longlong(t);
+}
+
+__device__ __forceinline__ uint4 fixed3(const double4_32a& p, const KArgs& a) {
+  return make_uint4(to_fixed(p.x, a.fxp_scale[0]), to_fixed(p.y, a.fxp_scale[1]), to_fixed(p.z, a.fxp_scale[2]), 0u);
+}
+
+// cell coordinate of a fixed-point coordinate: floor(s * nc / 2^32), always in [0, nc)
+__device__ __forceinline__ int fixed_cell(uint32_t s, int nc) {
+  return (int)(((unsigned long long)s * (unsigned long long)nc) >> 32);
+}
+
+__device__ __forceinline__ float frcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float fexp2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Error of s = a + b (s computed in round-to-nearest): a + b = s + two_sum_err(a, b, s) exactly.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  float bb = __fsub_rn(s, a);
+  float aa = __fsub_rn(s, bb);
+  return __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
+}
+
+// Kahan-compensated accumulation: sum + (-comp) tracks the exact sum of the added terms.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float term) {
+  float y = __fsub_rn(term, comp);
+  float t = __fadd_rn(sum, y);
+  comp = __fsub_rn(__fsub_rn(t, sum), y);
+  sum = t;
+}
+
+}  // namespace mdgb
+
+namespace mdgb {
+
+// Lab-frame patch sites of one particle from its FP64 quaternion (w, x, y, z): p_lab = R(q) p_body.
+__device__ __forceinline__ void write_patch_lab(const KArgs& a, int i, const double4_32a& q) {
+  if (a.precision == MD_MIXED) {
+    float w = (float)q.x, x = (float)q.y, y = (float)q.z, z = (float)q.w;
+    float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                     {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                     {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+    float4* out = (float4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+    for (int p = 0; p < MD_MAX_PATCH; p++) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < a.n_patch) {
+        float bx = (float)a.patch_body[p][0], by = (float)a.patch_body[p][1], bz = (float)a.patch_body[p][2];
+        v.x = R[0][0] * bx + R[0][1] * by + R[0][2] * bz;
+        v.y = R[1][0] * bx + R[1][1] * by + R[1][2] * bz;
+        v.z = R[2][0] * bx + R[2][1] * by + R[2][2] * bz;
+      }
+      out[p] = v;
+    }
+  } else {
+    double w = q.x, x = q.y, y = q.z, z = q.w;
+    double R[3][3] = {{1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y)},
+                      {2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x)},
+                      {2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)}};
+    double4_32a* out = (double4_32a*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+    for (int p = 0; p < MD_MAX_PATCH; p++) {
+      double4_32a v = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      if (p < a.n_patch) {
+        double bx = a.patch_body[p][0], by = a.patch_body[p][1], bz = a.patch_body[p][2];
+        v.x = R[0][0] * bx + R[0][1] * by + R[0][2] * bz;
+        v.y = R[1][0] * bx + R[1][1] * by + R[1][2] * bz;
+        v.z = R[2][0] * bx + R[2][1] * by + R[2][2] * bz;
+      }
+      out[p] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ bool gate_closed(const uint32_t* gate) { return gate != nullptr && *gate == 0u; }
+
+}  // namespace mdgb
+
+namespace mdgb {
+template <typename T>
+cudaError_t launch_scan(const int32_t* cnt, T* out, int64_t* tile_tot, int m, const uint32_t* gate, cudaStream_t st);
+}  // namespace mdgb
+
+namespace mdgb {
+
+// Squared minimum-image distance in FP64, operation for operation the definition used for pair
+// membership: d = x_j - x_i; d -= L * rint(d / L); r^2 = (dx*dx + dy*dy) + dz*dz, no contraction.
+__device__ __forceinline__ double exact_r2(const double4_32a& pi, const double4_32a& pj, const KArgs& a) {
+  double d[3] = {__dsub_rn(pj.x, pi.x), __dsub_rn(pj.y, pi.y), __dsub_rn(pj.z, pi.z)};
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double q = rint(__ddiv_rn(d[c], a.box[c]));
+    d[c] = __dsub_rn(d[c], __dmul_rn(a.box[c], q));
+  }
+  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+}  // namespace mdgb

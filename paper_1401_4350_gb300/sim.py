@@ -1,0 +1,186 @@
+"""Simulation: caller-side owner of the device memory of one system.
+
+Allocates the FP64 state and the library workspace as torch CUDA tensors, fills md_params from a
+systems.System, and exposes the library's results (forces, lists, energies) in the caller's
+original particle order.  All computation happens in libmdgb.so.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .systems import System, LJ, WCA, PATCHY
+
+
+def default_capacities(system: System, slack: float = 1.6):
+    """Full-list columns and half-list pairs for the system's density with head-room."""
+    rho = system.n / float(np.prod(system.box))
+    nbar = 4.0 / 3.0 * math.pi * system.rv ** 3 * rho
+    max_neigh = int(slack * nbar + 24)
+    max_pairs = int(system.n * (0.5 * slack * nbar + 12)) + 1024
+    return max_neigh, max_pairs
+
+
+def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, tpp: int = 1, block: int = 0,
+                trace_capacity: int = 0) -> B.md_params:
+    mn, mp = default_capacities(system)
+    p = B.md_params()
+    p.n = system.n
+    p.model = {LJ: B.MD_LJ, WCA: B.MD_WCA, PATCHY: B.MD_PATCHY}[system.kind]
+    p.precision = precision
+    p.max_neigh = int(max_neigh or mn)
+    p.max_pairs = int(max_pairs or mp)
+    p.n_patch = len(system.patches) if system.kind == PATCHY else 0
+    p.threads_per_particle = tpp
+    p.block_size = block
+    p.trace_capacity = trace_capacity
+    for c in range(3):
+        p.box[c] = float(system.box[c])
+    p.rc, p.skin, p.dt, p.mass, p.inertia = system.rc, system.skin, system.dt, system.mass, system.inertia
+    p.eps, p.sigma, p.eps_p, p.delta = system.eps, system.sigma, system.eps_p, system.delta
+    for a, v in enumerate(np.asarray(system.patches)):
+        for c in range(3):
+            p.patch[a][c] = float(v[c])
+    return p
+
+
+class Simulation:
+    def __init__(self, system: System, precision: int = B.MD_MIXED, max_neigh=None, max_pairs=None, tpp: int = 1,
+                 block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None):
+        self.system = system
+        self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity)
+        rc = B.md_check_params(self.params)
+        if rc != B.MD_OK:
+            raise B.MDError(rc, B.last_error())
+        self.layout = B.md_workspace_layout(self.params)
+        self.device = torch.device(device)
+        self.stream = stream
+        n = system.n
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.pos = torch.zeros((n, 4), **f64)
+        self.vel = torch.zeros((n, 4), **f64)
+        self.quat = torch.zeros((n, 4), **f64) if system.kind == PATCHY else None
+        self.angmom = torch.zeros((n, 4), **f64) if system.kind == PATCHY else None
+        self.id = torch.arange(n, dtype=torch.int32, device=self.device)
+        self.ws = torch.empty(int(self.layout.total), dtype=torch.uint8, device=self.device)
+        assert self.ws.data_ptr() % 256 == 0
+        self.load_state(system.pos, system.vel, system.quat, system.angmom)
+        B.md_init_workspace(self.params, self.ws, self._st())
+
+    # -- plumbing ---------------------------------------------------------------------------------
+    def _st(self):
+        return self.stream
+
+    def state(self) -> B.md_state:
+        s = B.md_state()
+        s.pos, s.vel, s.id = self.pos.data_ptr(), self.vel.data_ptr(), self.id.data_ptr()
+        s.quat = self.quat.data_ptr() if self.quat is not None else None
+        s.angmom = self.angmom.data_ptr() if self.angmom is not None else None
+        return s
+
+    def load_state(self, pos, vel, quat=None, angmom=None):
+        n = self.system.n
+        self.pos[:, :3] = torch.as_tensor(np.asarray(pos, dtype=np.float64), device=self.device)
+        self.vel[:, :3] = torch.as_tensor(np.asarray(vel, dtype=np.float64), device=self.device)
+        if self.quat is not None:
+            self.quat[:] = torch.as_tensor(np.asarray(quat, dtype=np.float64), device=self.device)
+            self.angmom[:, :3] = torch.as_tensor(np.asarray(angmom, dtype=np.float64), device=self.device)
+        self.id.copy_(torch.arange(n, dtype=torch.int32, device=self.device))
+
+    def view(self, name: str, dtype, count: int):
+        off = getattr(self.layout, name)
+        nbytes = count * torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + nbytes].view(dtype)
+
+    # -- the C ABI --------------------------------------------------------------------------------
+    def build_cells(self):
+        B.md_build_cells(self.params, self.state(), self.ws, self._st())
+
+    def build_verlet(self, which=B.MD_LIST_BOTH):
+        B.md_build_verlet(self.params, self.state(), self.ws, which, self._st())
+
+    def forces_vertex(self):
+        B.md_forces_vertex(self.params, self.state(), self.ws, self._st())
+
+    def forces_edge(self):
+        B.md_forces_edge(self.params, self.state(), self.ws, self._st())
+
+    def prepare(self, path=B.MD_VERTEX):
+        B.md_prepare(self.params, self.state(), self.ws, path, self._st())
+
+    def step(self, nsteps: int, path=B.MD_VERTEX, use_graph=True):
+        B.md_step_verlet(self.params, self.state(), self.ws, nsteps, path, use_graph, self._st())
+
+    def status(self):
+        return B.md_read_status(self.params, self.ws, self._st())
+
+    # -- results in the caller's original order -------------------------------------------------
+    def _order(self):
+        return self.id.long()
+
+    def forces(self):
+        """(F[n,3], E_i[n], T[n,3] or None, W_i[n]) as FP64 numpy arrays in the original order."""
+        n = self.system.n
+        fo = torch.empty((n, 4), dtype=torch.float64, device=self.device)
+        to = torch.empty((n, 4), dtype=torch.float64, device=self.device)
+        B.md_get_forces(self.params, self.ws, fo, to, self._st())
+        torch.cuda.synchronize(self.device)
+        inv = torch.empty_like(self._order())
+        inv[self._order()] = torch.arange(n, device=self.device)
+        fo = fo[inv].cpu().numpy()
+        to = to[inv].cpu().numpy()
+        T = to[:, :3] if self.system.kind == PATCHY else None
+        return fo[:, :3], fo[:, 3], T, to[:, 3]
+
+    def positions(self):
+        inv = torch.empty_like(self._order())
+        inv[self._order()] = torch.arange(self.system.n, device=self.device)
+        return self.pos[inv, :3].cpu().numpy(), self.vel[inv, :3].cpu().numpy()
+
+    def orientations(self):
+        inv = torch.empty_like(self._order())
+        inv[self._order()] = torch.arange(self.system.n, device=self.device)
+        return self.quat[inv].cpu().numpy(), self.angmom[inv, :3].cpu().numpy()
+
+    def energies(self):
+        e = self.view("energy", torch.float64, B.MD_ENERGY_WORDS)
+        torch.cuda.synchronize(self.device)
+        e = e.cpu().numpy()
+        return {"U": e[B.MD_ENERGY_U], "KT": e[B.MD_ENERGY_KT], "KR": e[B.MD_ENERGY_KR], "W": e[B.MD_ENERGY_W]}
+
+    def trace(self):
+        t = self.view("trace", torch.float64, 4 * self.params.trace_capacity).view(-1, 4)
+        torch.cuda.synchronize(self.device)
+        return t.cpu().numpy()
+
+    def full_list_pairs(self):
+        """Sorted unique (i, j), i < j, in original ids, from the full list; also checks symmetry."""
+        n = self.system.n
+        cnt = self.view("nbr_count", torch.int32, n).long()
+        cap = self.params.max_neigh
+        nbr = self.view("nbr", torch.int32, n * cap).view(cap, n)
+        k = torch.arange(cap, device=self.device)[:, None]
+        mask = k < cnt[None, :]
+        jj = nbr[mask].long()
+        ii = torch.arange(n, device=self.device)[None, :].expand(cap, n)[mask]
+        ids = self._order()
+        oi, oj = ids[ii], ids[jj]
+        a, b = torch.minimum(oi, oj), torch.maximum(oi, oj)
+        key = a * n + b
+        key, counts = torch.unique(key, return_counts=True)
+        return (torch.stack([key // n, key % n], 1).cpu().numpy(), counts.cpu().numpy(), int(mask.sum()))
+
+    def half_list_pairs(self):
+        n = self.system.n
+        hs = self.view("half_start", torch.int64, n + 1)
+        total = int(hs[-1].item())
+        pairs = self.view("pairs", torch.int32, 2 * total).view(total, 2).long()
+        ids = self._order()
+        oi, oj = ids[pairs[:, 0]], ids[pairs[:, 1]]
+        a, b = torch.minimum(oi, oj), torch.maximum(oi, oj)
+        key = torch.sort(a * n + b).values
+        ordered = bool((pairs[:, 0] < pairs[:, 1]).all()) and bool((pairs[1:, 0] >= pairs[:-1, 0]).all())
+        return torch.stack([key // n, key % n], 1).cpu().numpy(), ordered
