@@ -142,7 +142,7 @@ typedef struct md_ws_layout {
   size_t fxp;            /* uint32[n][4]: positions as fractions of the box edge times 2^32   */
   size_t fxp_build;      /* uint32[n][4]: the same at the last Verlet build                   */
   size_t patch_lab;      /* float[n][MD_MAX_PATCH][4]: lab-frame patch sites (patchy, mixed)  */
-  size_t nbr;            /* int32[max_neigh][n]: full list, column-major (entry k of slot i at k*n+i) */
+  size_t nbr;            /* int32[ceil(max_neigh/4)][n][4]: full list; entry k of slot i at ((k/4)*n+i)*4+k%4 */
   size_t nbr_count;      /* int32[n]: full-list length per slot                               */
   size_t half_start;     /* int64[n + 1]: half-list row offsets                               */
   size_t pairs;          /* int32[max_pairs][2]: half list (i, j), i < j, sorted by i          */

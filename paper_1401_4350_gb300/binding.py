@@ -188,3 +188,4 @@ def md_read_status(p, ws, stream=None):
 
 def md_release_graphs(ws=None):
     return load().md_release_graphs(_ptr(ws) if ws is not None else None)
+

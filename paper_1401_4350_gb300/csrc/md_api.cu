@@ -115,7 +115,7 @@ static void make_layout(const md_params* p, Layout* L) {
   P.fxp = take(16 * n);
   P.fxp_build = take(16 * n);
   P.patch_lab = take(patchy ? fe * 4 * MD_MAX_PATCH * n : 0);
-  P.nbr = take(sizeof(int32_t) * n * (size_t)p->max_neigh);
+  P.nbr = take(sizeof(int32_t) * 4 * n * (size_t)((p->max_neigh + 3) / 4));
   P.nbr_count = take(sizeof(int32_t) * n);
   P.half_start = take(sizeof(int64_t) * (n + 1));
   P.pairs = take(8 * (size_t)p->max_pairs);
@@ -177,6 +177,16 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.rwca2_hi_f = f32(a.rwca2_d * (1.0 + 1e-5));
   a.rwca2_lo_d = a.rwca2_d * (1.0 - 1e-13);
   a.rwca2_hi_d = a.rwca2_d * (1.0 + 1e-13);
+  a.cubic = (p->box[0] == p->box[1] && p->box[1] == p->box[2]) ? 1 : 0;
+  {
+    const double u = p->box[0] / 4294967296.0, u2 = u * u;
+    a.inv_unit_f = f32(1.0 / u);
+    a.sig2_u = f32(p->sigma * p->sigma / u2);
+    a.rwca2_u = f32(a.rwca2_d / u2);
+    a.rwca2_lo_u = f32(a.rwca2_d * (1.0 - 1e-5) / u2);
+    a.rwca2_hi_u = f32(a.rwca2_d * (1.0 + 1e-5) / u2);
+    if (p->model == MD_PATCHY) a.u2_over_delta2 = f32(u2 / (p->delta * p->delta));
+  }
   const double sr2 = p->sigma * p->sigma / a.rwca2_d, sr6 = sr2 * sr2 * sr2;
   a.sig2_d = p->sigma * p->sigma;
   a.lj_c4_d = 4.0 * p->eps;
@@ -254,6 +264,22 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.partial_capacity = L.partial_capacity;
   return a;
 }
+
+// Kernel arguments of p and s with every workspace pointer left null, for entry points that take
+// their arrays from elsewhere.
+KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, nullptr, L);
+  a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
+  a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
+  a.force = nullptr; a.force_lo = nullptr; a.torque = nullptr; a.torque_lo = nullptr; a.trace = nullptr;
+  a.scr_words = nullptr; a.block_partials = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;
+  a.count_tmp = nullptr; a.block_sums = nullptr; a.tmp_d4 = nullptr; a.tmp_i = nullptr;
+  return a;
+}
+
+int check_params_only(const md_params* p) { return check(p); }
 
 static int check_state(const md_params* p, const md_state* s, const void* ws) {
   if (!s || !s->pos || !s->vel || !s->id) { set_error("state arrays pos, vel and id are required"); return MD_ERR_INVALID; }

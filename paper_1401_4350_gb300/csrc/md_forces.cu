@@ -28,7 +28,7 @@ namespace mdgb {
 // Lennard-Jones (Sec. Models, Eq. 1), cut and energy-shifted at the isotropic cut-off:
 // F_i = fs * d with d = x_j - x_i, V = 4 eps (sr12 - sr6) - V(rc).
 __device__ __forceinline__ void lj_terms(const KArgs& a, float r2, float& fs, float& pe) {
-  const float r2i = frcp_approx(r2);
+  const float r2i = frcp_refined(r2);
   const float sr2 = a.sig2_f * r2i;
   const float sr6 = sr2 * sr2 * sr2;
   fs = -a.lj_c24_f * sr6 * (2.f * sr6 - 1.f) * r2i;
@@ -61,8 +61,6 @@ __device__ __forceinline__ Vec3<double> sep_fp64(const double4_32a& pi, const do
   return {dx, dy, dz};
 }
 
-__device__ __forceinline__ float exp_neg_half(const KArgs& a, float q5) { return fexp2_approx(a.half_log2e_f * q5); }
-__device__ __forceinline__ double exp_neg_half(const KArgs& a, double q5) { return exp(-0.5 * q5); }
 
 template <typename R> __device__ __forceinline__ R rc2_of(const KArgs& a);
 template <> __device__ __forceinline__ float rc2_of<float>(const KArgs& a) { return a.rc2_f; }
@@ -71,20 +69,25 @@ template <typename R> __device__ __forceinline__ R rwca2_of(const KArgs& a);
 template <> __device__ __forceinline__ float rwca2_of<float>(const KArgs& a) { return a.rwca2_f; }
 template <> __device__ __forceinline__ double rwca2_of<double>(const KArgs& a) { return a.rwca2_d; }
 
-// Patch sites of a particle (lab frame).
+// Patch sites of a particle (lab frame): FP64 vectors, or (mixed) fixed-point integer offsets.
 template <typename R, int NP>
 struct Patches {
   Vec3<R> p[NP];
 };
 
 template <int NP>
-__device__ __forceinline__ Patches<float, NP> load_patches(const KArgs& a, int i, float) {
-  Patches<float, NP> P;
-  const float4* src = (const float4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+struct IPatches {
+  int3 p[NP];
+};
+
+template <int NP>
+__device__ __forceinline__ IPatches<NP> load_ipatches(const KArgs& a, int i) {
+  IPatches<NP> P;
+  const int4* src = (const int4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
 #pragma unroll
   for (int k = 0; k < NP; k++) {
-    float4 v = __ldg(src + k);
-    P.p[k] = {v.x, v.y, v.z};
+    const int4 v = __ldg(src + k);
+    P.p[k] = make_int3(v.x, v.y, v.z);
   }
   return P;
 }
@@ -100,19 +103,6 @@ __device__ __forceinline__ Patches<double, NP> load_patches(const KArgs& a, int 
   }
   return P;
 }
-
-template <typename R> __device__ __forceinline__ R pgain_of(const KArgs& a);
-template <> __device__ __forceinline__ float pgain_of<float>(const KArgs& a) { return a.pgain_f; }
-template <> __device__ __forceinline__ double pgain_of<double>(const KArgs& a) { return a.pgain_d; }
-template <typename R> __device__ __forceinline__ R epsp_of(const KArgs& a);
-template <> __device__ __forceinline__ float epsp_of<float>(const KArgs& a) { return a.eps_p_f; }
-template <> __device__ __forceinline__ double epsp_of<double>(const KArgs& a) { return a.eps_p_d; }
-template <typename R> __device__ __forceinline__ R invd2_of(const KArgs& a);
-template <> __device__ __forceinline__ float invd2_of<float>(const KArgs& a) { return a.inv_delta2_f; }
-template <> __device__ __forceinline__ double invd2_of<double>(const KArgs& a) { return a.inv_delta2_d; }
-template <typename R> __device__ __forceinline__ R reach2_of(const KArgs& a);
-template <> __device__ __forceinline__ float reach2_of<float>(const KArgs& a) { return a.patch_reach2_f; }
-template <> __device__ __forceinline__ double reach2_of<double>(const KArgs& a) { return a.patch_reach2_d; }
 
 // Everything one pair contributes.  F: force on i (on j: -F); e: pair energy; w: -(d . F);
 // ti, tj: torques on i and j.
@@ -155,45 +145,86 @@ __device__ __forceinline__ PairOut<R> iso_pair(const KArgs& a, const Vec3<R>& d,
   return o;
 }
 
+// Cubic boxes, fixed-point units u = L / 2^32.  The squared separation is the exact 64-bit integer
+// sum of squares of the coordinate differences, rounded once to FP32: the steep repulsive core
+// multiplies the relative error of r^2 by up to ~10 in the force, so r^2 is not formed from rounded
+// components.
+__device__ __forceinline__ float exact_r2u(int dx, int dy, int dz) {
+  const unsigned long long s = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+                               (unsigned long long)((long long)dz * dz);
+  return __ull2float_rn(s);
+}
+
+// Lennard-Jones terms in units u: returns t = -fs r^2 (dimensionless), fsu = -t / r2_u (so that the
+// force is fsu * d_u / u) and the shifted pair energy.
+__device__ __forceinline__ void lj_terms_u(const KArgs& a, float r2u, float& fsu, float& t, float& pe) {
+  const float r2i = frcp_refined(r2u);
+  const float sr2 = a.sig2_u * r2i;
+  const float sr6 = sr2 * sr2 * sr2;
+  t = a.lj_c24_f * sr6 * (2.f * sr6 - 1.f);
+  fsu = -t * r2i;
+  pe = a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f;
+}
+
+__device__ __forceinline__ bool iso_inside_u(const KArgs& a, float r2u, int i, int j) {
+  bool in = r2u < a.rwca2_lo_u;
+  if (!in && r2u < a.rwca2_hi_u) in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
+  return in;
+}
+
+// Isotropic pair of a cubic box from the integer separation ds.
+__device__ __forceinline__ PairOut<float> iso_pair_cubic(const KArgs& a, const int3& ds, int i, int j) {
+  PairOut<float> o;
+  const float r2u = exact_r2u(ds.x, ds.y, ds.z);
+  float fsu, t, pe;
+  lj_terms_u(a, r2u, fsu, t, pe);
+  const bool in = iso_inside_u(a, r2u, i, j);
+  const float g = in ? fsu * a.inv_unit_f : 0.f;
+  o.F = {g * (float)ds.x, g * (float)ds.y, g * (float)ds.z};
+  o.e = in ? pe : 0.f;
+  o.w = in ? t : 0.f;
+  o.ti = o.tj = {0.f, 0.f, 0.f};
+  return o;
+}
+
 // Patchy pair: WCA core + sum over patch pairs of -eps_p exp(-(r_ab/delta)^10 / 2), applied when the
 // centre distance is below rc.  Patch terms are skipped when the centre distance is beyond the
 // reach at which every term has underflowed to zero in this precision (exact).
-template <typename R, int NP, bool WANT_TJ>
-__device__ __forceinline__ PairOut<R> patchy_pair(const KArgs& a, const Vec3<R>& d, R r2, const Patches<R, NP>& Pi,
-                                                  int i, int j) {
-  PairOut<R> o;
-  o.F = o.ti = o.tj = {R(0), R(0), R(0)};
-  o.e = o.w = R(0);
-  if (!(r2 < rc2_of<R>(a))) return o;
-  if (iso_inside<R>(a, r2, i, j)) {
-    R fs, pe;
+template <int NP, bool WANT_TJ>
+__device__ __forceinline__ PairOut<double> patchy_pair(const KArgs& a, const Vec3<double>& d, double r2,
+                                                       const Patches<double, NP>& Pi, int i, int j) {
+  PairOut<double> o;
+  o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
+  o.e = o.w = 0.0;
+  if (!(r2 < a.rc2_d)) return o;
+  if (iso_inside<double>(a, r2, i, j)) {
+    double fs, pe;
     lj_terms(a, r2, fs, pe);
     o.F = {fs * d.x, fs * d.y, fs * d.z};
     o.e = pe;
   }
-  if (r2 < reach2_of<R>(a)) {
-    const Patches<R, NP> Pj = load_patches<NP>(a, j, R(0));
-    const R invd2 = invd2_of<R>(a), gain = pgain_of<R>(a), epsp = epsp_of<R>(a);
-    Vec3<R> Fb[NP];
+  if (r2 < a.patch_reach2_d) {
+    const Patches<double, NP> Pj = load_patches<NP>(a, j, 0.0);
+    Vec3<double> Fb[NP];
 #pragma unroll
-    for (int b = 0; b < NP; b++) Fb[b] = {R(0), R(0), R(0)};
+    for (int b = 0; b < NP; b++) Fb[b] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int pa = 0; pa < NP; pa++) {
-      Vec3<R> Fa = {R(0), R(0), R(0)};
-      const Vec3<R> base = {d.x - Pi.p[pa].x, d.y - Pi.p[pa].y, d.z - Pi.p[pa].z};
+      Vec3<double> Fa = {0.0, 0.0, 0.0};
+      const Vec3<double> base = {d.x - Pi.p[pa].x, d.y - Pi.p[pa].y, d.z - Pi.p[pa].z};
 #pragma unroll
       for (int b = 0; b < NP; b++) {
-        const Vec3<R> s = {base.x + Pj.p[b].x, base.y + Pj.p[b].y, base.z + Pj.p[b].z};
-        const R q = (s.x * s.x + s.y * s.y + s.z * s.z) * invd2;
-        const R q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
-        const R ex = exp_neg_half(a, q5);
-        o.e -= epsp * ex;
-        const R g = gain * q4 * ex;  // force on site a: g * s
+        const Vec3<double> s = {base.x + Pj.p[b].x, base.y + Pj.p[b].y, base.z + Pj.p[b].z};
+        const double q = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_d;
+        const double q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
+        const double ex = exp(-0.5 * q5);
+        o.e -= a.eps_p_d * ex;
+        const double g = a.pgain_d * q4 * ex;  // force on site a: g * s
         Fa.x += g * s.x; Fa.y += g * s.y; Fa.z += g * s.z;
         if (WANT_TJ) { Fb[b].x -= g * s.x; Fb[b].y -= g * s.y; Fb[b].z -= g * s.z; }
       }
       o.F.x += Fa.x; o.F.y += Fa.y; o.F.z += Fa.z;
-      const Vec3<R>& p = Pi.p[pa];
+      const Vec3<double>& p = Pi.p[pa];
       o.ti.x += p.y * Fa.z - p.z * Fa.y;
       o.ti.y += p.z * Fa.x - p.x * Fa.z;
       o.ti.z += p.x * Fa.y - p.y * Fa.x;
@@ -201,7 +232,78 @@ __device__ __forceinline__ PairOut<R> patchy_pair(const KArgs& a, const Vec3<R>&
     if (WANT_TJ) {
 #pragma unroll
       for (int b = 0; b < NP; b++) {
-        const Vec3<R>& p = Pj.p[b];
+        const Vec3<double>& p = Pj.p[b];
+        o.tj.x += p.y * Fb[b].z - p.z * Fb[b].y;
+        o.tj.y += p.z * Fb[b].x - p.x * Fb[b].z;
+        o.tj.z += p.x * Fb[b].y - p.y * Fb[b].x;
+      }
+    }
+  }
+  o.w = -(d.x * o.F.x + d.y * o.F.y + d.z * o.F.z);
+  return o;
+}
+
+// Mixed precision: every patch-pair separation is the exact 32-bit integer sum ds + p_b - p_a of
+// fixed-point centre difference and site offsets, converted to FP32 once; the rest is FP32.
+template <int NP, bool WANT_TJ>
+__device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, const int3& ds, const Vec3<float>& d,
+                                                            float r2, const IPatches<NP>& Pi, int i, int j) {
+  PairOut<float> o;
+  o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
+  o.e = o.w = 0.f;
+  if (!(r2 < a.rc2_f)) return o;
+  if (a.cubic) {
+    const PairOut<float> c = iso_pair_cubic(a, ds, i, j);
+    o.F = c.F;
+    o.e = c.e;
+  } else if (iso_inside<float>(a, r2, i, j)) {
+    float fs, pe;
+    lj_terms(a, r2, fs, pe);
+    o.F = {fs * d.x, fs * d.y, fs * d.z};
+    o.e = pe;
+  }
+  if (r2 < a.patch_reach2_f) {
+    const IPatches<NP> Pj = load_ipatches<NP>(a, j);
+    const float ux = a.fxp_unit[0], uy = a.fxp_unit[1], uz = a.fxp_unit[2];
+    Vec3<float> Fb[NP];
+#pragma unroll
+    for (int b = 0; b < NP; b++) Fb[b] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int pa = 0; pa < NP; pa++) {
+      Vec3<float> Fa = {0.f, 0.f, 0.f};
+      const int bx = ds.x - Pi.p[pa].x, by = ds.y - Pi.p[pa].y, bz = ds.z - Pi.p[pa].z;
+#pragma unroll
+      for (int b = 0; b < NP; b++) {
+        const int sx = bx + Pj.p[b].x, sy = by + Pj.p[b].y, sz = bz + Pj.p[b].z;
+        const Vec3<float> s = {(float)sx * ux, (float)sy * uy, (float)sz * uz};
+        float q;
+        if (a.cubic) {
+          // |s|^2 exactly in 64-bit integer units, converted once: q carries one rounding, which
+          // matters because (r/delta)^10 multiplies its relative error by five
+          const unsigned long long r2i = (unsigned long long)((long long)sx * sx) +
+                                         (unsigned long long)((long long)sy * sy) +
+                                         (unsigned long long)((long long)sz * sz);
+          q = __ull2float_rn(r2i) * a.u2_over_delta2;
+        } else {
+          q = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_f;
+        }
+        const float q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
+        const float ex = fexp2_approx(a.half_log2e_f * q5);
+        o.e -= a.eps_p_f * ex;
+        const float g = a.pgain_f * q4 * ex;
+        Fa.x += g * s.x; Fa.y += g * s.y; Fa.z += g * s.z;
+        if (WANT_TJ) { Fb[b].x -= g * s.x; Fb[b].y -= g * s.y; Fb[b].z -= g * s.z; }
+      }
+      o.F.x += Fa.x; o.F.y += Fa.y; o.F.z += Fa.z;
+      const Vec3<float> p = {(float)Pi.p[pa].x * ux, (float)Pi.p[pa].y * uy, (float)Pi.p[pa].z * uz};
+      o.ti.x += p.y * Fa.z - p.z * Fa.y;
+      o.ti.y += p.z * Fa.x - p.x * Fa.z;
+      o.ti.z += p.x * Fa.y - p.y * Fa.x;
+    }
+    if (WANT_TJ) {
+#pragma unroll
+      for (int b = 0; b < NP; b++) {
+        const Vec3<float> p = {(float)Pj.p[b].x * ux, (float)Pj.p[b].y * uy, (float)Pj.p[b].z * uz};
         o.tj.x += p.y * Fb[b].z - p.z * Fb[b].y;
         o.tj.y += p.z * Fb[b].x - p.x * Fb[b].z;
         o.tj.z += p.x * Fb[b].y - p.y * Fb[b].x;
@@ -256,7 +358,15 @@ __device__ __forceinline__ void group_reduce(Comp3& F, Comp3& T, float& e, float
   }
 }
 
-// Mixed precision vertex kernel.  MODEL_PATCHY selects the patchy pair, NP its patch count.
+// The full list is stored in groups of four: entries 4g..4g+3 of slot i form the int4 at g * n + i,
+// so a warp reads 512 contiguous bytes per group.  The kernels prefetch the next group while the
+// current one is evaluated and issue the four coordinate gathers of a group together, which keeps
+// enough loads in flight per SM to cover the memory latency.
+__device__ __forceinline__ int4 load_group(const int4* nb4, int g, int ng, size_t n) {
+  return g < ng ? __ldcs(nb4 + (size_t)g * n) : make_int4(-1, -1, -1, -1);
+}
+
+// Mixed precision vertex kernel.  PATCHY selects the patchy pair, NP its patch count.
 template <int TPP, bool PATCHY, int NP>
 __global__ void __launch_bounds__(256) k_vertex_mixed(KArgs a) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,28 +378,41 @@ __global__ void __launch_bounds__(256) k_vertex_mixed(KArgs a) {
   if (valid) {
     const uint4 si = __ldg(a.fxp + i);
     const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
-    const int* nb = a.nbr + i;
+    const int ng = (cnt + 3) >> 2;
+    const int4* nb4 = (const int4*)a.nbr + i;
     const size_t n = (size_t)a.n;
-    Patches<float, (PATCHY ? NP : 1)> Pi;
-    if (PATCHY) Pi = load_patches<(PATCHY ? NP : 1)>(a, i, 0.f);
-#pragma unroll 4
-    for (int k = l; k < cnt; k += TPP) {
-      const int j = __ldcs(nb + (size_t)k * n);
-      const uint4 sj = __ldg(a.fxp + j);
-      const Vec3<float> d = sep_mixed(si, sj, a);
-      const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-      if (PATCHY) {
-        const PairOut<float> o = patchy_pair<float, (PATCHY ? NP : 1), false>(a, d, r2, Pi, i, j);
-        comp_add(F, o.F);
-        comp_add(T, o.ti);
-        e += o.e;
-        w += o.w;
-      } else {
-        const PairOut<float> o = iso_pair<float>(a, d, r2, i, j);
-        comp_add(F, o.F);
-        e += o.e;
-        w += o.w;
+    IPatches<(PATCHY ? NP : 1)> Pi;
+    if (PATCHY) Pi = load_ipatches<(PATCHY ? NP : 1)>(a, i);
+    int4 cur = load_group(nb4, l, ng, n);
+    for (int g = l; g < ng; g += TPP) {
+      const int4 nxt = load_group(nb4, g + TPP, ng, n);
+      int jj[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (4 * g + u >= cnt || (unsigned)jj[u] >= (unsigned)a.n) jj[u] = -1;  // past the end, or never built
+      uint4 sj[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) sj[u] = __ldg(a.fxp + (jj[u] >= 0 ? jj[u] : i));
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        if (jj[u] < 0) continue;
+        const Vec3<float> d = sep_mixed(si, sj[u], a);
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        if (PATCHY) {
+          const int3 ds = make_int3((int)(sj[u].x - si.x), (int)(sj[u].y - si.y), (int)(sj[u].z - si.z));
+          const PairOut<float> o = patchy_pair_mixed<(PATCHY ? NP : 1), false>(a, ds, d, r2, Pi, i, jj[u]);
+          comp_add(F, o.F);
+          comp_add(T, o.ti);
+          e += o.e;
+          w += o.w;
+        } else {
+          const PairOut<float> o = iso_pair<float>(a, d, r2, i, jj[u]);
+          comp_add(F, o.F);
+          e += o.e;
+          w += o.w;
+        }
       }
+      cur = nxt;
     }
   }
   group_reduce<TPP>(F, T, e, w);
@@ -302,6 +425,126 @@ __global__ void __launch_bounds__(256) k_vertex_mixed(KArgs a) {
       ((float4*)a.torque)[i] = make_float4(T.s[0], T.s[1], T.s[2], 0.f);
       ((float4*)a.torque_lo)[i] = make_float4(T.lo[0], T.lo[1], T.lo[2], 0.f);
     }
+  }
+}
+
+// Mixed-precision vertex kernel for the isotropic models (LJ, WCA).  Per group of four list entries
+// the pair forces are summed in plain FP32 and the group sum enters the per-particle sum through a
+// Kahan step (FP32 sum plus compensation term).  In a cubic box the separations stay in fixed-point
+// units u (the integer difference converted to FP32) and the constants are rescaled instead:
+// r2_u = |d_u|^2, (sigma/r)^2 = sig2_u / r2_u, and the force sum is multiplied by 1/u once.
+// The cut-off is first decided against the FP32 threshold; a particle with a pair inside the narrow
+// band around rc^2 re-walks its list afterwards and corrects the pairs whose exact FP64 decision
+// differs (rare), so the hot loop carries no FP64 state.
+template <bool CUBIC>
+__device__ __forceinline__ void iso_pair_mixed_u(const KArgs& a, const uint4& si, const uint4& sj, float sig2,
+                                                 float& r2, float& t, float& r2i, float& sr6, float& dx, float& dy,
+                                                 float& dz) {
+  const int ix = (int)(sj.x - si.x), iy = (int)(sj.y - si.y), iz = (int)(sj.z - si.z);
+  dx = (float)ix;
+  dy = (float)iy;
+  dz = (float)iz;
+  if (CUBIC) {
+    r2 = exact_r2u(ix, iy, iz);
+  } else {
+    dx = __fmul_rn(dx, a.fxp_unit[0]);
+    dy = __fmul_rn(dy, a.fxp_unit[1]);
+    dz = __fmul_rn(dz, a.fxp_unit[2]);
+    // explicit rounding: the main loop and the band fix-up must take the same FP32 decision
+    r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+  }
+  r2i = frcp_refined(r2);
+  const float sr2 = sig2 * r2i;
+  sr6 = sr2 * sr2 * sr2;
+  t = a.lj_c24_f * sr6 * (2.f * sr6 - 1.f);  // -fs r^2
+}
+
+template <int TPP, bool CUBIC>
+__global__ void __launch_bounds__(256, 4) k_vertex_iso_mixed(KArgs a) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / TPP, l = gt % TPP;
+  const bool valid = i < a.n;
+  float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, e = 0.f, w = 0.f;
+  const float sig2 = CUBIC ? a.sig2_u : a.sig2_f;
+  const float thr = CUBIC ? a.rwca2_u : a.rwca2_f;
+  const float lo = CUBIC ? a.rwca2_lo_u : a.rwca2_lo_f, hi = CUBIC ? a.rwca2_hi_u : a.rwca2_hi_f;
+  const size_t n = (size_t)a.n;
+  const unsigned jmax = (unsigned)a.n - 1u;
+  const int4* nb4 = (const int4*)a.nbr + (valid ? i : 0);
+  int cnt = 0;
+  bool band = false;
+  uint4 si = make_uint4(0u, 0u, 0u, 0u);
+  if (valid) {
+    si = __ldg(a.fxp + i);
+    cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
+    const int ng = (cnt + 3) >> 2;
+    int4 cur = load_group(nb4, l, ng, n);
+    for (int g = l; g < ng; g += TPP) {
+      const int4 nxt = load_group(nb4, g + TPP, ng, n);
+      const int lim = cnt - 4 * g;  // entries of this group that are in the list (>= 1)
+      // an index can only be out of range in a list that was never built: clamp, never fault
+      const unsigned jj[4] = {min((unsigned)cur.x, jmax), min((unsigned)cur.y, jmax), min((unsigned)cur.z, jmax),
+                              min((unsigned)cur.w, jmax)};
+      uint4 sj[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) sj[u] = __ldg(a.fxp + jj[u]);
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        float r2, t, r2i, sr6, dx, dy, dz;
+        iso_pair_mixed_u<CUBIC>(a, si, sj[u], sig2, r2, t, r2i, sr6, dx, dy, dz);
+        const bool live = u < lim;
+        band |= live && r2 >= lo && r2 < hi;
+        const bool in = live && r2 < thr;
+        const float fs = in ? -t * r2i : 0.f;
+        gx += fs * dx;
+        gy += fs * dy;
+        gz += fs * dz;
+        e += in ? (a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f) : 0.f;
+        w += in ? t : 0.f;
+      }
+      kahan_add(fx, cx, gx);
+      kahan_add(fy, cy, gy);
+      kahan_add(fz, cz, gz);
+      cur = nxt;
+    }
+  }
+  if (band) {
+    // pairs near rc: take the side of the exact FP64 definition
+    for (int k = l; k < cnt; k += TPP) {
+      const unsigned j = min((unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n)), jmax);
+      float r2, t, r2i, sr6, dx, dy, dz;
+      iso_pair_mixed_u<CUBIC>(a, si, __ldg(a.fxp + j), sig2, r2, t, r2i, sr6, dx, dy, dz);
+      if (!(r2 >= lo && r2 < hi)) continue;
+      const bool fp32_in = r2 < thr;
+      const bool exact_in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
+      if (fp32_in == exact_in) continue;
+      const float sgn = exact_in ? 1.f : -1.f;
+      const float fs = -t * r2i * sgn;
+      kahan_add(fx, cx, fs * dx);
+      kahan_add(fy, cy, fs * dy);
+      kahan_add(fz, cz, fs * dz);
+      e += sgn * (a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f);
+      w += sgn * t;
+    }
+  }
+  // the sum is s - c; combine the threads of a particle
+  float lx = -cx, ly = -cy, lz = -cz;
+  if (TPP > 1) {
+#pragma unroll
+    for (int off = TPP / 2; off > 0; off >>= 1) {
+      float s2, l2;
+      s2 = __shfl_xor_sync(0xffffffffu, fx, off); l2 = __shfl_xor_sync(0xffffffffu, lx, off); comp_merge(fx, lx, s2, l2);
+      s2 = __shfl_xor_sync(0xffffffffu, fy, off); l2 = __shfl_xor_sync(0xffffffffu, ly, off); comp_merge(fy, ly, s2, l2);
+      s2 = __shfl_xor_sync(0xffffffffu, fz, off); l2 = __shfl_xor_sync(0xffffffffu, lz, off); comp_merge(fz, lz, s2, l2);
+      e += __shfl_xor_sync(0xffffffffu, e, off);
+      w += __shfl_xor_sync(0xffffffffu, w, off);
+    }
+  }
+  if (valid && l == 0) {
+    const float s = CUBIC ? a.inv_unit_f : 1.f;
+    ((float4*)a.force)[i] = make_float4(fx * s, fy * s, fz * s, 0.5f * e);
+    ((float4*)a.force_lo)[i] = make_float4(lx * s, ly * s, lz * s, 0.5f * w);
   }
 }
 
@@ -321,20 +564,31 @@ __global__ void __launch_bounds__(256) k_vertex_fp64(KArgs a) {
   if (valid) {
     const double4_32a pi = a.pos[i];
     const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
-    const int* nb = a.nbr + i;
+    const int ng = (cnt + 3) >> 2;
+    const int4* nb4 = (const int4*)a.nbr + i;
     const size_t n = (size_t)a.n;
     Patches<double, (PATCHY ? NP : 1)> Pi;
     if (PATCHY) Pi = load_patches<(PATCHY ? NP : 1)>(a, i, 0.0);
-    for (int k = l; k < cnt; k += TPP) {
-      const int j = __ldcs(nb + (size_t)k * n);
-      const Vec3<double> d = sep_fp64(pi, a.pos[j], a);
-      const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-      PairOut<double> o;
-      if (PATCHY) o = patchy_pair<double, (PATCHY ? NP : 1), false>(a, d, r2, Pi, i, j);
-      else o = iso_pair<double>(a, d, r2, i, j);
-      acc[0] += o.F.x; acc[1] += o.F.y; acc[2] += o.F.z;
-      acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z;
-      acc[6] += o.e; acc[7] += o.w;
+    int4 cur = load_group(nb4, l, ng, n);
+    for (int g = l; g < ng; g += TPP) {
+      const int4 nxt = load_group(nb4, g + TPP, ng, n);
+      int jj[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (4 * g + u >= cnt || (unsigned)jj[u] >= (unsigned)a.n) jj[u] = -1;
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        if (jj[u] < 0) continue;
+        const Vec3<double> d = sep_fp64(pi, a.pos[jj[u]], a);
+        const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        PairOut<double> o;
+        if (PATCHY) o = patchy_pair<(PATCHY ? NP : 1), false>(a, d, r2, Pi, i, jj[u]);
+        else o = iso_pair<double>(a, d, r2, i, jj[u]);
+        acc[0] += o.F.x; acc[1] += o.F.y; acc[2] += o.F.z;
+        acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z;
+        acc[6] += o.e; acc[7] += o.w;
+      }
+      cur = nxt;
     }
   }
   group_reduce_d<TPP>(acc, 8);
@@ -416,22 +670,28 @@ __global__ void __launch_bounds__(256) k_edge_mixed(KArgs a) {
   float4* flo = (float4*)a.force_lo;
   float4* thi = (float4*)a.torque;
   float4* tlo = (float4*)a.torque_lo;
+  int2 pn = (warp * 32 + lane < E) ? __ldcs(a.pairs + warp * 32 + lane) : make_int2(-1, -1);
   for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
-    const int64_t e = base + lane;
-    const bool valid = e < E;
-    const int2 p = valid ? __ldcs(a.pairs + e) : make_int2(-1, -1);
+    int2 p = pn;  // this chunk's pair; the next chunk's is loaded before the arithmetic
+    const int64_t en = base + nwarps * 32 + lane;
+    pn = en < E ? __ldcs(a.pairs + en) : make_int2(-1, -1);
+    if ((unsigned)p.x >= (unsigned)a.n || (unsigned)p.y >= (unsigned)a.n) p = make_int2(-1, -1);
+    const bool ok = p.x >= 0;
     PairOut<float> o;
     o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
     o.e = o.w = 0.f;
-    if (valid) {
+    if (ok) {
       const uint4 si = __ldg(a.fxp + p.x), sj = __ldg(a.fxp + p.y);
       const Vec3<float> d = sep_mixed(si, sj, a);
       const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
       if (PATCHY) {
         if (r2 < a.rc2_f) {
-          const Patches<float, (PATCHY ? NP : 1)> Pi = load_patches<(PATCHY ? NP : 1)>(a, p.x, 0.f);
-          o = patchy_pair<float, (PATCHY ? NP : 1), true>(a, d, r2, Pi, p.x, p.y);
+          const IPatches<(PATCHY ? NP : 1)> Pi = load_ipatches<(PATCHY ? NP : 1)>(a, p.x);
+          const int3 ds = make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z));
+          o = patchy_pair_mixed<(PATCHY ? NP : 1), true>(a, ds, d, r2, Pi, p.x, p.y);
         }
+      } else if (a.cubic) {
+        o = iso_pair_cubic(a, make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z)), p.x, p.y);
       } else {
         o = iso_pair<float>(a, d, r2, p.x, p.y);
       }
@@ -474,20 +734,23 @@ __global__ void __launch_bounds__(256) k_edge_fp64(KArgs a) {
   double* f = (double*)a.force;
   double* flo = (double*)a.force_lo;
   double* t = (double*)a.torque;
+  int2 pn = (warp * 32 + lane < E) ? __ldcs(a.pairs + warp * 32 + lane) : make_int2(-1, -1);
   for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
-    const int64_t e = base + lane;
-    const bool valid = e < E;
-    const int2 p = valid ? __ldcs(a.pairs + e) : make_int2(-1, -1);
+    int2 p = pn;  // this chunk's pair; the next chunk's is loaded before the arithmetic
+    const int64_t en = base + nwarps * 32 + lane;
+    pn = en < E ? __ldcs(a.pairs + en) : make_int2(-1, -1);
+    if ((unsigned)p.x >= (unsigned)a.n || (unsigned)p.y >= (unsigned)a.n) p = make_int2(-1, -1);
+    const bool ok = p.x >= 0;
     PairOut<double> o;
     o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
     o.e = o.w = 0.0;
-    if (valid) {
+    if (ok) {
       const Vec3<double> d = sep_fp64(a.pos[p.x], a.pos[p.y], a);
       const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
       if (PATCHY) {
         if (r2 < a.rc2_d) {
           const Patches<double, (PATCHY ? NP : 1)> Pi = load_patches<(PATCHY ? NP : 1)>(a, p.x, 0.0);
-          o = patchy_pair<double, (PATCHY ? NP : 1), true>(a, d, r2, Pi, p.x, p.y);
+          o = patchy_pair<(PATCHY ? NP : 1), true>(a, d, r2, Pi, p.x, p.y);
         }
       } else {
         o = iso_pair<double>(a, d, r2, p.x, p.y);
@@ -550,7 +813,23 @@ template <bool PATCHY, int NP>
 static void launch_vertex(const KArgs& a, int block, cudaStream_t st) {
   const int64_t threads = (int64_t)a.n * a.tpp;
   const int grid = (int)((threads + block - 1) / block);
-  if (a.precision == MD_MIXED) {
+  if (a.precision == MD_MIXED && !PATCHY) {
+    if (a.cubic) {
+      switch (a.tpp) {
+        case 1: k_vertex_iso_mixed<1, true><<<grid, block, 0, st>>>(a); break;
+        case 2: k_vertex_iso_mixed<2, true><<<grid, block, 0, st>>>(a); break;
+        case 4: k_vertex_iso_mixed<4, true><<<grid, block, 0, st>>>(a); break;
+        default: k_vertex_iso_mixed<8, true><<<grid, block, 0, st>>>(a); break;
+      }
+    } else {
+      switch (a.tpp) {
+        case 1: k_vertex_iso_mixed<1, false><<<grid, block, 0, st>>>(a); break;
+        case 2: k_vertex_iso_mixed<2, false><<<grid, block, 0, st>>>(a); break;
+        case 4: k_vertex_iso_mixed<4, false><<<grid, block, 0, st>>>(a); break;
+        default: k_vertex_iso_mixed<8, false><<<grid, block, 0, st>>>(a); break;
+      }
+    }
+  } else if (a.precision == MD_MIXED) {
     switch (a.tpp) {
       case 1: k_vertex_mixed<1, PATCHY, NP><<<grid, block, 0, st>>>(a); break;
       case 2: k_vertex_mixed<2, PATCHY, NP><<<grid, block, 0, st>>>(a); break;

@@ -40,18 +40,27 @@ __device__ __forceinline__ double4_32a qmul(const double4_32a& a, const double4_
 // q <- exp(omega dt / 2) (x) q for the lab-frame angular velocity omega = L / I.
 __device__ __forceinline__ double4_32a rotate(const KArgs& a, const double4_32a& q, const double4_32a& L) {
   if (a.precision == MD_MIXED) {
-    // rotation increment |omega| dt << 1 in FP32; composition and renormalisation in FP64
+    // The increment (dq - 1) (x) q of a rotation by |omega| dt << 1 is small: it is computed in FP32
+    // (cos(theta/2) - 1 = -2 sin^2(theta/4) keeps its relative precision) and added to the FP64
+    // quaternion, which is then renormalised with one Newton step (|q|^2 - 1 ~ 1e-13).
     const float wx = (float)L.x * a.inv_inertia_f, wy = (float)L.y * a.inv_inertia_f,
                 wz = (float)L.z * a.inv_inertia_f;
     const float wn = sqrtf(wx * wx + wy * wy + wz * wz);
     if (!(wn > 0.f)) return q;
-    float s, c;
-    sincosf(0.5f * wn * a.dt_f, &s, &c);
-    const float k = s / wn;
-    const double4_32a dq = make_double4_32a((double)c, (double)(wx * k), (double)(wy * k), (double)(wz * k));
-    double4_32a r = qmul(dq, q);
+    float s4, c4;
+    sincosf(0.25f * wn * a.dt_f, &s4, &c4);
+    const float cm1 = -2.f * s4 * s4;           // cos(theta/2) - 1
+    const float k = 2.f * s4 * c4 / wn;         // sin(theta/2) / |omega|
+    const float vx = wx * k, vy = wy * k, vz = wz * k;
+    const float qw = (float)q.x, qx = (float)q.y, qy = (float)q.z, qz = (float)q.w;
+    // (cm1, v) (x) (qw, qv) = (cm1 qw - v.qv, cm1 qv + qw v + v x qv)
+    const float dw = cm1 * qw - (vx * qx + vy * qy + vz * qz);
+    const float dx = cm1 * qx + qw * vx + (vy * qz - vz * qy);
+    const float dy = cm1 * qy + qw * vy + (vz * qx - vx * qz);
+    const float dz = cm1 * qz + qw * vz + (vx * qy - vy * qx);
+    double4_32a r = make_double4_32a(q.x + (double)dw, q.y + (double)dx, q.z + (double)dy, q.w + (double)dz);
     const double n2 = r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
-    const double f = 1.5 - 0.5 * n2;  // one Newton step of 1/sqrt(n2) from 1: |n2 - 1| ~ 1e-7
+    const double f = 1.5 - 0.5 * n2;
     return make_double4_32a(r.x * f, r.y * f, r.z * f, r.w * f);
   }
   const double wx = L.x * a.inv_inertia, wy = L.y * a.inv_inertia, wz = L.z * a.inv_inertia;
@@ -312,10 +321,13 @@ __global__ void k_init_ws(KArgs a) {
   if (t < MD_ENERGY_WORDS) a.energy[t] = 0.0;
   if (t < SCR_WORDS) a.scr_words[t] = 0u;
   for (int k = t; k < a.trace_capacity * 4; k += gridDim.x * blockDim.x) a.trace[k] = 0.0;
+  // empty lists until the first build: force kernels called early see no pairs
+  for (int k = t; k < a.n; k += gridDim.x * blockDim.x) a.nbr_count[k] = 0;
+  for (int k = t; k <= a.n; k += gridDim.x * blockDim.x) a.half_start[k] = 0;
 }
 
 cudaError_t launch_init_ws(const KArgs& a, cudaStream_t st) {
-  k_init_ws<<<64, 256, 0, st>>>(a);
+  k_init_ws<<<256, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

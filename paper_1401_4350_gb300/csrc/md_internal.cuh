@@ -5,7 +5,8 @@
 //   fxp                  uint4   [n]      x/L * 2^32 per axis (periodic by integer wrap-around)
 //   fxp_build            uint4   [n]      fxp at the last Verlet build (skin criterion)
 //   patch_lab            float4 or double4_32a [n][MD_MAX_PATCH]  lab-frame patch sites
-//   nbr                  int32   [max_neigh][n] full list, column-major (coalesced per warp)
+//   nbr                  int32   [ceil(max_neigh/4)][n][4] full list: entry k of slot i at
+//                        ((k/4) n + i) 4 + k%4 (int4 groups, coalesced per warp)
 //   pairs                int2    [max_pairs]    half list (i, j), i < j, sorted by i
 //   force / force_lo     float4 or double4_32a [n]  (F, E_i) and (compensation of F, W_i)
 //   torque / torque_lo   float4 or double4_32a [n]
@@ -59,6 +60,12 @@ struct KArgs {
   float rwca2_f;
   // pairs whose r^2 falls inside (lo, hi) have their cut-off decided by exact_r2 in FP64
   float rwca2_lo_f, rwca2_hi_f;
+  // cubic boxes: the same constants in fixed-point units (u = L / 2^32), so that pair arithmetic
+  // can run on the converted integer differences without scaling each component
+  int32_t cubic;
+  float inv_unit_f;                      // 1 / u
+  float sig2_u, rwca2_u, rwca2_lo_u, rwca2_hi_u;
+  float u2_over_delta2;                  // u^2 / delta^2 (patchy, cubic box)
   double rwca2_lo_d, rwca2_hi_d;
   // patchy
   double inv_delta2_d, eps_p_d, pgain_d;  // 1/delta^2, eps_p, 5 eps_p / delta^2
@@ -106,6 +113,8 @@ struct KArgs {
 
 // Host-side helpers implemented in md_api.cu
 void set_error(const char* fmt, ...);
+int check_params_only(const md_params* p);
+KArgs kernel_args_without_workspace(const md_params* p, const md_state* s);
 
 // Launch wrappers (return cudaGetLastError() after the launch).
 cudaError_t launch_build_cells(const KArgs& a, const uint32_t* gate, cudaStream_t st);
@@ -122,6 +131,11 @@ int integrate_blocks(const KArgs& a);
 // ------------------------------------------------------------------------------------------------
 // Device helpers
 // ------------------------------------------------------------------------------------------------
+
+// Position of entry k of slot i in the grouped full list.
+__device__ __forceinline__ size_t nbr_index(int k, int i, size_t n) {
+  return (((size_t)(k >> 2) * n + (size_t)i) << 2) + (size_t)(k & 3);
+}
 
 __device__ __forceinline__ void record_error(int32_t* status, int code) {
   atomicCAS(status + MD_STATUS_CODE, MD_OK, code);
@@ -146,6 +160,14 @@ __device__ __forceinline__ float frcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// 1/x from the hardware approximation refined by one Newton step, y + y (1 - x y): the steep
+// (sigma/r)^12 term multiplies the reciprocal's relative error by about nine, so the pair kernels
+// use this form.
+__device__ __forceinline__ float frcp_refined(float x) {
+  const float y = frcp_approx(x);
+  return __fmaf_rn(y, __fmaf_rn(-x, y, 1.f), y);
 }
 
 __device__ __forceinline__ float fexp2_approx(float x) {
@@ -173,39 +195,28 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float term) {
 
 namespace mdgb {
 
-// Lab-frame patch sites of one particle from its FP64 quaternion (w, x, y, z): p_lab = R(q) p_body.
+// Lab-frame patch sites of one particle from its FP64 quaternion (w, x, y, z): p_lab = R(q) p_body,
+// computed in FP64.  MD_MIXED stores each site as a 32-bit fixed-point offset from the centre in the
+// units of the centre coordinates (box fraction times 2^32), so that a patch-pair separation
+// x_j + p_b - x_i - p_a is an exact integer sum; MD_FP64 stores the FP64 vector.
 __device__ __forceinline__ void write_patch_lab(const KArgs& a, int i, const double4_32a& q) {
-  if (a.precision == MD_MIXED) {
-    float w = (float)q.x, x = (float)q.y, y = (float)q.z, z = (float)q.w;
-    float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
-                     {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
-                     {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
-    float4* out = (float4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
-    for (int p = 0; p < MD_MAX_PATCH; p++) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (p < a.n_patch) {
-        float bx = (float)a.patch_body[p][0], by = (float)a.patch_body[p][1], bz = (float)a.patch_body[p][2];
-        v.x = R[0][0] * bx + R[0][1] * by + R[0][2] * bz;
-        v.y = R[1][0] * bx + R[1][1] * by + R[1][2] * bz;
-        v.z = R[2][0] * bx + R[2][1] * by + R[2][2] * bz;
-      }
-      out[p] = v;
+  const double w = q.x, x = q.y, y = q.z, z = q.w;
+  const double R[3][3] = {{1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y)},
+                          {2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x)},
+                          {2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)}};
+  for (int p = 0; p < MD_MAX_PATCH; p++) {
+    double v[3] = {0.0, 0.0, 0.0};
+    if (p < a.n_patch) {
+      const double bx = a.patch_body[p][0], by = a.patch_body[p][1], bz = a.patch_body[p][2];
+      for (int c = 0; c < 3; c++) v[c] = R[c][0] * bx + R[c][1] * by + R[c][2] * bz;
     }
-  } else {
-    double w = q.x, x = q.y, y = q.z, z = q.w;
-    double R[3][3] = {{1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y)},
-                      {2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x)},
-                      {2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)}};
-    double4_32a* out = (double4_32a*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
-    for (int p = 0; p < MD_MAX_PATCH; p++) {
-      double4_32a v = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-      if (p < a.n_patch) {
-        double bx = a.patch_body[p][0], by = a.patch_body[p][1], bz = a.patch_body[p][2];
-        v.x = R[0][0] * bx + R[0][1] * by + R[0][2] * bz;
-        v.y = R[1][0] * bx + R[1][1] * by + R[1][2] * bz;
-        v.z = R[2][0] * bx + R[2][1] * by + R[2][2] * bz;
-      }
-      out[p] = v;
+    if (a.precision == MD_MIXED) {
+      int4* out = (int4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+      out[p] = make_int4((int)to_fixed(v[0], a.fxp_scale[0]), (int)to_fixed(v[1], a.fxp_scale[1]),
+                         (int)to_fixed(v[2], a.fxp_scale[2]), 0);
+    } else {
+      double4_32a* out = (double4_32a*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+      out[p] = make_double4_32a(v[0], v[1], v[2], 0.0);
     }
   }
 }

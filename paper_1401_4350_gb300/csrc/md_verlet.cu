@@ -1,6 +1,7 @@
 // md_verlet.cu -- Verlet lists (Sec. Methods): for every particle i, every j whose minimum-image
 // distance is below rv = rc + rs, found through the 27 neighbouring cells, one particle per thread.
-// The full list (vertex path) is column-major so that a warp's k-th entries are one 128-byte line;
+// The full list (vertex path) is stored in groups of four entries per slot, group-major, so that a
+// warp's g-th groups are 512 contiguous bytes;
 // the half list (edge path) holds each pair once as (i, j), i < j, grouped by i.
 #include "md_internal.cuh"
 
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(128) k_verlet_full(KArgs a, const uint32_t* ga
             bool in = r2 < a.rv2_lo;
             if (!in && r2 < a.rv2_hi) in = exact_r2(a.pos[i], a.pos[j], a) < a.rv2_d;
             if (in) {
-              if (cnt < a.max_neigh) a.nbr[(size_t)cnt * n + i] = j;
+              if (cnt < a.max_neigh) a.nbr[nbr_index(cnt, i, n)] = j;
               cnt++;
               half += (j > i);
             }
@@ -77,7 +78,7 @@ __global__ void k_verlet_half(KArgs a, const uint32_t* gate) {
   const int cnt = min(a.nbr_count[i], a.max_neigh);
   int64_t w = a.half_start[i];
   for (int k = 0; k < cnt; k++) {
-    const int j = a.nbr[(size_t)k * n + i];
+    const int j = a.nbr[nbr_index(k, i, n)];
     if (j > i) {
       if (w < a.max_pairs) a.pairs[w] = make_int2(i, j);
       w++;

@@ -1,0 +1,71 @@
+"""Small driver for profiling one phase of the path under ncu.
+
+  python -m paper_1401_4350_gb300.profile --workload lj524288 --what forces --path vertex --reps 2
+
+Builds the seeded workload, prepares cells, lists and forces once, then launches the chosen phase
+`reps` times (forces: md_forces_vertex / md_forces_edge; build: md_build_cells + md_build_verlet;
+step: md_step_verlet of one step).  Prints the median CUDA-event time per launch.
+"""
+from __future__ import annotations
+
+import argparse
+import statistics
+
+import torch
+
+from . import binding as B
+from . import build as mdbuild
+from . import systems
+from .sim import Simulation
+
+WORKLOADS = {
+    "lj1m": lambda: systems.make_lj(1_048_576, 0.85, 1.0, seed=1001),
+    "lj524288": lambda: systems.make_lj(524_288, 0.85, 1.0, seed=1001),
+    "lj262144": lambda: systems.make_lj(262_144, 0.85, 1.0, seed=1001),
+    "wca1m": lambda: systems.make_wca(1_048_576, 0.2, seed=1002),
+    "patchy262k": lambda: systems.make_patchy(262_144, 0.3, seed=1003),
+}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="lj524288", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--path", default="vertex", choices=["vertex", "edge"])
+    ap.add_argument("--what", default="forces", choices=["forces", "build", "step"])
+    ap.add_argument("--tpp", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args(argv)
+    mdbuild.build()
+    B.load()
+    torch.cuda.set_device(0)
+    s = WORKLOADS[a.workload]()
+    prec = B.MD_MIXED if a.precision == "mixed" else B.MD_FP64
+    path = B.MD_VERTEX if a.path == "vertex" else B.MD_EDGE
+    sim = Simulation(s, prec, tpp=a.tpp)
+    sim.prepare(path)
+    if a.what == "forces":
+        fn = sim.forces_vertex if path == B.MD_VERTEX else sim.forces_edge
+    elif a.what == "build":
+        def fn():
+            sim.build_cells()
+            sim.build_verlet(B.MD_LIST_BOTH if path == B.MD_EDGE else B.MD_LIST_FULL)
+    else:
+        def fn():
+            sim.step(1, path, use_graph=False)
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    status = sim.status()
+    assert status[B.MD_STATUS_CODE] == 0, status
+    print(f"{a.workload} {a.precision} {a.path} {a.what}: median {statistics.median(times):.4f} ms over {a.reps}")
+
+
+if __name__ == "__main__":
+    main()

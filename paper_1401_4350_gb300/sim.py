@@ -161,7 +161,8 @@ class Simulation:
         n = self.system.n
         cnt = self.view("nbr_count", torch.int32, n).long()
         cap = self.params.max_neigh
-        nbr = self.view("nbr", torch.int32, n * cap).view(cap, n)
+        ng = (cap + 3) // 4
+        nbr = self.view("nbr", torch.int32, ng * n * 4).view(ng, n, 4).permute(0, 2, 1).reshape(ng * 4, n)[:cap]
         k = torch.arange(cap, device=self.device)[:, None]
         mask = k < cnt[None, :]
         jj = nbr[mask].long()
