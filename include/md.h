@@ -251,6 +251,35 @@ int md_read_status(const md_params* p, const void* ws, int32_t* host_out, void* 
 /* Releases the CUDA graphs cached by md_step_verlet for this workspace (ws may be NULL: all). */
 int md_release_graphs(const void* ws);
 
+/*
+ * ---- The cell build for callers that cannot allocate device memory ---------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that may not allocate
+ * GPU memory themselves (code running inside another framework's memory pool, plug-ins that only
+ * receive the arrays they work on, programs that must not grow their device footprint after
+ * start-up) and so cannot provide the workspace that md_build_cells takes its scratch from.
+ *
+ * md_build_cells_static does exactly what md_build_cells does (same kernels, same deterministic
+ * result), but its scratch (cell counts, ranks, the permutation and the reorder buffers) lives in a
+ * file-scope static device array of md_static_scratch_bytes() bytes (about 5 MiB) that every GPU
+ * which loads the library keeps until the process exits.  The caller passes the state (reordered in
+ * place, as by md_build_cells) and the outputs:
+ *   cell_start  int32[ncell_total + 1]  (ncell from md_workspace_layout)
+ *   fxp         uint32[n][4], 16-byte aligned
+ *   patch_lab   patchy only: [n][MD_MAX_PATCH] int4 (MD_MIXED) or double4 (MD_FP64), 32-byte aligned
+ * Limit: n <= MD_STATIC_MAX_N, else MD_ERR_INVALID with a message.  The call allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents (the counts that must start at
+ * zero are cleared by each call): calls whose kernels may overlap on the GPU race and must be
+ * serialised by the caller.
+ */
+#define MD_STATIC_MAX_N 32768
+int md_build_cells_static(const md_params* p, md_state* s, int32_t* cell_start, uint32_t* fxp, void* patch_lab,
+                          void* stream);
+
+/* Size in bytes of the static scratch array used by md_build_cells_static. */
+int md_static_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
         "md_get_forces": ([_P, _V, _V, _V, _V], ctypes.c_int),
         "md_read_status": ([_P, _V, ctypes.POINTER(ctypes.c_int32), _V], ctypes.c_int),
         "md_release_graphs": ([_V], ctypes.c_int),
+        "md_build_cells_static": ([_P, _S, _V, _V, _V, _V], ctypes.c_int),
+        "md_static_scratch_bytes": ([], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -189,3 +191,15 @@ def md_read_status(p, ws, stream=None):
 def md_release_graphs(ws=None):
     return load().md_release_graphs(_ptr(ws) if ws is not None else None)
 
+
+MD_STATIC_MAX_N = 32768
+
+
+def md_build_cells_static(p, s, cell_start, fxp, patch_lab=None, stream=None):
+    """The cell build without a workspace: scratch from the library's static device array."""
+    return _check(load().md_build_cells_static(ctypes.byref(p), ctypes.byref(s), _ptr(cell_start), _ptr(fxp),
+                                               _ptr(patch_lab), _stream(stream)))
+
+
+def md_static_scratch_bytes() -> int:
+    return load().md_static_scratch_bytes()
