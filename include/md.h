@@ -111,6 +111,9 @@ typedef struct md_params {
   int32_t threads_per_particle;  /* vertex path: 1, 2, 4 or 8 threads cooperate on a particle   */
   int32_t block_size;            /* force-kernel CTA size: 0 (default) or 32..1024, multiple of 32 */
   int32_t trace_capacity;        /* energy-trace rows kept by md_step_verlet (0 = none)         */
+  int32_t energy_every;          /* md_step_verlet reduces energies on steps that are multiples of this
+                                    (0 or 1: every step); the last step of a call always            */
+  int32_t reserved;              /* must be 0                                                    */
   double box[3];                 /* periodic box edges; each must exceed 2 rv                    */
   double rc;                     /* centre-centre cut-off (LJ: 2.5 sigma; WCA: 2^(1/6) sigma)    */
   double skin;                   /* Verlet skin rs > 0; rv = rc + rs                             */
@@ -135,7 +138,7 @@ typedef struct md_state {
 typedef struct md_ws_layout {
   size_t total;          /* md_workspace_bytes()                                              */
   int32_t ncell[3];      /* cells per axis (an axis with fewer than 3 cells of edge >= rv is 1) */
-  int32_t force_elem;    /* bytes per force component: 4 (MD_MIXED) or 8 (MD_FP64)            */
+  int32_t force_elem;    /* bytes per component of the force result (8: double)                */
   size_t status;         /* int32[MD_STATUS_WORDS]                                             */
   size_t energy;         /* double[MD_ENERGY_WORDS]                                            */
   size_t cell_start;     /* int32[ncells + 1]: first slot of each cell (cell-sorted order)     */
@@ -146,10 +149,11 @@ typedef struct md_ws_layout {
   size_t nbr_count;      /* int32[n]: full-list length per slot                               */
   size_t half_start;     /* int64[n + 1]: half-list row offsets                               */
   size_t pairs;          /* int32[max_pairs][2]: half list (i, j), i < j, sorted by i          */
-  size_t force;          /* [n][4] (Fx, Fy, Fz, E_i): float (mixed) or double (FP64)         */
-  size_t force_lo;       /* [n][4] (compensation of Fx, Fy, Fz; W_i)                          */
-  size_t torque;         /* [n][4] (tx, ty, tz, -) patchy                                      */
-  size_t torque_lo;      /* [n][4] compensation of the torque (mixed)                         */
+  size_t force;          /* double[n][4] (Fx, Fy, Fz, E_i): the force result of either precision */
+  size_t virial;         /* double[n] W_i: half of each pair virial -r_ij.F_ij                  */
+  size_t torque;         /* double[n][4] (tx, ty, tz, 0), patchy                                */
+  size_t acc;            /* mixed edge path: float[4][n][4] FP32 atomic accumulators and their
+                            compensation terms (force hi, force lo, torque hi, torque lo)          */
   size_t trace;          /* double[trace_capacity][4]: (step, K, U, W) rows of md_step_verlet */
   size_t scratch;        /* internal scratch                                                  */
 } md_ws_layout;
@@ -224,9 +228,10 @@ int md_forces_edge(const md_params* p, md_state* s, void* ws, void* stream);
  * Patchy particles also get the half kicks of the angular momentum and the
  * exact rotation q <- exp(omega dt / 2) (x) q, omega = L / inertia.
  * Precondition: cells, lists and forces are current for the state (e.g. after
- * md_prepare).  Each step's kinetic, potential energy and virial are reduced
- * in FP64 into the energy words and, when trace_capacity > 0, appended to the
- * trace.  use_graph != 0 replays a CUDA graph per step whose rebuild is a
+ * md_prepare).  The kinetic and potential energy and the virial of every
+ * energy_every-th step (and of the last step of the call) are reduced in FP64
+ * into the energy words and, when trace_capacity > 0, written to trace row
+ * step % trace_capacity.  use_graph != 0 replays a CUDA graph per step whose rebuild is a
  * conditional node (the graph is built on the first call for this
  * (p, s, ws, path) and cached); use_graph = 0 launches the kernels directly and
  * the rebuild kernels return early when no rebuild is due.

@@ -32,7 +32,8 @@ class md_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("model", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_neigh", ctypes.c_int32), ("max_pairs", ctypes.c_int64), ("n_patch", ctypes.c_int32),
                 ("threads_per_particle", ctypes.c_int32), ("block_size", ctypes.c_int32),
-                ("trace_capacity", ctypes.c_int32), ("box", ctypes.c_double * 3), ("rc", ctypes.c_double),
+                ("trace_capacity", ctypes.c_int32), ("energy_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("box", ctypes.c_double * 3), ("rc", ctypes.c_double),
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double), ("mass", ctypes.c_double),
                 ("inertia", ctypes.c_double), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("eps_p", ctypes.c_double), ("delta", ctypes.c_double),
@@ -48,7 +49,7 @@ class md_ws_layout(ctypes.Structure):
     _fields_ = [("total", ctypes.c_size_t), ("ncell", ctypes.c_int32 * 3), ("force_elem", ctypes.c_int32)] + [
         (name, ctypes.c_size_t) for name in
         ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr", "nbr_count", "half_start",
-         "pairs", "force", "force_lo", "torque", "torque_lo", "trace", "scratch")]
+         "pairs", "force", "virial", "torque", "acc", "trace", "scratch")]
 
 
 class MDError(RuntimeError):

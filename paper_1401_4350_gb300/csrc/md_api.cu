@@ -78,6 +78,8 @@ static int check(const md_params* p) {
     return MD_ERR_INVALID;
   }
   if (p->trace_capacity < 0) { set_error("trace_capacity must be >= 0"); return MD_ERR_INVALID; }
+  if (p->energy_every < 0) { set_error("energy_every must be >= 0"); return MD_ERR_INVALID; }
+  if (p->reserved != 0) { set_error("reserved must be 0"); return MD_ERR_INVALID; }
   if (p->model == MD_PATCHY) {
     if (p->n_patch < 1 || p->n_patch > MD_MAX_PATCH) { set_error("n_patch must be in 1..%d", MD_MAX_PATCH); return MD_ERR_INVALID; }
     if (!(p->inertia > 0.0) || !(p->delta > 0.0)) { set_error("inertia and delta must be > 0"); return MD_ERR_INVALID; }
@@ -98,7 +100,7 @@ static void make_layout(const md_params* p, Layout* L) {
   cell_dims(p, nc);
   const size_t n = (size_t)p->n;
   const size_t ncell = (size_t)nc[0] * nc[1] * nc[2];
-  const size_t fe = p->precision == MD_MIXED ? 4 : 8;
+  const size_t fe = p->precision == MD_MIXED ? 4 : 8;  // patch sites: int4 (mixed) or double4
   const bool patchy = p->model == MD_PATCHY;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -108,7 +110,7 @@ static void make_layout(const md_params* p, Layout* L) {
   };
   md_ws_layout& P = L->pub;
   for (int c = 0; c < 3; c++) P.ncell[c] = nc[c];
-  P.force_elem = (int32_t)fe;
+  P.force_elem = 8;
   P.status = take(sizeof(int32_t) * MD_STATUS_WORDS);
   P.energy = take(sizeof(double) * MD_ENERGY_WORDS);
   P.cell_start = take(sizeof(int32_t) * (ncell + 1));
@@ -119,10 +121,10 @@ static void make_layout(const md_params* p, Layout* L) {
   P.nbr_count = take(sizeof(int32_t) * n);
   P.half_start = take(sizeof(int64_t) * (n + 1));
   P.pairs = take(8 * (size_t)p->max_pairs);
-  P.force = take(fe * 4 * n);
-  P.force_lo = take(fe * 4 * n);
-  P.torque = take(patchy ? fe * 4 * n : 0);
-  P.torque_lo = take(patchy ? fe * 4 * n : 0);
+  P.force = take(32 * n);
+  P.virial = take(8 * n);
+  P.torque = take(patchy ? 32 * n : 0);
+  P.acc = take(p->precision == MD_MIXED ? 16 * n * (patchy ? 4 : 2) : 0);
   P.trace = take(sizeof(double) * 4 * (size_t)p->trace_capacity);
   P.scratch = off;
   L->scr_words = take(sizeof(uint32_t) * SCR_WORDS);
@@ -154,6 +156,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.n_patch = p->model == MD_PATCHY ? p->n_patch : 0;
   a.tpp = p->threads_per_particle;
   a.trace_capacity = p->trace_capacity;
+  a.energy_every = p->energy_every > 1 ? p->energy_every : 1;
   for (int c = 0; c < 3; c++) {
     a.ncell[c] = L.pub.ncell[c];
     a.box[c] = p->box[c];
@@ -247,10 +250,10 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.nbr_count = (int32_t*)(w + L.pub.nbr_count);
   a.half_start = (int64_t*)(w + L.pub.half_start);
   a.pairs = (int2*)(w + L.pub.pairs);
-  a.force = (void*)(w + L.pub.force);
-  a.force_lo = (void*)(w + L.pub.force_lo);
-  a.torque = (void*)(w + L.pub.torque);
-  a.torque_lo = (void*)(w + L.pub.torque_lo);
+  a.force = (double4_32a*)(w + L.pub.force);
+  a.virial = (double*)(w + L.pub.virial);
+  a.torque = (double4_32a*)(w + L.pub.torque);
+  a.acc = (float4*)(w + L.pub.acc);
   a.trace = (double*)(w + L.pub.trace);
   a.scr_words = (uint32_t*)(w + L.scr_words);
   a.block_partials = (double*)(w + L.block_partials);
@@ -273,7 +276,7 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   KArgs a = make_args(p, s, nullptr, L);
   a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
   a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
-  a.force = nullptr; a.force_lo = nullptr; a.torque = nullptr; a.torque_lo = nullptr; a.trace = nullptr;
+  a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
   a.scr_words = nullptr; a.block_partials = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;
   a.count_tmp = nullptr; a.block_sums = nullptr; a.tmp_d4 = nullptr; a.tmp_i = nullptr;
   return a;

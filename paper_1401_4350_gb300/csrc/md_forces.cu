@@ -17,780 +17,9 @@
 // Per-particle sums are FP32 with a Kahan compensation term (vertex) or FP32 atomics whose
 // rounding error is recovered with TwoSum from the returned old value and accumulated in a
 // second array (edge).
-#include "md_internal.cuh"
+#include "md_forces.cuh"
 
 namespace mdgb {
-
-// ------------------------------------------------------------------------------------------------
-// Pair terms
-// ------------------------------------------------------------------------------------------------
-
-// Lennard-Jones (Sec. Models, Eq. 1), cut and energy-shifted at the isotropic cut-off:
-// F_i = fs * d with d = x_j - x_i, V = 4 eps (sr12 - sr6) - V(rc).
-__device__ __forceinline__ void lj_terms(const KArgs& a, float r2, float& fs, float& pe) {
-  const float r2i = frcp_refined(r2);
-  const float sr2 = a.sig2_f * r2i;
-  const float sr6 = sr2 * sr2 * sr2;
-  fs = -a.lj_c24_f * sr6 * (2.f * sr6 - 1.f) * r2i;
-  pe = a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f;
-}
-
-__device__ __forceinline__ void lj_terms(const KArgs& a, double r2, double& fs, double& pe) {
-  const double r2i = __drcp_rn(r2);
-  const double sr2 = a.sig2_d * r2i;
-  const double sr6 = sr2 * sr2 * sr2;
-  fs = -a.lj_c24_d * sr6 * (2.0 * sr6 - 1.0) * r2i;
-  pe = a.lj_c4_d * sr6 * (sr6 - 1.0) - a.lj_shift_d;
-}
-
-template <typename R>
-struct Vec3 {
-  R x, y, z;
-};
-
-__device__ __forceinline__ Vec3<float> sep_mixed(const uint4& si, const uint4& sj, const KArgs& a) {
-  return {(float)(int)(sj.x - si.x) * a.fxp_unit[0], (float)(int)(sj.y - si.y) * a.fxp_unit[1],
-          (float)(int)(sj.z - si.z) * a.fxp_unit[2]};
-}
-
-__device__ __forceinline__ Vec3<double> sep_fp64(const double4_32a& pi, const double4_32a& pj, const KArgs& a) {
-  double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-  dx -= a.box[0] * rint(dx * a.inv_box[0]);
-  dy -= a.box[1] * rint(dy * a.inv_box[1]);
-  dz -= a.box[2] * rint(dz * a.inv_box[2]);
-  return {dx, dy, dz};
-}
-
-
-template <typename R> __device__ __forceinline__ R rc2_of(const KArgs& a);
-template <> __device__ __forceinline__ float rc2_of<float>(const KArgs& a) { return a.rc2_f; }
-template <> __device__ __forceinline__ double rc2_of<double>(const KArgs& a) { return a.rc2_d; }
-template <typename R> __device__ __forceinline__ R rwca2_of(const KArgs& a);
-template <> __device__ __forceinline__ float rwca2_of<float>(const KArgs& a) { return a.rwca2_f; }
-template <> __device__ __forceinline__ double rwca2_of<double>(const KArgs& a) { return a.rwca2_d; }
-
-// Patch sites of a particle (lab frame): FP64 vectors, or (mixed) fixed-point integer offsets.
-template <typename R, int NP>
-struct Patches {
-  Vec3<R> p[NP];
-};
-
-template <int NP>
-struct IPatches {
-  int3 p[NP];
-};
-
-template <int NP>
-__device__ __forceinline__ IPatches<NP> load_ipatches(const KArgs& a, int i) {
-  IPatches<NP> P;
-  const int4* src = (const int4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
-#pragma unroll
-  for (int k = 0; k < NP; k++) {
-    const int4 v = __ldg(src + k);
-    P.p[k] = make_int3(v.x, v.y, v.z);
-  }
-  return P;
-}
-
-template <int NP>
-__device__ __forceinline__ Patches<double, NP> load_patches(const KArgs& a, int i, double) {
-  Patches<double, NP> P;
-  const double4_32a* src = (const double4_32a*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
-#pragma unroll
-  for (int k = 0; k < NP; k++) {
-    double4_32a v = src[k];
-    P.p[k] = {v.x, v.y, v.z};
-  }
-  return P;
-}
-
-// Everything one pair contributes.  F: force on i (on j: -F); e: pair energy; w: -(d . F);
-// ti, tj: torques on i and j.
-template <typename R>
-struct PairOut {
-  Vec3<R> F, ti, tj;
-  R e, w;
-};
-
-template <typename R> __device__ __forceinline__ R rwca2_lo_of(const KArgs& a);
-template <> __device__ __forceinline__ float rwca2_lo_of<float>(const KArgs& a) { return a.rwca2_lo_f; }
-template <> __device__ __forceinline__ double rwca2_lo_of<double>(const KArgs& a) { return a.rwca2_lo_d; }
-template <typename R> __device__ __forceinline__ R rwca2_hi_of(const KArgs& a);
-template <> __device__ __forceinline__ float rwca2_hi_of<float>(const KArgs& a) { return a.rwca2_hi_f; }
-template <> __device__ __forceinline__ double rwca2_hi_of<double>(const KArgs& a) { return a.rwca2_hi_d; }
-
-// Cut-off test of the isotropic part.  The Lennard-Jones force is not shifted, so it jumps at rc:
-// pairs within a narrow band of rc^2 are decided with the exact FP64 distance of the FP64
-// positions, which makes the decision the same as the definition's in either precision.
-template <typename R>
-__device__ __forceinline__ bool iso_inside(const KArgs& a, R r2, int i, int j) {
-  bool in = r2 < rwca2_lo_of<R>(a);
-  if (!in && r2 < rwca2_hi_of<R>(a)) in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
-  return in;
-}
-
-// Isotropic pair (LJ or WCA) at separation d, r2 = |d|^2.
-template <typename R>
-__device__ __forceinline__ PairOut<R> iso_pair(const KArgs& a, const Vec3<R>& d, R r2, int i, int j) {
-  PairOut<R> o;
-  R fs, pe;
-  lj_terms(a, r2, fs, pe);
-  const bool in = iso_inside<R>(a, r2, i, j);
-  fs = in ? fs : R(0);
-  pe = in ? pe : R(0);
-  o.F = {fs * d.x, fs * d.y, fs * d.z};
-  o.e = pe;
-  o.w = -fs * r2;
-  o.ti = o.tj = {R(0), R(0), R(0)};
-  return o;
-}
-
-// Cubic boxes, fixed-point units u = L / 2^32.  The squared separation is the exact 64-bit integer
-// sum of squares of the coordinate differences, rounded once to FP32: the steep repulsive core
-// multiplies the relative error of r^2 by up to ~10 in the force, so r^2 is not formed from rounded
-// components.
-__device__ __forceinline__ float exact_r2u(int dx, int dy, int dz) {
-  const unsigned long long s = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
-                               (unsigned long long)((long long)dz * dz);
-  return __ull2float_rn(s);
-}
-
-// Lennard-Jones terms in units u: returns t = -fs r^2 (dimensionless), fsu = -t / r2_u (so that the
-// force is fsu * d_u / u) and the shifted pair energy.
-__device__ __forceinline__ void lj_terms_u(const KArgs& a, float r2u, float& fsu, float& t, float& pe) {
-  const float r2i = frcp_refined(r2u);
-  const float sr2 = a.sig2_u * r2i;
-  const float sr6 = sr2 * sr2 * sr2;
-  t = a.lj_c24_f * sr6 * (2.f * sr6 - 1.f);
-  fsu = -t * r2i;
-  pe = a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f;
-}
-
-__device__ __forceinline__ bool iso_inside_u(const KArgs& a, float r2u, int i, int j) {
-  bool in = r2u < a.rwca2_lo_u;
-  if (!in && r2u < a.rwca2_hi_u) in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
-  return in;
-}
-
-// Isotropic pair of a cubic box from the integer separation ds.
-__device__ __forceinline__ PairOut<float> iso_pair_cubic(const KArgs& a, const int3& ds, int i, int j) {
-  PairOut<float> o;
-  const float r2u = exact_r2u(ds.x, ds.y, ds.z);
-  float fsu, t, pe;
-  lj_terms_u(a, r2u, fsu, t, pe);
-  const bool in = iso_inside_u(a, r2u, i, j);
-  const float g = in ? fsu * a.inv_unit_f : 0.f;
-  o.F = {g * (float)ds.x, g * (float)ds.y, g * (float)ds.z};
-  o.e = in ? pe : 0.f;
-  o.w = in ? t : 0.f;
-  o.ti = o.tj = {0.f, 0.f, 0.f};
-  return o;
-}
-
-// Patchy pair: WCA core + sum over patch pairs of -eps_p exp(-(r_ab/delta)^10 / 2), applied when the
-// centre distance is below rc.  Patch terms are skipped when the centre distance is beyond the
-// reach at which every term has underflowed to zero in this precision (exact).
-template <int NP, bool WANT_TJ>
-__device__ __forceinline__ PairOut<double> patchy_pair(const KArgs& a, const Vec3<double>& d, double r2,
-                                                       const Patches<double, NP>& Pi, int i, int j) {
-  PairOut<double> o;
-  o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
-  o.e = o.w = 0.0;
-  if (!(r2 < a.rc2_d)) return o;
-  if (iso_inside<double>(a, r2, i, j)) {
-    double fs, pe;
-    lj_terms(a, r2, fs, pe);
-    o.F = {fs * d.x, fs * d.y, fs * d.z};
-    o.e = pe;
-  }
-  if (r2 < a.patch_reach2_d) {
-    const Patches<double, NP> Pj = load_patches<NP>(a, j, 0.0);
-    Vec3<double> Fb[NP];
-#pragma unroll
-    for (int b = 0; b < NP; b++) Fb[b] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int pa = 0; pa < NP; pa++) {
-      Vec3<double> Fa = {0.0, 0.0, 0.0};
-      const Vec3<double> base = {d.x - Pi.p[pa].x, d.y - Pi.p[pa].y, d.z - Pi.p[pa].z};
-#pragma unroll
-      for (int b = 0; b < NP; b++) {
-        const Vec3<double> s = {base.x + Pj.p[b].x, base.y + Pj.p[b].y, base.z + Pj.p[b].z};
-        const double q = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_d;
-        const double q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
-        const double ex = exp(-0.5 * q5);
-        o.e -= a.eps_p_d * ex;
-        const double g = a.pgain_d * q4 * ex;  // force on site a: g * s
-        Fa.x += g * s.x; Fa.y += g * s.y; Fa.z += g * s.z;
-        if (WANT_TJ) { Fb[b].x -= g * s.x; Fb[b].y -= g * s.y; Fb[b].z -= g * s.z; }
-      }
-      o.F.x += Fa.x; o.F.y += Fa.y; o.F.z += Fa.z;
-      const Vec3<double>& p = Pi.p[pa];
-      o.ti.x += p.y * Fa.z - p.z * Fa.y;
-      o.ti.y += p.z * Fa.x - p.x * Fa.z;
-      o.ti.z += p.x * Fa.y - p.y * Fa.x;
-    }
-    if (WANT_TJ) {
-#pragma unroll
-      for (int b = 0; b < NP; b++) {
-        const Vec3<double>& p = Pj.p[b];
-        o.tj.x += p.y * Fb[b].z - p.z * Fb[b].y;
-        o.tj.y += p.z * Fb[b].x - p.x * Fb[b].z;
-        o.tj.z += p.x * Fb[b].y - p.y * Fb[b].x;
-      }
-    }
-  }
-  o.w = -(d.x * o.F.x + d.y * o.F.y + d.z * o.F.z);
-  return o;
-}
-
-// Mixed precision: every patch-pair separation is the exact 32-bit integer sum ds + p_b - p_a of
-// fixed-point centre difference and site offsets, converted to FP32 once; the rest is FP32.
-template <int NP, bool WANT_TJ>
-__device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, const int3& ds, const Vec3<float>& d,
-                                                            float r2, const IPatches<NP>& Pi, int i, int j) {
-  PairOut<float> o;
-  o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
-  o.e = o.w = 0.f;
-  if (!(r2 < a.rc2_f)) return o;
-  if (a.cubic) {
-    const PairOut<float> c = iso_pair_cubic(a, ds, i, j);
-    o.F = c.F;
-    o.e = c.e;
-  } else if (iso_inside<float>(a, r2, i, j)) {
-    float fs, pe;
-    lj_terms(a, r2, fs, pe);
-    o.F = {fs * d.x, fs * d.y, fs * d.z};
-    o.e = pe;
-  }
-  if (r2 < a.patch_reach2_f) {
-    const IPatches<NP> Pj = load_ipatches<NP>(a, j);
-    const float ux = a.fxp_unit[0], uy = a.fxp_unit[1], uz = a.fxp_unit[2];
-    Vec3<float> Fb[NP];
-#pragma unroll
-    for (int b = 0; b < NP; b++) Fb[b] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int pa = 0; pa < NP; pa++) {
-      Vec3<float> Fa = {0.f, 0.f, 0.f};
-      const int bx = ds.x - Pi.p[pa].x, by = ds.y - Pi.p[pa].y, bz = ds.z - Pi.p[pa].z;
-#pragma unroll
-      for (int b = 0; b < NP; b++) {
-        const int sx = bx + Pj.p[b].x, sy = by + Pj.p[b].y, sz = bz + Pj.p[b].z;
-        const Vec3<float> s = {(float)sx * ux, (float)sy * uy, (float)sz * uz};
-        float q;
-        if (a.cubic) {
-          // |s|^2 exactly in 64-bit integer units, converted once: q carries one rounding, which
-          // matters because (r/delta)^10 multiplies its relative error by five
-          const unsigned long long r2i = (unsigned long long)((long long)sx * sx) +
-                                         (unsigned long long)((long long)sy * sy) +
-                                         (unsigned long long)((long long)sz * sz);
-          q = __ull2float_rn(r2i) * a.u2_over_delta2;
-        } else {
-          q = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_f;
-        }
-        const float q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
-        const float ex = fexp2_approx(a.half_log2e_f * q5);
-        o.e -= a.eps_p_f * ex;
-        const float g = a.pgain_f * q4 * ex;
-        Fa.x += g * s.x; Fa.y += g * s.y; Fa.z += g * s.z;
-        if (WANT_TJ) { Fb[b].x -= g * s.x; Fb[b].y -= g * s.y; Fb[b].z -= g * s.z; }
-      }
-      o.F.x += Fa.x; o.F.y += Fa.y; o.F.z += Fa.z;
-      const Vec3<float> p = {(float)Pi.p[pa].x * ux, (float)Pi.p[pa].y * uy, (float)Pi.p[pa].z * uz};
-      o.ti.x += p.y * Fa.z - p.z * Fa.y;
-      o.ti.y += p.z * Fa.x - p.x * Fa.z;
-      o.ti.z += p.x * Fa.y - p.y * Fa.x;
-    }
-    if (WANT_TJ) {
-#pragma unroll
-      for (int b = 0; b < NP; b++) {
-        const Vec3<float> p = {(float)Pj.p[b].x * ux, (float)Pj.p[b].y * uy, (float)Pj.p[b].z * uz};
-        o.tj.x += p.y * Fb[b].z - p.z * Fb[b].y;
-        o.tj.y += p.z * Fb[b].x - p.x * Fb[b].z;
-        o.tj.z += p.x * Fb[b].y - p.y * Fb[b].x;
-      }
-    }
-  }
-  o.w = -(d.x * o.F.x + d.y * o.F.y + d.z * o.F.z);
-  return o;
-}
-
-// ------------------------------------------------------------------------------------------------
-// Vertex-based kernels
-// ------------------------------------------------------------------------------------------------
-
-struct Comp3 {
-  float s[3], lo[3];
-};
-
-__device__ __forceinline__ void comp_add(Comp3& c, const Vec3<float>& v) {
-  // lo holds minus the Kahan compensation: the sum is s + lo
-  float cx = -c.lo[0], cy = -c.lo[1], cz = -c.lo[2];
-  kahan_add(c.s[0], cx, v.x);
-  kahan_add(c.s[1], cy, v.y);
-  kahan_add(c.s[2], cz, v.z);
-  c.lo[0] = -cx; c.lo[1] = -cy; c.lo[2] = -cz;
-}
-
-// Combine two compensated sums (s1 + lo1) + (s2 + lo2) without losing the rounding of s1 + s2.
-__device__ __forceinline__ void comp_merge(float& s, float& lo, float s2, float lo2) {
-  const float t = __fadd_rn(s, s2);
-  const float err = two_sum_err(s, s2, t);
-  lo = __fadd_rn(__fadd_rn(lo, lo2), err);
-  s = t;
-}
-
-template <int TPP>
-__device__ __forceinline__ void group_reduce(Comp3& F, Comp3& T, float& e, float& w) {
-  if (TPP == 1) return;
-#pragma unroll
-  for (int off = TPP / 2; off > 0; off >>= 1) {
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      float s2 = __shfl_xor_sync(0xffffffffu, F.s[c], off);
-      float l2 = __shfl_xor_sync(0xffffffffu, F.lo[c], off);
-      comp_merge(F.s[c], F.lo[c], s2, l2);
-      s2 = __shfl_xor_sync(0xffffffffu, T.s[c], off);
-      l2 = __shfl_xor_sync(0xffffffffu, T.lo[c], off);
-      comp_merge(T.s[c], T.lo[c], s2, l2);
-    }
-    e += __shfl_xor_sync(0xffffffffu, e, off);
-    w += __shfl_xor_sync(0xffffffffu, w, off);
-  }
-}
-
-// The full list is stored in groups of four: entries 4g..4g+3 of slot i form the int4 at g * n + i,
-// so a warp reads 512 contiguous bytes per group.  The kernels prefetch the next group while the
-// current one is evaluated and issue the four coordinate gathers of a group together, which keeps
-// enough loads in flight per SM to cover the memory latency.
-__device__ __forceinline__ int4 load_group(const int4* nb4, int g, int ng, size_t n) {
-  return g < ng ? __ldcs(nb4 + (size_t)g * n) : make_int4(-1, -1, -1, -1);
-}
-
-// Mixed precision vertex kernel.  PATCHY selects the patchy pair, NP its patch count.
-template <int TPP, bool PATCHY, int NP>
-__global__ void __launch_bounds__(256) k_vertex_mixed(KArgs a) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt / TPP, l = gt % TPP;
-  const bool valid = i < a.n;
-  Comp3 F = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  Comp3 T = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  float e = 0.f, w = 0.f;
-  if (valid) {
-    const uint4 si = __ldg(a.fxp + i);
-    const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
-    const int ng = (cnt + 3) >> 2;
-    const int4* nb4 = (const int4*)a.nbr + i;
-    const size_t n = (size_t)a.n;
-    IPatches<(PATCHY ? NP : 1)> Pi;
-    if (PATCHY) Pi = load_ipatches<(PATCHY ? NP : 1)>(a, i);
-    int4 cur = load_group(nb4, l, ng, n);
-    for (int g = l; g < ng; g += TPP) {
-      const int4 nxt = load_group(nb4, g + TPP, ng, n);
-      int jj[4] = {cur.x, cur.y, cur.z, cur.w};
-#pragma unroll
-      for (int u = 0; u < 4; u++)
-        if (4 * g + u >= cnt || (unsigned)jj[u] >= (unsigned)a.n) jj[u] = -1;  // past the end, or never built
-      uint4 sj[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) sj[u] = __ldg(a.fxp + (jj[u] >= 0 ? jj[u] : i));
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        if (jj[u] < 0) continue;
-        const Vec3<float> d = sep_mixed(si, sj[u], a);
-        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-        if (PATCHY) {
-          const int3 ds = make_int3((int)(sj[u].x - si.x), (int)(sj[u].y - si.y), (int)(sj[u].z - si.z));
-          const PairOut<float> o = patchy_pair_mixed<(PATCHY ? NP : 1), false>(a, ds, d, r2, Pi, i, jj[u]);
-          comp_add(F, o.F);
-          comp_add(T, o.ti);
-          e += o.e;
-          w += o.w;
-        } else {
-          const PairOut<float> o = iso_pair<float>(a, d, r2, i, jj[u]);
-          comp_add(F, o.F);
-          e += o.e;
-          w += o.w;
-        }
-      }
-      cur = nxt;
-    }
-  }
-  group_reduce<TPP>(F, T, e, w);
-  if (valid && l == 0) {
-    float4* fo = (float4*)a.force;
-    float4* flo = (float4*)a.force_lo;
-    fo[i] = make_float4(F.s[0], F.s[1], F.s[2], 0.5f * e);
-    flo[i] = make_float4(F.lo[0], F.lo[1], F.lo[2], 0.5f * w);
-    if (PATCHY) {
-      ((float4*)a.torque)[i] = make_float4(T.s[0], T.s[1], T.s[2], 0.f);
-      ((float4*)a.torque_lo)[i] = make_float4(T.lo[0], T.lo[1], T.lo[2], 0.f);
-    }
-  }
-}
-
-// Mixed-precision vertex kernel for the isotropic models (LJ, WCA).  Per group of four list entries
-// the pair forces are summed in plain FP32 and the group sum enters the per-particle sum through a
-// Kahan step (FP32 sum plus compensation term).  In a cubic box the separations stay in fixed-point
-// units u (the integer difference converted to FP32) and the constants are rescaled instead:
-// r2_u = |d_u|^2, (sigma/r)^2 = sig2_u / r2_u, and the force sum is multiplied by 1/u once.
-// The cut-off is first decided against the FP32 threshold; a particle with a pair inside the narrow
-// band around rc^2 re-walks its list afterwards and corrects the pairs whose exact FP64 decision
-// differs (rare), so the hot loop carries no FP64 state.
-template <bool CUBIC>
-__device__ __forceinline__ void iso_pair_mixed_u(const KArgs& a, const uint4& si, const uint4& sj, float sig2,
-                                                 float& r2, float& t, float& r2i, float& sr6, float& dx, float& dy,
-                                                 float& dz) {
-  const int ix = (int)(sj.x - si.x), iy = (int)(sj.y - si.y), iz = (int)(sj.z - si.z);
-  dx = (float)ix;
-  dy = (float)iy;
-  dz = (float)iz;
-  if (CUBIC) {
-    r2 = exact_r2u(ix, iy, iz);
-  } else {
-    dx = __fmul_rn(dx, a.fxp_unit[0]);
-    dy = __fmul_rn(dy, a.fxp_unit[1]);
-    dz = __fmul_rn(dz, a.fxp_unit[2]);
-    // explicit rounding: the main loop and the band fix-up must take the same FP32 decision
-    r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-  }
-  r2i = frcp_refined(r2);
-  const float sr2 = sig2 * r2i;
-  sr6 = sr2 * sr2 * sr2;
-  t = a.lj_c24_f * sr6 * (2.f * sr6 - 1.f);  // -fs r^2
-}
-
-template <int TPP, bool CUBIC>
-__global__ void __launch_bounds__(256, 4) k_vertex_iso_mixed(KArgs a) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt / TPP, l = gt % TPP;
-  const bool valid = i < a.n;
-  float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, e = 0.f, w = 0.f;
-  const float sig2 = CUBIC ? a.sig2_u : a.sig2_f;
-  const float thr = CUBIC ? a.rwca2_u : a.rwca2_f;
-  const float lo = CUBIC ? a.rwca2_lo_u : a.rwca2_lo_f, hi = CUBIC ? a.rwca2_hi_u : a.rwca2_hi_f;
-  const size_t n = (size_t)a.n;
-  const unsigned jmax = (unsigned)a.n - 1u;
-  const int4* nb4 = (const int4*)a.nbr + (valid ? i : 0);
-  int cnt = 0;
-  bool band = false;
-  uint4 si = make_uint4(0u, 0u, 0u, 0u);
-  if (valid) {
-    si = __ldg(a.fxp + i);
-    cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
-    const int ng = (cnt + 3) >> 2;
-    int4 cur = load_group(nb4, l, ng, n);
-    for (int g = l; g < ng; g += TPP) {
-      const int4 nxt = load_group(nb4, g + TPP, ng, n);
-      const int lim = cnt - 4 * g;  // entries of this group that are in the list (>= 1)
-      // an index can only be out of range in a list that was never built: clamp, never fault
-      const unsigned jj[4] = {min((unsigned)cur.x, jmax), min((unsigned)cur.y, jmax), min((unsigned)cur.z, jmax),
-                              min((unsigned)cur.w, jmax)};
-      uint4 sj[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) sj[u] = __ldg(a.fxp + jj[u]);
-      float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        float r2, t, r2i, sr6, dx, dy, dz;
-        iso_pair_mixed_u<CUBIC>(a, si, sj[u], sig2, r2, t, r2i, sr6, dx, dy, dz);
-        const bool live = u < lim;
-        band |= live && r2 >= lo && r2 < hi;
-        const bool in = live && r2 < thr;
-        const float fs = in ? -t * r2i : 0.f;
-        gx += fs * dx;
-        gy += fs * dy;
-        gz += fs * dz;
-        e += in ? (a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f) : 0.f;
-        w += in ? t : 0.f;
-      }
-      kahan_add(fx, cx, gx);
-      kahan_add(fy, cy, gy);
-      kahan_add(fz, cz, gz);
-      cur = nxt;
-    }
-  }
-  if (band) {
-    // pairs near rc: take the side of the exact FP64 definition
-    for (int k = l; k < cnt; k += TPP) {
-      const unsigned j = min((unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n)), jmax);
-      float r2, t, r2i, sr6, dx, dy, dz;
-      iso_pair_mixed_u<CUBIC>(a, si, __ldg(a.fxp + j), sig2, r2, t, r2i, sr6, dx, dy, dz);
-      if (!(r2 >= lo && r2 < hi)) continue;
-      const bool fp32_in = r2 < thr;
-      const bool exact_in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
-      if (fp32_in == exact_in) continue;
-      const float sgn = exact_in ? 1.f : -1.f;
-      const float fs = -t * r2i * sgn;
-      kahan_add(fx, cx, fs * dx);
-      kahan_add(fy, cy, fs * dy);
-      kahan_add(fz, cz, fs * dz);
-      e += sgn * (a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f);
-      w += sgn * t;
-    }
-  }
-  // the sum is s - c; combine the threads of a particle
-  float lx = -cx, ly = -cy, lz = -cz;
-  if (TPP > 1) {
-#pragma unroll
-    for (int off = TPP / 2; off > 0; off >>= 1) {
-      float s2, l2;
-      s2 = __shfl_xor_sync(0xffffffffu, fx, off); l2 = __shfl_xor_sync(0xffffffffu, lx, off); comp_merge(fx, lx, s2, l2);
-      s2 = __shfl_xor_sync(0xffffffffu, fy, off); l2 = __shfl_xor_sync(0xffffffffu, ly, off); comp_merge(fy, ly, s2, l2);
-      s2 = __shfl_xor_sync(0xffffffffu, fz, off); l2 = __shfl_xor_sync(0xffffffffu, lz, off); comp_merge(fz, lz, s2, l2);
-      e += __shfl_xor_sync(0xffffffffu, e, off);
-      w += __shfl_xor_sync(0xffffffffu, w, off);
-    }
-  }
-  if (valid && l == 0) {
-    const float s = CUBIC ? a.inv_unit_f : 1.f;
-    ((float4*)a.force)[i] = make_float4(fx * s, fy * s, fz * s, 0.5f * e);
-    ((float4*)a.force_lo)[i] = make_float4(lx * s, ly * s, lz * s, 0.5f * w);
-  }
-}
-
-template <int TPP>
-__device__ __forceinline__ void group_reduce_d(double* v, int nv) {
-  if (TPP == 1) return;
-  for (int off = TPP / 2; off > 0; off >>= 1)
-    for (int c = 0; c < nv; c++) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
-}
-
-template <int TPP, bool PATCHY, int NP>
-__global__ void __launch_bounds__(256) k_vertex_fp64(KArgs a) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt / TPP, l = gt % TPP;
-  const bool valid = i < a.n;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // F(3), T(3), e, w
-  if (valid) {
-    const double4_32a pi = a.pos[i];
-    const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
-    const int ng = (cnt + 3) >> 2;
-    const int4* nb4 = (const int4*)a.nbr + i;
-    const size_t n = (size_t)a.n;
-    Patches<double, (PATCHY ? NP : 1)> Pi;
-    if (PATCHY) Pi = load_patches<(PATCHY ? NP : 1)>(a, i, 0.0);
-    int4 cur = load_group(nb4, l, ng, n);
-    for (int g = l; g < ng; g += TPP) {
-      const int4 nxt = load_group(nb4, g + TPP, ng, n);
-      int jj[4] = {cur.x, cur.y, cur.z, cur.w};
-#pragma unroll
-      for (int u = 0; u < 4; u++)
-        if (4 * g + u >= cnt || (unsigned)jj[u] >= (unsigned)a.n) jj[u] = -1;
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        if (jj[u] < 0) continue;
-        const Vec3<double> d = sep_fp64(pi, a.pos[jj[u]], a);
-        const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-        PairOut<double> o;
-        if (PATCHY) o = patchy_pair<(PATCHY ? NP : 1), false>(a, d, r2, Pi, i, jj[u]);
-        else o = iso_pair<double>(a, d, r2, i, jj[u]);
-        acc[0] += o.F.x; acc[1] += o.F.y; acc[2] += o.F.z;
-        acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z;
-        acc[6] += o.e; acc[7] += o.w;
-      }
-      cur = nxt;
-    }
-  }
-  group_reduce_d<TPP>(acc, 8);
-  if (valid && l == 0) {
-    ((double4_32a*)a.force)[i] = make_double4_32a(acc[0], acc[1], acc[2], 0.5 * acc[6]);
-    ((double4_32a*)a.force_lo)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.5 * acc[7]);
-    if (PATCHY) {
-      ((double4_32a*)a.torque)[i] = make_double4_32a(acc[3], acc[4], acc[5], 0.0);
-      ((double4_32a*)a.torque_lo)[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    }
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
-// Edge-based kernels
-// ------------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ float4 atom_add_v4(float4* addr, float4 v) {
-  float4 old;
-  asm volatile("atom.global.add.v4.f32 {%0,%1,%2,%3}, [%4], {%5,%6,%7,%8};"
-               : "=f"(old.x), "=f"(old.y), "=f"(old.z), "=f"(old.w)
-               : "l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-               : "memory");
-  return old;
-}
-
-__device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-               : "memory");
-}
-
-// hi += (v.xyz, v.w); the rounding errors of the three force components go to lo.xyz, and `extra`
-// is added to lo.w (the per-particle virial).
-__device__ __forceinline__ void comp_atomic(float4* hi, float4* lo, float4 v, float extra) {
-  const float4 old = atom_add_v4(hi, v);
-  float4 err;
-  err.x = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
-  err.y = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
-  err.z = two_sum_err(old.z, v.z, __fadd_rn(old.z, v.z));
-  err.w = extra;
-  if (err.x != 0.f || err.y != 0.f || err.z != 0.f || err.w != 0.f) red_add_v4(lo, err);
-}
-
-// Segmented suffix sum over lanes with equal key: after the call the first lane of each run holds
-// the run total.  `end` is the first lane of the next run (or 32).
-__device__ __forceinline__ float seg_sum(float v, int lane, int end) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    float o = __shfl_down_sync(0xffffffffu, v, d);
-    if (lane + d < end) v += o;
-  }
-  return v;
-}
-
-__device__ __forceinline__ double seg_sum(double v, int lane, int end) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    double o = __shfl_down_sync(0xffffffffu, v, d);
-    if (lane + d < end) v += o;
-  }
-  return v;
-}
-
-__device__ __forceinline__ void run_bounds(int key, int lane, bool& head, int& end) {
-  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-  head = (lane == 0) || (prev != key);
-  const unsigned heads = __ballot_sync(0xffffffffu, head);
-  const unsigned above = heads & ~((2u << lane) - 1u);
-  end = above ? (__ffs(above) - 1) : 32;
-}
-
-template <bool PATCHY, int NP>
-__global__ void __launch_bounds__(256) k_edge_mixed(KArgs a) {
-  const int64_t E = min(a.half_start[a.n], a.max_pairs);
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float4* fhi = (float4*)a.force;
-  float4* flo = (float4*)a.force_lo;
-  float4* thi = (float4*)a.torque;
-  float4* tlo = (float4*)a.torque_lo;
-  int2 pn = (warp * 32 + lane < E) ? __ldcs(a.pairs + warp * 32 + lane) : make_int2(-1, -1);
-  for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
-    int2 p = pn;  // this chunk's pair; the next chunk's is loaded before the arithmetic
-    const int64_t en = base + nwarps * 32 + lane;
-    pn = en < E ? __ldcs(a.pairs + en) : make_int2(-1, -1);
-    if ((unsigned)p.x >= (unsigned)a.n || (unsigned)p.y >= (unsigned)a.n) p = make_int2(-1, -1);
-    const bool ok = p.x >= 0;
-    PairOut<float> o;
-    o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
-    o.e = o.w = 0.f;
-    if (ok) {
-      const uint4 si = __ldg(a.fxp + p.x), sj = __ldg(a.fxp + p.y);
-      const Vec3<float> d = sep_mixed(si, sj, a);
-      const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-      if (PATCHY) {
-        if (r2 < a.rc2_f) {
-          const IPatches<(PATCHY ? NP : 1)> Pi = load_ipatches<(PATCHY ? NP : 1)>(a, p.x);
-          const int3 ds = make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z));
-          o = patchy_pair_mixed<(PATCHY ? NP : 1), true>(a, ds, d, r2, Pi, p.x, p.y);
-        }
-      } else if (a.cubic) {
-        o = iso_pair_cubic(a, make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z)), p.x, p.y);
-      } else {
-        o = iso_pair<float>(a, d, r2, p.x, p.y);
-      }
-    }
-    const float eh = 0.5f * o.e, wh = 0.5f * o.w;
-    const bool nz = o.F.x != 0.f || o.F.y != 0.f || o.F.z != 0.f || eh != 0.f || wh != 0.f ||
-                    (PATCHY && (o.ti.x != 0.f || o.ti.y != 0.f || o.ti.z != 0.f || o.tj.x != 0.f ||
-                                o.tj.y != 0.f || o.tj.z != 0.f));
-    // j side: one atomic per contributing pair
-    if (nz) {
-      comp_atomic(fhi + p.y, flo + p.y, make_float4(-o.F.x, -o.F.y, -o.F.z, eh), wh);
-      if (PATCHY) comp_atomic(thi + p.y, tlo + p.y, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f), 0.f);
-    }
-    // i side: one atomic per run of equal i within the warp
-    bool head;
-    int end;
-    run_bounds(p.x, lane, head, end);
-    const unsigned any_nz = __ballot_sync(0xffffffffu, nz);
-    if (any_nz) {
-      const float fx = seg_sum(o.F.x, lane, end), fy = seg_sum(o.F.y, lane, end), fz = seg_sum(o.F.z, lane, end);
-      const float es = seg_sum(eh, lane, end), ws = seg_sum(wh, lane, end);
-      float tx = 0.f, ty = 0.f, tz = 0.f;
-      if (PATCHY) { tx = seg_sum(o.ti.x, lane, end); ty = seg_sum(o.ti.y, lane, end); tz = seg_sum(o.ti.z, lane, end); }
-      // a run contributes iff one of its lanes does
-      const unsigned run_mask = (end == 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
-      if (head && p.x >= 0 && (any_nz & run_mask)) {
-        comp_atomic(fhi + p.x, flo + p.x, make_float4(fx, fy, fz, es), ws);
-        if (PATCHY) comp_atomic(thi + p.x, tlo + p.x, make_float4(tx, ty, tz, 0.f), 0.f);
-      }
-    }
-  }
-}
-
-template <bool PATCHY, int NP>
-__global__ void __launch_bounds__(256) k_edge_fp64(KArgs a) {
-  const int64_t E = min(a.half_start[a.n], a.max_pairs);
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double* f = (double*)a.force;
-  double* flo = (double*)a.force_lo;
-  double* t = (double*)a.torque;
-  int2 pn = (warp * 32 + lane < E) ? __ldcs(a.pairs + warp * 32 + lane) : make_int2(-1, -1);
-  for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
-    int2 p = pn;  // this chunk's pair; the next chunk's is loaded before the arithmetic
-    const int64_t en = base + nwarps * 32 + lane;
-    pn = en < E ? __ldcs(a.pairs + en) : make_int2(-1, -1);
-    if ((unsigned)p.x >= (unsigned)a.n || (unsigned)p.y >= (unsigned)a.n) p = make_int2(-1, -1);
-    const bool ok = p.x >= 0;
-    PairOut<double> o;
-    o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
-    o.e = o.w = 0.0;
-    if (ok) {
-      const Vec3<double> d = sep_fp64(a.pos[p.x], a.pos[p.y], a);
-      const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-      if (PATCHY) {
-        if (r2 < a.rc2_d) {
-          const Patches<double, (PATCHY ? NP : 1)> Pi = load_patches<(PATCHY ? NP : 1)>(a, p.x, 0.0);
-          o = patchy_pair<(PATCHY ? NP : 1), true>(a, d, r2, Pi, p.x, p.y);
-        }
-      } else {
-        o = iso_pair<double>(a, d, r2, p.x, p.y);
-      }
-    }
-    const double eh = 0.5 * o.e, wh = 0.5 * o.w;
-    const bool nz = o.F.x != 0.0 || o.F.y != 0.0 || o.F.z != 0.0 || eh != 0.0 || wh != 0.0 ||
-                    (PATCHY && (o.ti.x != 0.0 || o.ti.y != 0.0 || o.ti.z != 0.0 || o.tj.x != 0.0 ||
-                                o.tj.y != 0.0 || o.tj.z != 0.0));
-    if (nz) {
-      double* fj = f + 4 * (size_t)p.y;
-      atomicAdd(fj + 0, -o.F.x); atomicAdd(fj + 1, -o.F.y); atomicAdd(fj + 2, -o.F.z); atomicAdd(fj + 3, eh);
-      atomicAdd(flo + 4 * (size_t)p.y + 3, wh);
-      if (PATCHY) {
-        double* tj = t + 4 * (size_t)p.y;
-        atomicAdd(tj + 0, o.tj.x); atomicAdd(tj + 1, o.tj.y); atomicAdd(tj + 2, o.tj.z);
-      }
-    }
-    bool head;
-    int end;
-    run_bounds(p.x, lane, head, end);
-    const unsigned any_nz = __ballot_sync(0xffffffffu, nz);
-    if (any_nz) {
-      const double fx = seg_sum(o.F.x, lane, end), fy = seg_sum(o.F.y, lane, end), fz = seg_sum(o.F.z, lane, end);
-      const double es = seg_sum(eh, lane, end), ws = seg_sum(wh, lane, end);
-      double tx = 0.0, ty = 0.0, tz = 0.0;
-      if (PATCHY) { tx = seg_sum(o.ti.x, lane, end); ty = seg_sum(o.ti.y, lane, end); tz = seg_sum(o.ti.z, lane, end); }
-      const unsigned run_mask = (end == 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
-      if (head && p.x >= 0 && (any_nz & run_mask)) {
-        double* fi = f + 4 * (size_t)p.x;
-        atomicAdd(fi + 0, fx); atomicAdd(fi + 1, fy); atomicAdd(fi + 2, fz); atomicAdd(fi + 3, es);
-        atomicAdd(flo + 4 * (size_t)p.x + 3, ws);
-        if (PATCHY) {
-          double* ti = t + 4 * (size_t)p.x;
-          atomicAdd(ti + 0, tx); atomicAdd(ti + 1, ty); atomicAdd(ti + 2, tz);
-        }
-      }
-    }
-  }
-}
 
 // ------------------------------------------------------------------------------------------------
 // Launch
@@ -856,15 +85,32 @@ static void launch_edge(const KArgs& a, int block, cudaStream_t st) {
   else k_edge_fp64<PATCHY, NP><<<grid, block, 0, st>>>(a);
 }
 
+// Mixed edge path: FP32 atomic sums plus their compensation terms become the FP64 result.
+__global__ void k_edge_finalize(KArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const size_t n = (size_t)a.n;
+  const float4 hi = a.acc[i], lo = a.acc[n + i];
+  a.force[i] = make_double4_32a((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y,
+                                (double)hi.z + (double)lo.z, (double)hi.w);
+  a.virial[i] = (double)lo.w;
+  if (a.model == MD_PATCHY) {
+    const float4 th = a.acc[2 * n + i], tl = a.acc[3 * n + i];
+    a.torque[i] = make_double4_32a((double)th.x + (double)tl.x, (double)th.y + (double)tl.y,
+                                   (double)th.z + (double)tl.z, 0.0);
+  }
+}
+
 cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st) {
   if (block <= 0) block = (path == MD_VERTEX) ? 128 : 256;
   if (path == MD_EDGE) {
-    const size_t elem = a.precision == MD_MIXED ? sizeof(float4) : sizeof(double4_32a);
-    cudaMemsetAsync(a.force, 0, elem * (size_t)a.n, st);
-    cudaMemsetAsync(a.force_lo, 0, elem * (size_t)a.n, st);
-    if (a.model == MD_PATCHY) {
-      cudaMemsetAsync(a.torque, 0, elem * (size_t)a.n, st);
-      cudaMemsetAsync(a.torque_lo, 0, elem * (size_t)a.n, st);
+    const size_t n = (size_t)a.n;
+    if (a.precision == MD_MIXED) {
+      cudaMemsetAsync(a.acc, 0, sizeof(float4) * n * (a.model == MD_PATCHY ? 4 : 2), st);
+    } else {
+      cudaMemsetAsync(a.force, 0, sizeof(double4_32a) * n, st);
+      cudaMemsetAsync(a.virial, 0, sizeof(double) * n, st);
+      if (a.model == MD_PATCHY) cudaMemsetAsync(a.torque, 0, sizeof(double4_32a) * n, st);
     }
   }
   if (a.model != MD_PATCHY) {
@@ -878,6 +124,7 @@ cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st) 
       default: if (path == MD_VERTEX) launch_vertex<true, 4>(a, block, st); else launch_edge<true, 4>(a, block, st); break;
     }
   }
+  if (path == MD_EDGE && a.precision == MD_MIXED) k_edge_finalize<<<(a.n + 255) / 256, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

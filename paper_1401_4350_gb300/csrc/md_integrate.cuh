@@ -1,0 +1,252 @@
+// md_integrate.cuh -- bodies of the velocity-Verlet phases and of the per-step decision (see
+// md_integrate.cu), shared by the single-system kernels and the batched kernels.
+#pragma once
+
+#include "md_internal.cuh"
+
+namespace mdgb {
+
+constexpr int kIntBlock = 256;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// Quaternion product a (x) b, (w, x, y, z) stored as double4_32a (x=w, y=x, z=y, w=z).
+__device__ __forceinline__ double4_32a qmul(const double4_32a& a, const double4_32a& b) {
+  return make_double4_32a(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                      a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                      a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
+                      a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+
+// q <- exp(omega dt / 2) (x) q for the lab-frame angular velocity omega = L / I.
+__device__ __forceinline__ double4_32a rotate(const KArgs& a, const double4_32a& q, const double4_32a& L) {
+  if (a.precision == MD_MIXED) {
+    // The increment (dq - 1) (x) q of a rotation by |omega| dt << 1 is small: it is computed in FP32
+    // (cos(theta/2) - 1 = -2 sin^2(theta/4) keeps its relative precision) and added to the FP64
+    // quaternion, which is then renormalised with one Newton step (|q|^2 - 1 ~ 1e-13).
+    const float wx = (float)L.x * a.inv_inertia_f, wy = (float)L.y * a.inv_inertia_f,
+                wz = (float)L.z * a.inv_inertia_f;
+    const float wn = sqrtf(wx * wx + wy * wy + wz * wz);
+    if (!(wn > 0.f)) return q;
+    float s4, c4;
+    sincosf(0.25f * wn * a.dt_f, &s4, &c4);
+    const float cm1 = -2.f * s4 * s4;           // cos(theta/2) - 1
+    const float k = 2.f * s4 * c4 / wn;         // sin(theta/2) / |omega|
+    const float vx = wx * k, vy = wy * k, vz = wz * k;
+    const float qw = (float)q.x, qx = (float)q.y, qy = (float)q.z, qz = (float)q.w;
+    // (cm1, v) (x) (qw, qv) = (cm1 qw - v.qv, cm1 qv + qw v + v x qv)
+    const float dw = cm1 * qw - (vx * qx + vy * qy + vz * qz);
+    const float dx = cm1 * qx + qw * vx + (vy * qz - vz * qy);
+    const float dy = cm1 * qy + qw * vy + (vz * qx - vx * qz);
+    const float dz = cm1 * qz + qw * vz + (vx * qy - vy * qx);
+    double4_32a r = make_double4_32a(q.x + (double)dw, q.y + (double)dx, q.z + (double)dy, q.w + (double)dz);
+    const double n2 = r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+    const double f = 1.5 - 0.5 * n2;
+    return make_double4_32a(r.x * f, r.y * f, r.z * f, r.w * f);
+  }
+  const double wx = L.x * a.inv_inertia, wy = L.y * a.inv_inertia, wz = L.z * a.inv_inertia;
+  const double wn = sqrt(wx * wx + wy * wy + wz * wz);
+  double4_32a r = q;
+  if (wn > 0.0) {
+    const double half = 0.5 * wn * a.dt;
+    const double s = sin(half) / wn;
+    const double4_32a dq = make_double4_32a(cos(half), wx * s, wy * s, wz * s);
+    r = qmul(dq, q);
+  }
+  const double nq = sqrt(r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w);
+  return make_double4_32a(r.x / nq, r.y / nq, r.z / nq, r.w / nq);
+}
+
+__device__ __forceinline__ bool finite3(const double4_32a& p) { return isfinite(p.x) && isfinite(p.y) && isfinite(p.z); }
+
+// Whether this launch reduces energies: always for LAST and ENERGY, for MIDDLE when the step it
+// completes is a multiple of energy_every.  The step counter is read before k_step_decide advances it.
+__device__ __forceinline__ bool energy_step(const KArgs& a, int mode) {
+  if (mode == 2 || mode == 3) return true;
+  if (mode != 1) return false;
+  return ((a.status[MD_STATUS_STEPS] + 1) % a.energy_every) == 0;
+}
+
+// One particle's share of a velocity-Verlet phase (every thread of the block calls it: it ends with
+// block reductions); block_index selects the block's slot in block_partials.
+__device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, int block_index) {
+  const bool valid = i < a.n;
+  const bool drift = (mode == 0 || mode == 1);
+  const bool energies = energy_step(a, mode);
+  const bool patchy = a.model == MD_PATCHY;
+  const bool mixed = a.precision == MD_MIXED;
+  double kt = 0.0, kr = 0.0, u = 0.0, w = 0.0;  // per-particle energy terms (FP64 values)
+  float ktf = 0.f, krf = 0.f;                    // mixed: kinetic terms in FP32
+  float disp2 = 0.f;
+  if (valid) {
+    double4_32a v = a.vel[i];
+    const double4_32a F = a.force[i];
+    if (energies) {
+      u = F.w;
+      w = a.virial[i];
+    }
+    if (mode == 1) {
+      // closing half kick of the finished step (energies from v_n) and opening half kick of the next
+      if (mixed) {
+        if (energies) {
+          const float vx = (float)v.x + (float)F.x * a.half_dt_over_m_f, vy = (float)v.y + (float)F.y * a.half_dt_over_m_f,
+                      vz = (float)v.z + (float)F.z * a.half_dt_over_m_f;
+          ktf = a.half_mass_f * (vx * vx + vy * vy + vz * vz);
+        }
+        v.x = fma(F.x, a.dt_over_m, v.x);
+        v.y = fma(F.y, a.dt_over_m, v.y);
+        v.z = fma(F.z, a.dt_over_m, v.z);
+      } else {
+        v.x = fma(F.x, a.half_dt_over_m, v.x);
+        v.y = fma(F.y, a.half_dt_over_m, v.y);
+        v.z = fma(F.z, a.half_dt_over_m, v.z);
+        kt = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+        v.x = fma(F.x, a.half_dt_over_m, v.x);
+        v.y = fma(F.y, a.half_dt_over_m, v.y);
+        v.z = fma(F.z, a.half_dt_over_m, v.z);
+      }
+    } else if (mode == 0 || mode == 2) {
+      v.x = fma(F.x, a.half_dt_over_m, v.x);
+      v.y = fma(F.y, a.half_dt_over_m, v.y);
+      v.z = fma(F.z, a.half_dt_over_m, v.z);
+    }
+    if (mode == 2 || mode == 3) {
+      if (mixed) {
+        const float vx = (float)v.x, vy = (float)v.y, vz = (float)v.z;
+        ktf = a.half_mass_f * (vx * vx + vy * vy + vz * vz);
+      } else {
+        kt = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+      }
+    }
+    if (mode != 3) a.vel[i] = v;
+    if (patchy) {
+      double4_32a L = a.angmom[i];
+      const double4_32a T = a.torque[i];
+      const double hdt = 0.5 * a.dt;
+      if (mode == 1) {
+        L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
+        if (mixed) {
+          const float lx = (float)L.x, ly = (float)L.y, lz = (float)L.z;
+          krf = 0.5f * a.inv_inertia_f * (lx * lx + ly * ly + lz * lz);
+        } else {
+          kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
+        }
+        L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
+      } else if (mode == 0 || mode == 2) {
+        L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
+      }
+      if (mode == 2 || mode == 3) {
+        if (mixed) {
+          const float lx = (float)L.x, ly = (float)L.y, lz = (float)L.z;
+          krf = 0.5f * a.inv_inertia_f * (lx * lx + ly * ly + lz * lz);
+        } else {
+          kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
+        }
+      }
+      if (mode != 3) a.angmom[i] = L;
+      if (drift) {
+        const double4_32a q = rotate(a, a.quat[i], L);
+        a.quat[i] = q;
+        write_patch_lab(a, i, q);
+      }
+    }
+    if (drift) {
+      double4_32a x = a.pos[i];
+      x.x = fma(v.x, a.dt, x.x);
+      x.y = fma(v.y, a.dt, x.y);
+      x.z = fma(v.z, a.dt, x.z);
+      a.pos[i] = x;
+      if (!finite3(x)) record_error(a.status, MD_ERR_NONFINITE);
+      const uint4 f = fixed3(x, a);
+      a.fxp[i] = f;
+      const uint4 b = a.fxp_build[i];
+      const float dx = (float)(int)(f.x - b.x) * a.fxp_unit[0];
+      const float dy = (float)(int)(f.y - b.y) * a.fxp_unit[1];
+      const float dz = (float)(int)(f.z - b.z) * a.fxp_unit[2];
+      disp2 = dx * dx + dy * dy + dz * dz;
+      if (!(disp2 == disp2)) disp2 = 3.0e38f;  // NaN: force a rebuild (and the error is recorded)
+    }
+  }
+  // ---- per-block reductions; the totals are formed by k_step_decide ----
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (drift) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
+    if (lane == 0 && m) atomicMax(a.scr_words + SCR_DISPMAX, m);
+  }
+  if (energies) {
+    __shared__ double sred[kIntBlock / 32][4];
+    double s0, s1, s2, s3;
+    if (mixed) {
+      // kinetic terms in FP32 within the warp; energies and virial arrive as FP64 values
+      s0 = (double)warp_sum(ktf);
+      s1 = (double)warp_sum(krf);
+      s2 = warp_sum(u);
+      s3 = warp_sum(w);
+    } else {
+      s0 = warp_sum(kt); s1 = warp_sum(kr); s2 = warp_sum(u); s3 = warp_sum(w);
+    }
+    if (lane == 0) { sred[wid][0] = s0; sred[wid][1] = s1; sred[wid][2] = s2; sred[wid][3] = s3; }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sred[k][threadIdx.x];
+      a.block_partials[(size_t)block_index * 4 + threadIdx.x] = t;
+    }
+  }
+}
+
+// After k_integrate: totals of the block partials in a fixed order (FP64), the trace row, the step
+// counter, and the rebuild decision (largest displacement since the build against (skin/2)^2), which
+// sets the gate word for the gated rebuild kernels and, inside a graph, the IF node's condition.
+__device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int nblocks, int use_cond,
+                                                 unsigned long long cond_handle) {
+  const bool drift = (mode == 0 || mode == 1);
+  const bool energies = energy_step(a, mode);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (energies) {
+    __shared__ double tot[8][4];
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+      for (int c = 0; c < 4; c++) t[c] += a.block_partials[(size_t)b * 4 + c];
+    for (int c = 0; c < 4; c++) t[c] = warp_sum(t[c]);
+    if (lane == 0) for (int c = 0; c < 4; c++) tot[wid][c] = t[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double K = 0.0, KR = 0.0, U = 0.0, W = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) { K += tot[k][0]; KR += tot[k][1]; U += tot[k][2]; W += tot[k][3]; }
+      a.energy[MD_ENERGY_U] = U;
+      a.energy[MD_ENERGY_KT] = K;
+      a.energy[MD_ENERGY_KR] = KR;
+      a.energy[MD_ENERGY_W] = W;
+      int step = a.status[MD_STATUS_STEPS];
+      if (mode == 1 || mode == 2) step += 1;
+      if (a.trace_capacity > 0) {
+        double* row = a.trace + (size_t)(step % a.trace_capacity) * 4;
+        row[0] = (double)step; row[1] = K + KR; row[2] = U; row[3] = W;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (mode == 1 || mode == 2) a.status[MD_STATUS_STEPS] += 1;
+    if (drift) {
+      const unsigned m = a.scr_words[SCR_DISPMAX];
+      a.scr_words[SCR_DISPMAX] = 0u;
+      const unsigned g = __uint_as_float(m) > a.disp_thr2 ? 1u : 0u;
+      a.scr_words[SCR_GATE] = g;
+      a.status[MD_STATUS_REBUILDS] += (int)g;
+      if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, g);
+    }
+  }
+}
+
+}  // namespace mdgb

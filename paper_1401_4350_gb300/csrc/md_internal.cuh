@@ -42,6 +42,7 @@ struct KArgs {
   int32_t n_patch;
   int32_t tpp;
   int32_t trace_capacity;
+  int32_t energy_every;
   int32_t ncell[3];
   int32_t ncell_total;
   double box[3];
@@ -94,10 +95,10 @@ struct KArgs {
   int32_t* nbr_count;
   int64_t* half_start;
   int2* pairs;
-  void* force;
-  void* force_lo;
-  void* torque;
-  void* torque_lo;
+  double4_32a* force;   // (F, E_i) result, FP64
+  double* virial;        // W_i result
+  double4_32a* torque;   // (tau, 0) result, patchy
+  float4* acc;           // mixed edge accumulators: F hi [n], F lo [n], tau hi [n], tau lo [n]
   double* trace;
   uint32_t* scr_words;   // SCR_WORDS control words
   double* block_partials;  // [max_blocks][8] FP64 partial sums of the integrate kernels

@@ -25,7 +25,7 @@ def default_capacities(system: System, slack: float = 1.6):
 
 
 def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, tpp: int = 1, block: int = 0,
-                trace_capacity: int = 0) -> B.md_params:
+                trace_capacity: int = 0, energy_every: int = 1) -> B.md_params:
     mn, mp = default_capacities(system)
     p = B.md_params()
     p.n = system.n
@@ -37,6 +37,7 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
     p.threads_per_particle = tpp
     p.block_size = block
     p.trace_capacity = trace_capacity
+    p.energy_every = energy_every
     for c in range(3):
         p.box[c] = float(system.box[c])
     p.rc, p.skin, p.dt, p.mass, p.inertia = system.rc, system.skin, system.dt, system.mass, system.inertia
@@ -49,9 +50,9 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
 
 class Simulation:
     def __init__(self, system: System, precision: int = B.MD_MIXED, max_neigh=None, max_pairs=None, tpp: int = 1,
-                 block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None):
+                 block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None, energy_every: int = 1):
         self.system = system
-        self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity)
+        self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity, energy_every)
         rc = B.md_check_params(self.params)
         if rc != B.MD_OK:
             raise B.MDError(rc, B.last_error())

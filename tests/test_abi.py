@@ -46,6 +46,8 @@ def _lj_params(n=4000, precision=B.MD_MIXED):
     ("block_size", 512, "block_size"),
     ("skin", 0.0, "skin"),
     ("dt", -1.0, "dt"),
+    ("energy_every", -2, "energy_every"),
+    ("reserved", 1, "reserved"),
 ])
 def test_invalid_params_rejected(lib, field, value, needle):
     p = _lj_params()
@@ -84,14 +86,14 @@ def test_workspace_layout(lib, precision, kind):
     L = B.md_workspace_layout(p)
     assert L.total == B.md_workspace_bytes(p) > 0
     offs = [getattr(L, f) for f in ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr",
-                                    "nbr_count", "half_start", "pairs", "force", "force_lo", "torque",
-                                    "torque_lo", "trace", "scratch")]
+                                    "nbr_count", "half_start", "pairs", "force", "virial", "torque",
+                                    "acc", "trace", "scratch")]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and len(set(offs)) == len(offs)
-    assert L.force_elem == (4 if precision == B.MD_MIXED else 8)
+    assert L.force_elem == 8
     n = s.n
     assert L.nbr_count - L.nbr >= 4 * n * p.max_neigh
-    assert L.force_lo - L.force >= L.force_elem * 4 * n
+    assert L.virial - L.force >= 32 * n
     # cells of edge >= rv; an axis with fewer than three such cells is a single cell
     for c in range(3):
         k = L.ncell[c]

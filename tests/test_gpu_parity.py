@@ -374,3 +374,20 @@ def test_pairs_at_the_cutoff_follow_the_exact_decision(precision, path, box_shap
     fmag = 0.039
     tol = (1e-12 if precision == B.MD_FP64 else 1e-5) * fmag
     assert np.abs(F - Fr).max() <= tol, np.abs(F - Fr).max()
+
+
+def test_energy_every_keeps_dynamics_and_reports_the_same_energies():
+    s = get_sys("lj4000")
+    out = []
+    for every in (1, 5):
+        sim = Sim(s, B.MD_MIXED, trace_capacity=32, energy_every=every)
+        sim.prepare(B.MD_VERTEX)
+        sim.step(20, B.MD_VERTEX, True)
+        assert sim.status()[B.MD_STATUS_STEPS] == 20
+        out.append((sim.positions()[0], sim.trace()))
+    assert np.array_equal(out[0][0], out[1][0])  # energies do not feed back into the dynamics
+    t1, t5 = out[0][1], out[1][1]
+    for step in (5, 10, 15, 20):
+        assert t5[step, 0] == step
+        np.testing.assert_array_equal(t5[step], t1[step])
+    assert t5[7, 0] == 0.0  # not an energy step: the row was never written
