@@ -266,9 +266,79 @@ def run_ours(args, rank, world, dist):
         "clocks": clocks,
         "graph": not args.direct,
     }
+    if not args.no_batch:
+        line["batch"] = run_batch()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system)
     return line
+
+
+def run_batch(steps: int = 50, fp64_steps: int = 5):
+    """512 replicas (N log-uniform in [500, 32768], rho ~ U(0.2, 0.9), every fourth WCA at rho 0.2, the
+    rest LJ rc 2.5): mixed-precision batched path, autotuned, against looping the plain FP64
+    single-system path over the same replicas.  Also the batch's max force error against FP64."""
+    import numpy as np
+    import torch
+    from paper_1401_4350_gb300 import binding as B
+    from paper_1401_4350_gb300 import systems
+    from paper_1401_4350_gb300.sim import BatchSimulation, Simulation
+
+    reps = [systems.make_replica(*spec) for spec in systems.batch_specs(512)]
+    n_total = sum(s.n for s in reps)
+    bs = BatchSimulation(reps)
+    t0 = time.perf_counter()
+    paths, tpps = bs.autotune()
+    tune_s = time.perf_counter() - t0
+    # accuracy at the prepared state: mixed batch forces vs FP64 single-system forces, every replica
+    worst = 0.0
+    for r, s in enumerate(reps):
+        F, _, _ = bs.replica_forces(r)
+        ref = Simulation(s, B.MD_FP64)
+        ref.prepare(B.MD_VERTEX)
+        Fr, _, _, _ = ref.forces()
+        del ref
+        frms = np.sqrt((Fr ** 2).sum(1).mean())
+        worst = max(worst, float(np.abs(F - Fr).max() / frms))
+    torch.cuda.empty_cache()
+    bs.step(3)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    bs.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    assert all(bs.replica_status(r)[B.MD_STATUS_CODE] == 0 for r in range(len(reps)))
+    bs.release()
+    del bs
+    torch.cuda.empty_cache()
+    # the plain FP64 per-system path, looped over the replicas
+    loop_ms = 0.0
+    for s in reps:
+        sim = Simulation(s, B.MD_FP64)
+        sim.prepare(B.MD_VERTEX)
+        sim.step(1, B.MD_VERTEX)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        sim.step(fp64_steps, B.MD_VERTEX)
+        c.record(st)
+        torch.cuda.synchronize()
+        loop_ms += a.elapsed_time(c)
+        del sim
+    torch.cuda.empty_cache()
+    batch_rs = len(reps) * steps / (batch_ms * 1e-3)
+    loop_rs = len(reps) * fp64_steps / (loop_ms * 1e-3)
+    return {"workload": "512 replicas, N log-uniform [500, 32768], rho U(0.2, 0.9), 1/4 WCA rho 0.2, 3/4 LJ rc 2.5",
+            "particles": n_total, "steps": steps, "ms_per_step": batch_ms / steps,
+            "replica_steps_per_s": batch_rs, "particle_steps_per_s": n_total * steps / (batch_ms * 1e-3),
+            "fp64_loop_replica_steps_per_s": loop_rs, "speedup_vs_fp64_loop": batch_rs / loop_rs,
+            "max_force_error_vs_fp64_frms": worst, "autotune_s": tune_s,
+            "chosen": {"edge": int(sum(1 for p in paths if p == B.MD_EDGE)),
+                       "vertex_tpp1": int(sum(1 for p, t in zip(paths, tpps) if p == B.MD_VERTEX and t == 1)),
+                       "vertex_tpp2": int(sum(1 for p, t in zip(paths, tpps) if p == B.MD_VERTEX and t == 2)),
+                       "vertex_tpp4": int(sum(1 for p, t in zip(paths, tpps) if p == B.MD_VERTEX and t == 4))}}
 
 
 def cpu_baseline(system, max_seconds=25.0):
@@ -321,6 +391,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica measurement")
     ap.add_argument("--direct", action="store_true",
                     help="launch the kernels directly instead of replaying the step graph (for profilers that "
                          "do not replay kernels inside graphs with conditional nodes)")

@@ -257,6 +257,54 @@ int md_read_status(const md_params* p, const void* ws, int32_t* host_out, void* 
 int md_release_graphs(const void* ws);
 
 /*
+ * ---- Batched replicas ---------------------------------------------------------------------------
+ * Many independent systems of uneven size stepped together on one GPU.  Every replica is an
+ * ordinary system (md_params, mixed-precision LJ or WCA) with its own sub-workspace inside one batch
+ * workspace, laid out exactly as md_workspace_layout describes for that replica, at byte offset
+ * md_batch_replica_offset(); the single-system entry points therefore work on a replica's
+ * sub-workspace too (e.g. md_get_forces, md_read_status).  The state arrays of all replicas are
+ * concatenated in replica order (pos, vel [N_total][4], id [N_total]).
+ *
+ * One batched step is: one integration launch over all replicas, one decision launch (per-replica
+ * energies, trace and skin criterion), the cell + Verlet rebuild of only the replicas that need it
+ * (a CUDA-graph IF node when use_graph is set), and ONE persistent force launch in which blocks take
+ * (replica, tile) work items from a device counter; each replica is evaluated with its own
+ * decomposition: vertex with threads_per_particle in {1, 2, 4, 8}, or edge.  The decomposition per
+ * replica is set by md_batch_init / md_batch_set_config or chosen by md_autotune (Sec. Conclusions:
+ * vertex for many simple interactions, edge for few or complicated ones, decided here by
+ * measurement).  A replica stepped in a batch computes what md_step_verlet computes for it alone.
+ * The library keeps a host-side record of each batch keyed by the workspace pointer.
+ */
+size_t md_batch_workspace_bytes(const md_params* reps, int32_t nrep);
+size_t md_batch_replica_offset(const md_params* reps, int32_t nrep, int32_t r); /* (size_t)-1 if invalid */
+/* Records the batch, uploads its tables and clears every replica's status words.  path[r] is
+ * MD_VERTEX or MD_EDGE (NULL: all MD_VERTEX); threads per particle from reps[r]. */
+int md_batch_init(const md_params* reps, int32_t nrep, const md_state* s, void* ws, const int32_t* path,
+                  void* stream);
+/* Cells, lists (half lists for edge replicas), forces and step-0 energies of every replica. */
+int md_batch_prepare(void* ws, void* stream);
+/* One batched force evaluation with the current lists. */
+int md_batch_forces(void* ws, void* stream);
+/* nsteps velocity-Verlet steps of every replica (precondition: md_batch_prepare). */
+int md_batch_step(void* ws, int32_t nsteps, int32_t use_graph, void* stream);
+/* Sets path[r] / tpp[r] (either may be NULL); synchronises the stream.  A replica that becomes edge
+ * needs its half list: call md_batch_prepare before the next step. */
+int md_batch_set_config(void* ws, const int32_t* path, const int32_t* tpp, void* stream);
+int md_batch_get_config(const void* ws, int32_t* path, int32_t* tpp);
+/* Forgets the batch recorded for ws (NULL: every batch) and its graphs. */
+int md_batch_release(const void* ws);
+
+/*
+ * md_autotune -- chooses each replica's decomposition by measurement.  Replicas are grouped by
+ * model, mean neighbours per particle (from the lists, octave buckets) and size (octave buckets);
+ * for every group each candidate (vertex with 1, 2 or 4 threads per particle, edge) is timed in the
+ * batched force kernel on that group alone, and the fastest is kept (and remembered for later calls
+ * with the same group key).  Leaves the batch prepared with the chosen configuration and returns it
+ * in path_out / tpp_out (either may be NULL).  Synchronises the stream.
+ */
+int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream);
+
+/*
  * ---- The cell build for callers that cannot allocate device memory ---------------------------
  * The paper has no counterpart to this entry point; it exists for callers that may not allocate
  * GPU memory themselves (code running inside another framework's memory pool, plug-ins that only

@@ -96,6 +96,16 @@ def load(path: str = LIB_PATH):
         "md_read_status": ([_P, _V, ctypes.POINTER(ctypes.c_int32), _V], ctypes.c_int),
         "md_release_graphs": ([_V], ctypes.c_int),
         "md_build_cells_static": ([_P, _S, _V, _V, _V, _V], ctypes.c_int),
+        "md_batch_workspace_bytes": ([_P, ctypes.c_int32], ctypes.c_size_t),
+        "md_batch_replica_offset": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_size_t),
+        "md_batch_init": ([_P, ctypes.c_int32, _S, _V, _V, _V], ctypes.c_int),
+        "md_batch_prepare": ([_V, _V], ctypes.c_int),
+        "md_batch_forces": ([_V, _V], ctypes.c_int),
+        "md_batch_step": ([_V, ctypes.c_int32, ctypes.c_int32, _V], ctypes.c_int),
+        "md_batch_set_config": ([_V, _V, _V, _V], ctypes.c_int),
+        "md_batch_get_config": ([_V, _V, _V], ctypes.c_int),
+        "md_batch_release": ([_V], ctypes.c_int),
+        "md_autotune": ([_V, _V, _V, _V], ctypes.c_int),
         "md_static_scratch_bytes": ([], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -204,3 +214,66 @@ def md_build_cells_static(p, s, cell_start, fxp, patch_lab=None, stream=None):
 
 def md_static_scratch_bytes() -> int:
     return load().md_static_scratch_bytes()
+
+
+# ---- batched replicas ---------------------------------------------------------------------------
+
+def _params_array(reps):
+    arr = (md_params * len(reps))()
+    for k, p in enumerate(reps):
+        arr[k] = p
+    return arr
+
+
+def md_batch_workspace_bytes(reps) -> int:
+    return load().md_batch_workspace_bytes(_params_array(reps), len(reps))
+
+
+def md_batch_replica_offset(reps, r) -> int:
+    return load().md_batch_replica_offset(_params_array(reps), len(reps), r)
+
+
+def _i32_array(vals):
+    if vals is None:
+        return None
+    arr = (ctypes.c_int32 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def md_batch_init(reps, s, ws, path=None, stream=None):
+    return _check(load().md_batch_init(_params_array(reps), len(reps), ctypes.byref(s), _ptr(ws),
+                                       _i32_array(path), _stream(stream)))
+
+
+def md_batch_prepare(ws, stream=None):
+    return _check(load().md_batch_prepare(_ptr(ws), _stream(stream)))
+
+
+def md_batch_forces(ws, stream=None):
+    return _check(load().md_batch_forces(_ptr(ws), _stream(stream)))
+
+
+def md_batch_step(ws, nsteps, use_graph=True, stream=None):
+    return _check(load().md_batch_step(_ptr(ws), int(nsteps), int(bool(use_graph)), _stream(stream)))
+
+
+def md_batch_set_config(ws, path=None, tpp=None, stream=None):
+    return _check(load().md_batch_set_config(_ptr(ws), _i32_array(path), _i32_array(tpp), _stream(stream)))
+
+
+def md_batch_get_config(ws, nrep):
+    path = (ctypes.c_int32 * nrep)()
+    tpp = (ctypes.c_int32 * nrep)()
+    _check(load().md_batch_get_config(_ptr(ws), path, tpp))
+    return list(path), list(tpp)
+
+
+def md_batch_release(ws=None):
+    return load().md_batch_release(_ptr(ws) if ws is not None else None)
+
+
+def md_autotune(ws, nrep, stream=None):
+    path = (ctypes.c_int32 * nrep)()
+    tpp = (ctypes.c_int32 * nrep)()
+    _check(load().md_autotune(_ptr(ws), path, tpp, _stream(stream)))
+    return list(path), list(tpp)

@@ -22,7 +22,7 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
-static int cuda_fail(cudaError_t e, const char* what) {
+int cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
   return MD_ERR_CUDA;
 }
@@ -284,6 +284,20 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
 
 int check_params_only(const md_params* p) { return check(p); }
 
+size_t replica_workspace_bytes(const md_params* p) {
+  Layout L;
+  make_layout(p, &L);
+  return L.pub.total;
+}
+
+KArgs replica_kernel_args(const md_params* p, const md_state* s, void* ws) {
+  Layout L;
+  make_layout(p, &L);
+  return make_args(p, s, ws, L);
+}
+
+
+
 static int check_state(const md_params* p, const md_state* s, const void* ws) {
   if (!s || !s->pos || !s->vel || !s->id) { set_error("state arrays pos, vel and id are required"); return MD_ERR_INVALID; }
   if (p->model == MD_PATCHY && (!s->quat || !s->angmom)) { set_error("patchy model needs quat and angmom"); return MD_ERR_INVALID; }
@@ -292,6 +306,8 @@ static int check_state(const md_params* p, const md_state* s, const void* ws) {
   if (((uintptr_t)s->pos | (uintptr_t)s->vel) & 31) { set_error("pos and vel must be 32-byte aligned"); return MD_ERR_INVALID; }
   return MD_OK;
 }
+
+int check_replica_state(const md_params* p, const md_state* s, const void* ws) { return check_state(p, s, ws); }
 
 // ------------------------------------------------------------------------------------------------
 // Graph cache for md_step_verlet

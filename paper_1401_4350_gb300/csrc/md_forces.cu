@@ -85,20 +85,9 @@ static void launch_edge(const KArgs& a, int block, cudaStream_t st) {
   else k_edge_fp64<PATCHY, NP><<<grid, block, 0, st>>>(a);
 }
 
-// Mixed edge path: FP32 atomic sums plus their compensation terms become the FP64 result.
 __global__ void k_edge_finalize(KArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const size_t n = (size_t)a.n;
-  const float4 hi = a.acc[i], lo = a.acc[n + i];
-  a.force[i] = make_double4_32a((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y,
-                                (double)hi.z + (double)lo.z, (double)hi.w);
-  a.virial[i] = (double)lo.w;
-  if (a.model == MD_PATCHY) {
-    const float4 th = a.acc[2 * n + i], tl = a.acc[3 * n + i];
-    a.torque[i] = make_double4_32a((double)th.x + (double)tl.x, (double)th.y + (double)tl.y,
-                                   (double)th.z + (double)tl.z, 0.0);
-  }
+  if (i < a.n) edge_finalize_one(a, i);
 }
 
 cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st) {

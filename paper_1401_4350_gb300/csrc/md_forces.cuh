@@ -801,4 +801,18 @@ __global__ void __launch_bounds__(256) k_edge_fp64(KArgs a) {
                             ((int64_t)gridDim.x * blockDim.x) >> 5, E);
 }
 
+// Mixed edge path: FP32 atomic sums plus their compensation terms become the FP64 result.
+__device__ __forceinline__ void edge_finalize_one(const KArgs& a, int i) {
+  const size_t n = (size_t)a.n;
+  const float4 hi = a.acc[i], lo = a.acc[n + i];
+  a.force[i] = make_double4_32a((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y,
+                                (double)hi.z + (double)lo.z, (double)hi.w);
+  a.virial[i] = (double)lo.w;
+  if (a.model == MD_PATCHY) {
+    const float4 th = a.acc[2 * n + i], tl = a.acc[3 * n + i];
+    a.torque[i] = make_double4_32a((double)th.x + (double)tl.x, (double)th.y + (double)tl.y,
+                                   (double)th.z + (double)tl.z, 0.0);
+  }
+}
+
 }  // namespace mdgb

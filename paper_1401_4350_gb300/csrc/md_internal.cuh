@@ -116,6 +116,10 @@ struct KArgs {
 void set_error(const char* fmt, ...);
 int check_params_only(const md_params* p);
 KArgs kernel_args_without_workspace(const md_params* p, const md_state* s);
+size_t replica_workspace_bytes(const md_params* p);
+KArgs replica_kernel_args(const md_params* p, const md_state* s, void* ws);
+int check_replica_state(const md_params* p, const md_state* s, const void* ws);
+int cuda_fail(cudaError_t e, const char* what);
 
 // Launch wrappers (return cudaGetLastError() after the launch).
 cudaError_t launch_build_cells(const KArgs& a, const uint32_t* gate, cudaStream_t st);

@@ -186,3 +186,104 @@ class Simulation:
         key = torch.sort(a * n + b).values
         ordered = bool((pairs[:, 0] < pairs[:, 1]).all()) and bool((pairs[1:, 0] >= pairs[:-1, 0]).all())
         return torch.stack([key // n, key % n], 1).cpu().numpy(), ordered
+
+
+class BatchSimulation:
+    """Many independent mixed-precision LJ/WCA systems stepped together (md_batch_*).
+
+    The state arrays of all replicas are concatenated in replica order; replica r's sub-workspace is
+    an ordinary single-system workspace at byte offset md_batch_replica_offset(r), so the
+    single-system entry points (md_get_forces, md_read_status) work on it directly.
+    """
+
+    def __init__(self, system_list, paths=None, tpps=None, trace_capacity: int = 0, energy_every: int = 1,
+                 device: str = "cuda", stream=None):
+        self.systems = list(system_list)
+        tpps = tpps or [1] * len(self.systems)
+        self.params = [make_params(s, B.MD_MIXED, tpp=int(t), trace_capacity=trace_capacity,
+                                   energy_every=energy_every) for s, t in zip(self.systems, tpps)]
+        self.nrep = len(self.systems)
+        self.counts = [s.n for s in self.systems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.counts)]).astype(np.int64)
+        self.device = torch.device(device)
+        self.stream = stream
+        total = int(self.offsets[-1])
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.pos = torch.zeros((total, 4), **f64)
+        self.vel = torch.zeros((total, 4), **f64)
+        self.id = torch.zeros(total, dtype=torch.int32, device=self.device)
+        for r, s in enumerate(self.systems):
+            a, b = int(self.offsets[r]), int(self.offsets[r + 1])
+            self.pos[a:b, :3] = torch.as_tensor(s.pos, device=self.device)
+            self.vel[a:b, :3] = torch.as_tensor(s.vel, device=self.device)
+            self.id[a:b] = torch.arange(s.n, dtype=torch.int32, device=self.device)
+        nbytes = B.md_batch_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise B.MDError(B.MD_ERR_INVALID, B.last_error())
+        self.ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        self.ws_offsets = [B.md_batch_replica_offset(self.params, r) for r in range(self.nrep)]
+        self.layouts = [B.md_workspace_layout(p) for p in self.params]
+        st = B.md_state()
+        st.pos, st.vel, st.id = self.pos.data_ptr(), self.vel.data_ptr(), self.id.data_ptr()
+        st.quat = st.angmom = None
+        self._state = st
+        B.md_batch_init(self.params, st, self.ws, paths, stream)
+
+    def release(self):
+        B.md_batch_release(self.ws)
+
+    # -- the C ABI --------------------------------------------------------------------------------
+    def prepare(self):
+        B.md_batch_prepare(self.ws, self.stream)
+
+    def forces_eval(self):
+        B.md_batch_forces(self.ws, self.stream)
+
+    def step(self, nsteps: int, use_graph: bool = True):
+        B.md_batch_step(self.ws, nsteps, use_graph, self.stream)
+
+    def set_config(self, paths=None, tpps=None):
+        B.md_batch_set_config(self.ws, paths, tpps, self.stream)
+
+    def config(self):
+        return B.md_batch_get_config(self.ws, self.nrep)
+
+    def autotune(self):
+        return B.md_autotune(self.ws, self.nrep, self.stream)
+
+    # -- per-replica results in the original order ------------------------------------------------
+    def _ws(self, r):
+        return self.ws[self.ws_offsets[r]:]
+
+    def _inv(self, r):
+        a, b = int(self.offsets[r]), int(self.offsets[r + 1])
+        ids = self.id[a:b].long()
+        inv = torch.empty_like(ids)
+        inv[ids] = torch.arange(b - a, device=self.device)
+        return inv
+
+    def replica_forces(self, r):
+        n = self.counts[r]
+        fo = torch.empty((n, 4), dtype=torch.float64, device=self.device)
+        to = torch.empty((n, 4), dtype=torch.float64, device=self.device)
+        B.md_get_forces(self.params[r], self._ws(r), fo, to, self.stream)
+        torch.cuda.synchronize(self.device)
+        inv = self._inv(r)
+        fo, to = fo[inv].cpu().numpy(), to[inv].cpu().numpy()
+        return fo[:, :3], fo[:, 3], to[:, 3]
+
+    def replica_positions(self, r):
+        a = int(self.offsets[r])
+        inv = self._inv(r)
+        return self.pos[a:a + self.counts[r]][inv, :3].cpu().numpy(), self.vel[a:a + self.counts[r]][inv, :3].cpu().numpy()
+
+    def replica_status(self, r):
+        return B.md_read_status(self.params[r], self._ws(r), self.stream)
+
+    def replica_energies(self, r):
+        L = self.layouts[r]
+        off = self.ws_offsets[r] + L.energy
+        e = self.ws[off:off + 8 * B.MD_ENERGY_WORDS].view(torch.float64)
+        torch.cuda.synchronize(self.device)
+        e = e.cpu().numpy()
+        return {"U": e[B.MD_ENERGY_U], "KT": e[B.MD_ENERGY_KT], "W": e[B.MD_ENERGY_W]}
