@@ -500,23 +500,25 @@ __device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
     }
   }
   if (band) {
-    // pairs near rc: take the side of the exact FP64 definition
-    for (int k = l; k < cnt; k += TPP) {
-      const unsigned j = min((unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n)), jmax);
-      float r2, t, r2i, sr6, dx, dy, dz;
-      iso_pair_mixed_u<CUBIC>(a, si, __ldg(a.fxp + j), sig2, r2, t, r2i, sr6, dx, dy, dz);
-      if (!(r2 >= lo && r2 < hi)) continue;
-      const bool fp32_in = r2 < thr;
-      const bool exact_in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
-      if (fp32_in == exact_in) continue;
-      const float sgn = exact_in ? 1.f : -1.f;
-      const float fs = -t * r2i * sgn;
-      kahan_add(fx, cx, fs * dx);
-      kahan_add(fy, cy, fs * dy);
-      kahan_add(fz, cz, fs * dz);
-      e += sgn * (a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f);
-      w += sgn * t;
-    }
+    // pairs near rc: take the side of the exact FP64 definition; this lane's entries only (the groups
+    // g = l, l + TPP, ... of the main loop)
+    for (int k0 = 4 * l; k0 < cnt; k0 += 4 * TPP)
+      for (int k = k0; k < min(k0 + 4, cnt); k++) {
+        const unsigned j = min((unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n)), jmax);
+        float r2, t, r2i, sr6, dx, dy, dz;
+        iso_pair_mixed_u<CUBIC>(a, si, __ldg(a.fxp + j), sig2, r2, t, r2i, sr6, dx, dy, dz);
+        if (!(r2 >= lo && r2 < hi)) continue;
+        const bool fp32_in = r2 < thr;
+        const bool exact_in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
+        if (fp32_in == exact_in) continue;
+        const float sgn = exact_in ? 1.f : -1.f;
+        const float fs = -t * r2i * sgn;
+        kahan_add(fx, cx, fs * dx);
+        kahan_add(fy, cy, fs * dy);
+        kahan_add(fz, cz, fs * dz);
+        e += sgn * (a.lj_c4_f * sr6 * (sr6 - 1.f) - a.lj_shift_f);
+        w += sgn * t;
+      }
   }
   // the sum is s - c; combine the threads of a particle
   float lx = -cx, ly = -cy, lz = -cz;

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a, int mode) {
   integrate_body(a, mode, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256) k_step_decide(KArgs a, int mode, int nblocks, int use_cond,
+__global__ void __launch_bounds__(32) k_step_decide(KArgs a, int mode, int nblocks, int use_cond,
                                                      unsigned long long cond_handle) {
   step_decide_body(a, mode, nblocks, use_cond, cond_handle);
 }
@@ -29,7 +29,7 @@ int integrate_blocks(const KArgs& a) { return (a.n + kIntBlock - 1) / kIntBlock;
 cudaError_t launch_integrate(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle, cudaStream_t st) {
   const int nb = integrate_blocks(a);
   k_integrate<<<nb, kIntBlock, 0, st>>>(a, mode);
-  k_step_decide<<<1, 256, 0, st>>>(a, mode, nb, use_cond, cond_handle);
+  k_step_decide<<<1, 32, 0, st>>>(a, mode, nb, use_cond, cond_handle);
   return cudaGetLastError();
 }
 
@@ -57,6 +57,7 @@ __global__ void k_init_ws(KArgs a) {
   if (t < MD_STATUS_WORDS) a.status[t] = 0;
   if (t < MD_ENERGY_WORDS) a.energy[t] = 0.0;
   if (t < SCR_WORDS) a.scr_words[t] = 0u;
+  if (t < 4) ((unsigned long long*)a.block_partials)[t] = 0ULL;  // energy accumulators
   for (int k = t; k < a.trace_capacity * 4; k += gridDim.x * blockDim.x) a.trace[k] = 0.0;
   // empty lists until the first build: force kernels called early see no pairs
   for (int k = t; k < a.n; k += gridDim.x * blockDim.x) a.nbr_count[k] = 0;

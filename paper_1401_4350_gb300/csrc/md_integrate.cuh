@@ -69,6 +69,12 @@ __device__ __forceinline__ double4_32a rotate(const KArgs& a, const double4_32a&
 
 __device__ __forceinline__ bool finite3(const double4_32a& p) { return isfinite(p.x) && isfinite(p.y) && isfinite(p.z); }
 
+// The four energy accumulators (K_trans, K_rot, U, W) as 64-bit fixed-point words in 2^-32 units,
+// kept in the first 32 bytes of the block-partials scratch.
+__device__ __forceinline__ unsigned long long* energy_accumulators(const KArgs& a) {
+  return (unsigned long long*)a.block_partials;
+}
+
 // Whether this launch reduces energies: always for LAST and ENERGY, for MIDDLE when the step it
 // completes is a multiple of energy_every.  The step counter is read before k_step_decide advances it.
 __device__ __forceinline__ bool energy_step(const KArgs& a, int mode) {
@@ -200,7 +206,9 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
     if (threadIdx.x < 4) {
       double t = 0.0;
       for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sred[k][threadIdx.x];
-      a.block_partials[(size_t)block_index * 4 + threadIdx.x] = t;
+      // block sum -> 64-bit fixed point (2^-32 units): integer atomics make the total exact and
+      // independent of the order in which blocks finish
+      atomicAdd(energy_accumulators(a) + threadIdx.x, (unsigned long long)llrint(t * 4294967296.0));
     }
   }
 }
@@ -212,18 +220,16 @@ __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int n
                                                  unsigned long long cond_handle) {
   const bool drift = (mode == 0 || mode == 1);
   const bool energies = energy_step(a, mode);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  (void)nblocks;
   if (energies) {
-    __shared__ double tot[8][4];
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-      for (int c = 0; c < 4; c++) t[c] += a.block_partials[(size_t)b * 4 + c];
-    for (int c = 0; c < 4; c++) t[c] = warp_sum(t[c]);
-    if (lane == 0) for (int c = 0; c < 4; c++) tot[wid][c] = t[c];
-    __syncthreads();
     if (threadIdx.x == 0) {
-      double K = 0.0, KR = 0.0, U = 0.0, W = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++) { K += tot[k][0]; KR += tot[k][1]; U += tot[k][2]; W += tot[k][3]; }
+      unsigned long long* acc = energy_accumulators(a);
+      double v[4];
+      for (int c = 0; c < 4; c++) {
+        v[c] = (double)(long long)acc[c] * (1.0 / 4294967296.0);
+        acc[c] = 0ULL;
+      }
+      const double K = v[0], KR = v[1], U = v[2], W = v[3];
       a.energy[MD_ENERGY_U] = U;
       a.energy[MD_ENERGY_KT] = K;
       a.energy[MD_ENERGY_KR] = KR;

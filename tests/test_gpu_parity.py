@@ -391,3 +391,17 @@ def test_energy_every_keeps_dynamics_and_reports_the_same_energies():
         assert t5[step, 0] == step
         np.testing.assert_array_equal(t5[step], t1[step])
     assert t5[7, 0] == 0.0  # not an energy step: the row was never written
+
+
+@pytest.mark.parametrize("tpp", [1, 2, 4, 8])
+def test_cutoff_band_fixup_with_threads_per_particle(tpp):
+    """A random (not lattice) LJ configuration has pairs within the 1e-5 band around rc^2 for tens of
+    particles; with several threads per particle each lane must correct exactly its own entries."""
+    s = systems.make_wca(40000, 0.42, seed=88)
+    s = systems.System(systems.LJ, s.pos, s.vel, s.box, 2.5, 0.3, 0.001, 1.0, name="lj_random_0.42")
+    Fr, _, _, _ = oracle.forces(s.pos, model_of(s), use_cells=True)
+    outer = len(oracle.pairs(s.pos, s.box, 2.5 * np.sqrt(1 + 1e-5), use_cells=True))
+    inner = len(oracle.pairs(s.pos, s.box, 2.5 * np.sqrt(1 - 1e-5), use_cells=True))
+    assert outer - inner >= 5  # the configuration does exercise the band
+    _, (F, _, _, _) = run_forces(s, B.MD_MIXED, B.MD_VERTEX, tpp=tpp)
+    check_mixed(F, Fr, f"force tpp={tpp}")
