@@ -152,14 +152,17 @@ def run_ours(args, rank, world, dist):
         assert st1[B.MD_STATUS_CODE] == 0, f"device status {st1}"
         return e0.elapsed_time(e1), st1[B.MD_STATUS_REBUILDS] - st0[B.MD_STATUS_REBUILDS], clocks
 
-    def list_stats(sim):
+    def list_stats(sim, path=B.MD_VERTEX):
         cnt = sim.view("nbr_count", torch.int32, n)
-        full = int(cnt.sum().item())
-        return full, full // 2
+        entries = int(cnt.sum().item())
+        if path == B.MD_VERTEX_NEWTON:  # the Newton list holds every pair once
+            return 2 * entries, entries
+        return entries, entries // 2
 
     def force_launch_ms(sim, path, k):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        fn = sim.forces_vertex if path == B.MD_VERTEX else sim.forces_edge
+        fn = {B.MD_VERTEX: sim.forces_vertex, B.MD_EDGE: sim.forces_edge,
+              B.MD_VERTEX_NEWTON: sim.forces_vertex_newton, B.MD_EDGE_STORE: sim.forces_edge_store}[path]
         fn()
         torch.cuda.synchronize()
         for a, b in evs:
@@ -218,18 +221,26 @@ def run_ours(args, rank, world, dist):
 
     # ---- the other decompositions / precisions on the same workload ----
     if not args.no_variants:
-        for name, path, precision, k in (("edge_mixed", B.MD_EDGE, B.MD_MIXED, min(args.steps, 1000)),
-                                         ("vertex_fp64", B.MD_VERTEX, B.MD_FP64, min(args.steps, 40)),
-                                         ("edge_fp64", B.MD_EDGE, B.MD_FP64, min(args.steps, 40))):
-            v = Simulation(system, precision, stream=stream)
+        NW, ES = B.MD_VERTEX_NEWTON, B.MD_EDGE_STORE
+        HIL = {"cell_order": B.MD_ORDER_HILBERT}
+        for name, path, precision, k, opts in (
+                ("vertex_mixed_hilbert", B.MD_VERTEX, B.MD_MIXED, min(args.steps, 1000), HIL),
+                ("edge_mixed", B.MD_EDGE, B.MD_MIXED, min(args.steps, 1000), {}),
+                ("edge_store_mixed", ES, B.MD_MIXED, min(args.steps, 300), {"edge_store": 1}),
+                ("vertex_newton_mixed_m1", NW, B.MD_MIXED, min(args.steps, 300), {"force_copies": 1}),
+                ("vertex_newton_mixed_m16", NW, B.MD_MIXED, min(args.steps, 300), {"force_copies": 16}),
+                ("vertex_fp64", B.MD_VERTEX, B.MD_FP64, min(args.steps, 40), {}),
+                ("edge_fp64", B.MD_EDGE, B.MD_FP64, min(args.steps, 40), {}),
+                ("vertex_newton_fp64_m16", NW, B.MD_FP64, min(args.steps, 40), {"force_copies": 16})):
+            v = Simulation(system, precision, stream=stream, **opts)
             v.prepare(path)
             v.step(3, path, use_graph=True)
             vms, vreb, _ = time_steps(v, path, k)
             vms = max_over_ranks(vms)
-            _, vpairs = list_stats(v)
+            _, vpairs = list_stats(v, path)
             fms = force_launch_ms(v, path, min(k, 20))
             results[name] = {"steps_per_s": 1e3 * k / vms, "ms_per_step": vms / k, "rebuilds": vreb,
-                             "pair_evals_per_s": vpairs * 1e3 * k / vms, "force_kernel_ms": fms, "steps": k}
+                             "pair_evals_per_s": vpairs * 1e3 * k / vms, "force_kernel_ms": fms, "steps": k, **opts}
             del v
             torch.cuda.empty_cache()
 

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 1
+#define MD_ABI_VERSION 2
 
 /* Return / status codes. */
 enum {
@@ -72,11 +72,17 @@ enum {
                      reductions and periodic wrap (Sec. Methods, mixed precision)              */
 };
 
-/* Decomposition of the force evaluation. */
-enum { MD_VERTEX = 0, MD_EDGE = 1 };
+/* Decomposition of the force evaluation.  MD_VERTEX_NEWTON is the paper's third variant (Sec.
+ * Methods, Newton's third law in the vertex approach): one thread per particle over half of its
+ * neighbours, with the reaction forces added atomically to one of m force copies. */
+enum { MD_VERTEX = 0, MD_EDGE = 1, MD_VERTEX_NEWTON = 2, MD_EDGE_STORE = 3 };
 
-/* Which neighbour lists md_build_verlet writes. */
-enum { MD_LIST_FULL = 1, MD_LIST_HALF = 2, MD_LIST_BOTH = 3 };
+/* Order of the cells, and with them of the particles, after md_build_cells. */
+enum { MD_ORDER_ROWS = 0, MD_ORDER_HILBERT = 1 };
+
+/* Which neighbour lists md_build_verlet writes.  MD_LIST_NEWTON is the half list of the
+ * MD_VERTEX_NEWTON path in the full list's storage (so it replaces the full list). */
+enum { MD_LIST_FULL = 1, MD_LIST_HALF = 2, MD_LIST_BOTH = 3, MD_LIST_NEWTON = 4 };
 
 #define MD_MAX_PATCH 4
 
@@ -88,6 +94,7 @@ enum {
   MD_STATUS_NEED_PAIRS_HI = 3, /* ... and the bits above                                  */
   MD_STATUS_REBUILDS = 4,      /* number of cell + Verlet rebuilds done by md_step_verlet  */
   MD_STATUS_STEPS = 5,         /* number of steps done by md_step_verlet                   */
+  MD_STATUS_LISTS = 6,         /* MD_LIST_* bits of the lists built by the last md_build_verlet */
   MD_STATUS_WORDS = 16
 };
 
@@ -113,7 +120,12 @@ typedef struct md_params {
   int32_t trace_capacity;        /* energy-trace rows kept by md_step_verlet (0 = none)         */
   int32_t energy_every;          /* md_step_verlet reduces energies on steps that are multiples of this
                                     (0 or 1: every step); the last step of a call always            */
-  int32_t reserved;              /* must be 0                                                    */
+  int32_t force_copies;          /* MD_VERTEX_NEWTON: m force copies per particle (1..64); 0: the
+                                    path is not used and no copies are allocated                 */
+  int32_t cell_order;            /* MD_ORDER_ROWS (0): cells, and so particles, in row-major order;
+                                    MD_ORDER_HILBERT (1): along a Hilbert curve through the cells */
+  int32_t edge_store;            /* 1: reserve the per-edge force store of MD_EDGE_STORE and build its
+                                    by-partner index with the half list; 0: not used              */
   double box[3];                 /* periodic box edges; each must exceed 2 rv                    */
   double rc;                     /* centre-centre cut-off (LJ: 2.5 sigma; WCA: 2^(1/6) sigma)    */
   double skin;                   /* Verlet skin rs > 0; rv = rc + rs                             */
@@ -154,6 +166,16 @@ typedef struct md_ws_layout {
   size_t torque;         /* double[n][4] (tx, ty, tz, 0), patchy                                */
   size_t acc;            /* mixed edge path: float[4][n][4] FP32 atomic accumulators and their
                             compensation terms (force hi, force lo, torque hi, torque lo)          */
+  size_t copies;         /* MD_VERTEX_NEWTON reaction-force copies (force_copies > 0), zero between
+                            calls.  Mixed: float[2 or 4][m][n][4] as in acc, one block of n per copy;
+                            FP64: double[m][n][4] forces + double[m][n] virials + double[m][n][4]
+                            torques (patchy)                                                       */
+  size_t estore;         /* MD_EDGE_STORE (edge_store = 1): per-pair results of the half list, in
+                            blocks of max_pairs entries: A = (F_ij, e_ij), B = (tau_i, w_ij) and,
+                            patchy, C = (tau_j, 0); float[4] (mixed) or double[4] (FP64) each    */
+  size_t jstart;         /* int64[n + 1]: rows of the by-partner index (edge_store = 1)          */
+  size_t jedge;          /* int32[max_pairs]: half-list positions k with pairs[k].j = i, row i in
+                            increasing partner order (edge_store = 1)                           */
   size_t trace;          /* double[trace_capacity][4]: (step, K, U, W) rows of md_step_verlet */
   size_t scratch;        /* internal scratch                                                  */
 } md_ws_layout;
@@ -191,7 +213,9 @@ int md_build_cells(const md_params* p, md_state* s, void* ws, void* stream);
  * md_build_verlet -- Verlet lists L_i of every j with |x_j - x_i|^2 < rv^2,
  * rv = rc + skin (Sec. Methods), minimum image, from the cells of the last
  * md_build_cells.  which = MD_LIST_FULL (column-major list used by the vertex
- * path), MD_LIST_HALF (pairs i < j used by the edge path) or MD_LIST_BOTH.
+ * path), MD_LIST_HALF (pairs i < j used by the edge path), MD_LIST_BOTH, or
+ * MD_LIST_NEWTON (the half rows of md_forces_vertex_newton, stored in place of
+ * the full list).  MD_STATUS_LISTS records which lists are current.
  * The membership decision is exact in FP64 (candidates are filtered in FP32
  * and those within a relative band of 1e-5 of rv^2 are re-decided with the
  * FP64 distance d = x_j - x_i, d -= L rint(d / L), r^2 = dx^2 + dy^2 + dz^2
@@ -221,10 +245,35 @@ int md_forces_vertex(const md_params* p, md_state* s, void* ws, void* stream);
 int md_forces_edge(const md_params* p, md_state* s, void* ws, void* stream);
 
 /*
+ * md_forces_edge_store -- edge-based evaluation without atomics (Sec. Methods,
+ * the most general form of the edge approach): one thread per pair of the
+ * half list stores F_ij (and the pair energy, virial and torques) in the pair's
+ * slot of the per-edge store; a second kernel, one thread per particle, sums
+ * its own pairs' slots (+F_ij) and the slots where it is the partner (-F_ij,
+ * found through the by-partner index built with the half list) in a fixed
+ * order.  The result is deterministic.  Needs edge_store = 1 and MD_LIST_HALF.
+ */
+int md_forces_edge_store(const md_params* p, md_state* s, void* ws, void* stream);
+
+/*
+ * md_forces_vertex_newton -- vertex-based evaluation with Newton's third law
+ * (Sec. Methods): one thread per particle i loops over its half of the pairs
+ * (the list of MD_LIST_NEWTON: a pair (i, j) belongs to i when i < j and i + j
+ * is odd or i > j and i + j is even, which halves every row), sums F_ij into
+ * its own total and, only when the pair contributes, adds the reaction -F_ij
+ * (and half the pair energy and virial) atomically to copy i mod m of j's
+ * accumulators, m = force_copies.  A second kernel adds the m copies to the
+ * totals and clears them.  Needs MD_LIST_NEWTON and force_copies >= 1; with
+ * another list current it sets MD_ERR_INVALID in the status and writes nothing.
+ * The accumulation order is not deterministic.
+ */
+int md_forces_vertex_newton(const md_params* p, md_state* s, void* ws, void* stream);
+
+/*
  * md_step_verlet -- nsteps of NVE velocity Verlet on the caller's stream,
  * without host synchronisation: half kick with the current forces, drift,
  * rebuild of cells and lists when the largest displacement since the last
- * build exceeds skin/2, forces by `path` (MD_VERTEX or MD_EDGE), half kick.
+ * build exceeds skin/2, forces by `path` (MD_VERTEX, MD_EDGE or MD_VERTEX_NEWTON), half kick.
  * Patchy particles also get the half kicks of the angular momentum and the
  * exact rotation q <- exp(omega dt / 2) (x) q, omega = L / inertia.
  * Precondition: cells, lists and forces are current for the state (e.g. after
@@ -252,6 +301,16 @@ int md_get_forces(const md_params* p, const void* ws, double* force_out, double*
 
 /* Synchronises `stream` and copies the MD_STATUS_WORDS status words to host_out. */
 int md_read_status(const md_params* p, const void* ws, int32_t* host_out, void* stream);
+
+/*
+ * md_cell_order -- the order of the cells for p (host only, no device access): host_out[c] is the
+ * position of row-major cell c = (z ncell[1] + y) ncell[0] + x in the cell order, for the
+ * md_ws_layout.ncell grid (ncell[0] ncell[1] ncell[2] entries, caller-owned).  MD_ORDER_ROWS: the
+ * identity.  MD_ORDER_HILBERT: the rank of the cell's index on the Hilbert curve through the 2^b
+ * cube enclosing the grid (Sec. Methods: particle data sorted along a Hilbert curve for cache
+ * hits); md_build_cells then orders particles by that rank.
+ */
+int md_cell_order(const md_params* p, int32_t* host_out);
 
 /* Releases the CUDA graphs cached by md_step_verlet for this workspace (ws may be NULL: all). */
 int md_release_graphs(const void* ws);

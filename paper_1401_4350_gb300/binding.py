@@ -20,11 +20,12 @@ HEADER = os.path.join(ROOT, "include", "md.h")
 MD_OK, MD_ERR_INVALID, MD_ERR_CUDA, MD_ERR_NEIGH_OVERFLOW, MD_ERR_NONFINITE, MD_ERR_TIMEOUT, MD_ERR_UNSUPPORTED = range(7)
 MD_LJ, MD_WCA, MD_PATCHY = 0, 1, 2
 MD_FP64, MD_MIXED = 0, 1
-MD_VERTEX, MD_EDGE = 0, 1
-MD_LIST_FULL, MD_LIST_HALF, MD_LIST_BOTH = 1, 2, 3
+MD_VERTEX, MD_EDGE, MD_VERTEX_NEWTON, MD_EDGE_STORE = 0, 1, 2, 3
+MD_ORDER_ROWS, MD_ORDER_HILBERT = 0, 1
+MD_LIST_FULL, MD_LIST_HALF, MD_LIST_BOTH, MD_LIST_NEWTON = 1, 2, 3, 4
 MD_MAX_PATCH = 4
 MD_STATUS_CODE, MD_STATUS_NEED_NEIGH, MD_STATUS_NEED_PAIRS_LO, MD_STATUS_NEED_PAIRS_HI = 0, 1, 2, 3
-MD_STATUS_REBUILDS, MD_STATUS_STEPS, MD_STATUS_WORDS = 4, 5, 16
+MD_STATUS_REBUILDS, MD_STATUS_STEPS, MD_STATUS_LISTS, MD_STATUS_WORDS = 4, 5, 6, 16
 MD_ENERGY_U, MD_ENERGY_KT, MD_ENERGY_KR, MD_ENERGY_W, MD_ENERGY_WORDS = 0, 1, 2, 3, 8
 
 
@@ -32,7 +33,8 @@ class md_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("model", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_neigh", ctypes.c_int32), ("max_pairs", ctypes.c_int64), ("n_patch", ctypes.c_int32),
                 ("threads_per_particle", ctypes.c_int32), ("block_size", ctypes.c_int32),
-                ("trace_capacity", ctypes.c_int32), ("energy_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("trace_capacity", ctypes.c_int32), ("energy_every", ctypes.c_int32), ("force_copies", ctypes.c_int32),
+                ("cell_order", ctypes.c_int32), ("edge_store", ctypes.c_int32),
                 ("box", ctypes.c_double * 3), ("rc", ctypes.c_double),
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double), ("mass", ctypes.c_double),
                 ("inertia", ctypes.c_double), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
@@ -49,7 +51,7 @@ class md_ws_layout(ctypes.Structure):
     _fields_ = [("total", ctypes.c_size_t), ("ncell", ctypes.c_int32 * 3), ("force_elem", ctypes.c_int32)] + [
         (name, ctypes.c_size_t) for name in
         ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr", "nbr_count", "half_start",
-         "pairs", "force", "virial", "torque", "acc", "trace", "scratch")]
+         "pairs", "force", "virial", "torque", "acc", "copies", "estore", "jstart", "jedge", "trace", "scratch")]
 
 
 class MDError(RuntimeError):
@@ -90,11 +92,14 @@ def load(path: str = LIB_PATH):
         "md_build_verlet": ([_P, _S, _V, ctypes.c_int32, _V], ctypes.c_int),
         "md_forces_vertex": ([_P, _S, _V, _V], ctypes.c_int),
         "md_forces_edge": ([_P, _S, _V, _V], ctypes.c_int),
+        "md_forces_vertex_newton": ([_P, _S, _V, _V], ctypes.c_int),
+        "md_forces_edge_store": ([_P, _S, _V, _V], ctypes.c_int),
         "md_step_verlet": ([_P, _S, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _V], ctypes.c_int),
         "md_prepare": ([_P, _S, _V, ctypes.c_int32, _V], ctypes.c_int),
         "md_get_forces": ([_P, _V, _V, _V, _V], ctypes.c_int),
         "md_read_status": ([_P, _V, ctypes.POINTER(ctypes.c_int32), _V], ctypes.c_int),
         "md_release_graphs": ([_V], ctypes.c_int),
+        "md_cell_order": ([_P, _V], ctypes.c_int),
         "md_build_cells_static": ([_P, _S, _V, _V, _V, _V], ctypes.c_int),
         "md_batch_workspace_bytes": ([_P, ctypes.c_int32], ctypes.c_size_t),
         "md_batch_replica_offset": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_size_t),
@@ -179,6 +184,14 @@ def md_forces_edge(p, s, ws, stream=None):
     return _check(load().md_forces_edge(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
 
 
+def md_forces_edge_store(p, s, ws, stream=None):
+    return _check(load().md_forces_edge_store(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
+
+
+def md_forces_vertex_newton(p, s, ws, stream=None):
+    return _check(load().md_forces_vertex_newton(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
+
+
 def md_step_verlet(p, s, ws, nsteps, path=MD_VERTEX, use_graph=True, stream=None):
     return _check(load().md_step_verlet(ctypes.byref(p), ctypes.byref(s), _ptr(ws), int(nsteps), int(path),
                                         int(bool(use_graph)), _stream(stream)))
@@ -201,6 +214,15 @@ def md_read_status(p, ws, stream=None):
 
 def md_release_graphs(ws=None):
     return load().md_release_graphs(_ptr(ws) if ws is not None else None)
+
+
+def md_cell_order(p):
+    """Position of every row-major cell in the cell order of p (numpy int32 array, host only)."""
+    import numpy as np
+    L = md_workspace_layout(p)
+    out = np.empty(int(L.ncell[0]) * int(L.ncell[1]) * int(L.ncell[2]), dtype=np.int32)
+    _check(load().md_cell_order(ctypes.byref(p), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 MD_STATIC_MAX_N = 32768

@@ -79,7 +79,16 @@ static int check(const md_params* p) {
   }
   if (p->trace_capacity < 0) { set_error("trace_capacity must be >= 0"); return MD_ERR_INVALID; }
   if (p->energy_every < 0) { set_error("energy_every must be >= 0"); return MD_ERR_INVALID; }
-  if (p->reserved != 0) { set_error("reserved must be 0"); return MD_ERR_INVALID; }
+  if (p->force_copies < 0 || p->force_copies > 64) { set_error("force_copies must be in 0..64"); return MD_ERR_INVALID; }
+  if (p->cell_order != MD_ORDER_ROWS && p->cell_order != MD_ORDER_HILBERT) {
+    set_error("cell_order must be MD_ORDER_ROWS or MD_ORDER_HILBERT");
+    return MD_ERR_INVALID;
+  }
+  if (p->edge_store != 0 && p->edge_store != 1) { set_error("edge_store must be 0 or 1"); return MD_ERR_INVALID; }
+  if (p->edge_store && p->max_pairs >= (int64_t)1 << 31) {
+    set_error("edge_store needs max_pairs < 2^31 (32-bit positions in the by-partner index)");
+    return MD_ERR_INVALID;
+  }
   if (p->model == MD_PATCHY) {
     if (p->n_patch < 1 || p->n_patch > MD_MAX_PATCH) { set_error("n_patch must be in 1..%d", MD_MAX_PATCH); return MD_ERR_INVALID; }
     if (!(p->inertia > 0.0) || !(p->delta > 0.0)) { set_error("inertia and delta must be > 0"); return MD_ERR_INVALID; }
@@ -88,9 +97,23 @@ static int check(const md_params* p) {
   return MD_OK;
 }
 
+// Bytes of the per-edge store (0 unless edge_store): blocks A, B and, patchy, C of max_pairs entries.
+static size_t estore_bytes(const md_params* p) {
+  if (!p->edge_store) return 0;
+  const size_t elem = p->precision == MD_MIXED ? 16 : 32;
+  return elem * (size_t)p->max_pairs * (p->model == MD_PATCHY ? 3 : 2);
+}
+
+// Bytes of the Newton-vertex reaction copies (0 when force_copies is 0).
+static size_t copies_bytes(const md_params* p) {
+  const size_t m = (size_t)p->force_copies, n = (size_t)p->n;
+  const bool patchy = p->model == MD_PATCHY;
+  return p->precision == MD_MIXED ? 16 * n * m * (patchy ? 4 : 2) : m * n * (32 + 8 + (patchy ? 32 : 0));
+}
+
 struct Layout {
   md_ws_layout pub;
-  size_t scr_words, block_partials, cell_of, rank, perm, count_tmp, block_sums, tmp_d4, tmp_i;
+  size_t scr_words, block_partials, cell_of, rank, perm, count_tmp, block_sums, tmp_d4, tmp_i, cell_rank;
   int partial_capacity;
 };
 
@@ -125,6 +148,10 @@ static void make_layout(const md_params* p, Layout* L) {
   P.virial = take(8 * n);
   P.torque = take(patchy ? 32 * n : 0);
   P.acc = take(p->precision == MD_MIXED ? 16 * n * (patchy ? 4 : 2) : 0);
+  P.copies = take(copies_bytes(p));
+  P.estore = take(estore_bytes(p));
+  P.jstart = take(p->edge_store ? sizeof(int64_t) * (n + 1) : 0);
+  P.jedge = take(p->edge_store ? sizeof(int32_t) * (size_t)p->max_pairs : 0);
   P.trace = take(sizeof(double) * 4 * (size_t)p->trace_capacity);
   P.scratch = off;
   L->scr_words = take(sizeof(uint32_t) * SCR_WORDS);
@@ -139,6 +166,7 @@ static void make_layout(const md_params* p, Layout* L) {
   L->block_sums = take(sizeof(int64_t) * (mcount / kScanTile + 4));
   L->tmp_d4 = take(32 * n * (patchy ? 4 : 2));
   L->tmp_i = take(sizeof(int32_t) * n);
+  L->cell_rank = take(p->cell_order == MD_ORDER_HILBERT ? sizeof(int32_t) * ncell : 0);
   P.total = off;
 }
 
@@ -189,6 +217,23 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     a.rwca2_lo_u = f32(a.rwca2_d * (1.0 - 1e-5) / u2);
     a.rwca2_hi_u = f32(a.rwca2_d * (1.0 + 1e-5) / u2);
     if (p->model == MD_PATCHY) a.u2_over_delta2 = f32(u2 / (p->delta * p->delta));
+    // Scaled units of the isotropic vertex kernel.  A pair of a current list is closer than
+    // rv + skin (each particle moves less than skin/2 between builds), so the shift leaves the
+    // largest such r^2 below 2^31 and keeps more than 24 bits of r^2 for every r > (rv + skin) / 6.
+    const double rmax_u = (rv + p->skin) * 1.01 / u;
+    int S = (int)ceil(log2(rmax_u * rmax_u)) - 31;
+    S = S < 1 ? 1 : (S > 31 ? 31 : S);
+    const double unit2 = u2 * ldexp(1.0, S);
+    a.r2_shift = S;
+    a.r2_hi_max = (uint32_t)((1ull << S) - 1ull);
+    a.nsig2_s = f32(-p->sigma * p->sigma / unit2);
+    a.rwca2_s = f32(a.rwca2_d / unit2);
+    a.rwca2_lo_s = f32(a.rwca2_d * (1.0 - 1e-5) / unit2);
+    a.rwca2_hi_s = f32(a.rwca2_d * (1.0 + 1e-5) / unit2);
+    a.rwca2_band_s = fmaxf(a.rwca2_hi_s - a.rwca2_s, a.rwca2_s - a.rwca2_lo_s);
+    const double fscale = -24.0 * p->eps / (u * ldexp(1.0, S));
+    a.fscale_hi = f32(fscale);
+    a.fscale_lo = f32(fscale - (double)a.fscale_hi);
   }
   const double sr2 = p->sigma * p->sigma / a.rwca2_d, sr6 = sr2 * sr2 * sr2;
   a.sig2_d = p->sigma * p->sigma;
@@ -254,6 +299,11 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.virial = (double*)(w + L.pub.virial);
   a.torque = (double4_32a*)(w + L.pub.torque);
   a.acc = (float4*)(w + L.pub.acc);
+  a.copies = (void*)(w + L.pub.copies);
+  a.force_copies = p->force_copies;
+  a.estore = p->edge_store ? (void*)(w + L.pub.estore) : nullptr;
+  a.jstart = p->edge_store ? (int64_t*)(w + L.pub.jstart) : nullptr;
+  a.jedge = p->edge_store ? (int32_t*)(w + L.pub.jedge) : nullptr;
   a.trace = (double*)(w + L.pub.trace);
   a.scr_words = (uint32_t*)(w + L.scr_words);
   a.block_partials = (double*)(w + L.block_partials);
@@ -264,6 +314,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.block_sums = (int64_t*)(w + L.block_sums);
   a.tmp_d4 = (double4_32a*)(w + L.tmp_d4);
   a.tmp_i = (int32_t*)(w + L.tmp_i);
+  a.cell_rank = p->cell_order == MD_ORDER_HILBERT ? (const int32_t*)(w + L.cell_rank) : nullptr;
   a.partial_capacity = L.partial_capacity;
   return a;
 }
@@ -277,8 +328,9 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
   a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
   a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
+  a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr;
   a.scr_words = nullptr; a.block_partials = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;
-  a.count_tmp = nullptr; a.block_sums = nullptr; a.tmp_d4 = nullptr; a.tmp_i = nullptr;
+  a.count_tmp = nullptr; a.block_sums = nullptr; a.tmp_d4 = nullptr; a.tmp_i = nullptr; a.cell_rank = nullptr;
   return a;
 }
 
@@ -335,7 +387,36 @@ static void destroy_entry(GraphEntry& e) {
   }
 }
 
-static int list_kind(int path) { return path == MD_EDGE ? MD_LIST_BOTH : MD_LIST_FULL; }
+static int list_kind(int path) {
+  if (path == MD_EDGE || path == MD_EDGE_STORE) return MD_LIST_BOTH;
+  return path == MD_VERTEX_NEWTON ? MD_LIST_NEWTON : MD_LIST_FULL;
+}
+
+static const char* path_name(int path) {
+  switch (path) {
+    case MD_VERTEX: return "md_forces_vertex";
+    case MD_EDGE: return "md_forces_edge";
+    case MD_VERTEX_NEWTON: return "md_forces_vertex_newton";
+    default: return "md_forces_edge_store";
+  }
+}
+
+// Path argument check; the Newton path also needs force copies in the workspace.
+static int check_path(const md_params* p, int path) {
+  if (path != MD_VERTEX && path != MD_EDGE && path != MD_VERTEX_NEWTON && path != MD_EDGE_STORE) {
+    set_error("path must be MD_VERTEX, MD_EDGE, MD_VERTEX_NEWTON or MD_EDGE_STORE");
+    return MD_ERR_INVALID;
+  }
+  if (path == MD_VERTEX_NEWTON && p->force_copies < 1) {
+    set_error("MD_VERTEX_NEWTON needs force_copies >= 1");
+    return MD_ERR_INVALID;
+  }
+  if (path == MD_EDGE_STORE && !p->edge_store) {
+    set_error("MD_EDGE_STORE needs edge_store = 1");
+    return MD_ERR_INVALID;
+  }
+  return MD_OK;
+}
 
 static int build_step_graph(const KArgs& a, int mode, int path, int block, cudaGraph_t* g_out, cudaGraphExec_t* exec_out) {
   cudaStream_t cs = nullptr;
@@ -473,6 +554,17 @@ int md_init_workspace(const md_params* p, void* ws, void* stream) {
   make_layout(p, &L);
   KArgs a = make_args(p, nullptr, ws, L);
   cudaError_t e = launch_init_ws(a, (cudaStream_t)stream);
+  const size_t cb = copies_bytes(p);
+  if (e == cudaSuccess && cb) e = cudaMemsetAsync((char*)ws + L.pub.copies, 0, cb, (cudaStream_t)stream);
+  if (e == cudaSuccess && p->cell_order == MD_ORDER_HILBERT) {
+    // the rank table depends on the grid only; a copy from pageable memory has been staged when
+    // cudaMemcpyAsync returns, so the host vector may go out of scope afterwards
+    const int nc[3] = {L.pub.ncell[0], L.pub.ncell[1], L.pub.ncell[2]};
+    std::vector<int32_t> rank((size_t)nc[0] * nc[1] * nc[2]);
+    hilbert_cell_ranks(nc, rank.data());
+    e = cudaMemcpyAsync((char*)ws + L.cell_rank, rank.data(), sizeof(int32_t) * rank.size(), cudaMemcpyHostToDevice,
+                        (cudaStream_t)stream);
+  }
   return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_init_workspace");
 }
 
@@ -491,7 +583,7 @@ int md_build_verlet(const md_params* p, md_state* s, void* ws, int32_t which, vo
   int rc = check(p);
   if (rc == MD_OK) rc = check_state(p, s, ws);
   if (rc != MD_OK) return rc;
-  if (which < MD_LIST_FULL || which > MD_LIST_BOTH) { set_error("which must be 1, 2 or 3"); return MD_ERR_INVALID; }
+  if (which < MD_LIST_FULL || which > MD_LIST_NEWTON) { set_error("which must be 1, 2, 3 or 4"); return MD_ERR_INVALID; }
   Layout L;
   make_layout(p, &L);
   KArgs a = make_args(p, s, ws, L);
@@ -502,12 +594,13 @@ int md_build_verlet(const md_params* p, md_state* s, void* ws, int32_t which, vo
 static int forces_entry(const md_params* p, md_state* s, void* ws, int path, void* stream) {
   int rc = check(p);
   if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc == MD_OK) rc = check_path(p, path);
   if (rc != MD_OK) return rc;
   Layout L;
   make_layout(p, &L);
   KArgs a = make_args(p, s, ws, L);
   cudaError_t e = launch_forces(a, path, p->block_size, (cudaStream_t)stream);
-  return e == cudaSuccess ? MD_OK : cuda_fail(e, path == MD_VERTEX ? "md_forces_vertex" : "md_forces_edge");
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, path_name(path));
 }
 
 int md_forces_vertex(const md_params* p, md_state* s, void* ws, void* stream) {
@@ -518,11 +611,19 @@ int md_forces_edge(const md_params* p, md_state* s, void* ws, void* stream) {
   return forces_entry(p, s, ws, MD_EDGE, stream);
 }
 
+int md_forces_edge_store(const md_params* p, md_state* s, void* ws, void* stream) {
+  return forces_entry(p, s, ws, MD_EDGE_STORE, stream);
+}
+
+int md_forces_vertex_newton(const md_params* p, md_state* s, void* ws, void* stream) {
+  return forces_entry(p, s, ws, MD_VERTEX_NEWTON, stream);
+}
+
 int md_prepare(const md_params* p, md_state* s, void* ws, int32_t path, void* stream) {
   int rc = check(p);
   if (rc == MD_OK) rc = check_state(p, s, ws);
   if (rc != MD_OK) return rc;
-  if (path != MD_VERTEX && path != MD_EDGE) { set_error("path must be MD_VERTEX or MD_EDGE"); return MD_ERR_INVALID; }
+  if ((rc = check_path(p, path)) != MD_OK) return rc;
   Layout L;
   make_layout(p, &L);
   KArgs a = make_args(p, s, ws, L);
@@ -539,7 +640,7 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
   int rc = check(p);
   if (rc == MD_OK) rc = check_state(p, s, ws);
   if (rc != MD_OK) return rc;
-  if (path != MD_VERTEX && path != MD_EDGE) { set_error("path must be MD_VERTEX or MD_EDGE"); return MD_ERR_INVALID; }
+  if ((rc = check_path(p, path)) != MD_OK) return rc;
   if (nsteps < 0) { set_error("nsteps must be >= 0"); return MD_ERR_INVALID; }
   if (nsteps == 0) return MD_OK;
   Layout L;
@@ -593,6 +694,21 @@ int md_read_status(const md_params* p, const void* ws, int32_t* host_out, void* 
   if (e == cudaSuccess)
     e = cudaMemcpy(host_out, (const char*)ws + L.pub.status, sizeof(int32_t) * MD_STATUS_WORDS, cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_read_status");
+}
+
+int md_cell_order(const md_params* p, int32_t* host_out) {
+  int rc = check(p);
+  if (rc != MD_OK) return rc;
+  if (!host_out) { set_error("host_out is NULL"); return MD_ERR_INVALID; }
+  int nc[3];
+  cell_dims(p, nc);
+  const size_t total = (size_t)nc[0] * nc[1] * nc[2];
+  if (p->cell_order == MD_ORDER_HILBERT) {
+    hilbert_cell_ranks(nc, host_out);
+  } else {
+    for (size_t c = 0; c < total; c++) host_out[c] = (int32_t)c;
+  }
+  return MD_OK;
 }
 
 int md_release_graphs(const void* ws) {

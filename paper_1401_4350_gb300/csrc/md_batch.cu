@@ -237,7 +237,10 @@ __global__ void __launch_bounds__(1024) k_b_rb_replica(BatchDev b) {
   __syncthreads();
   if (PHASE == RBR_ZERO) {
     for (int c = threadIdx.x; c < ka.ncell_total; c += blockDim.x) ka.count_tmp[c] = 0;
-    if (threadIdx.x == 0) ka.status[MD_STATUS_NEED_NEIGH] = 0;
+    if (threadIdx.x == 0) {
+      ka.status[MD_STATUS_NEED_NEIGH] = 0;
+      ka.status[MD_STATUS_LISTS] = MD_LIST_FULL | ((b.all_half || (b.kind[r] & KIND_EDGE)) ? MD_LIST_HALF : 0);
+    }
   }
   if (PHASE == RBR_CELLSCAN) block_scan_array<int32_t>(ka.count_tmp, ka.cell_start, ka.ncell_total);
   if (PHASE == RBR_SORT)
@@ -407,6 +410,10 @@ static int check_batch_params(const md_params* reps, int nrep) {
     if (rc != MD_OK) return rc;
     if (reps[r].precision != MD_MIXED || reps[r].model == MD_PATCHY) {
       set_error("batch: replica %d: the batched path supports mixed-precision LJ and WCA replicas", r);
+      return MD_ERR_INVALID;
+    }
+    if (reps[r].cell_order != MD_ORDER_ROWS || reps[r].force_copies != 0 || reps[r].edge_store != 0) {
+      set_error("batch: replica %d: cell_order, force_copies and edge_store must be 0 in a batch", r);
       return MD_ERR_INVALID;
     }
   }

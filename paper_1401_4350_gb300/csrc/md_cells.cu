@@ -1,6 +1,10 @@
 // md_cells.cu -- cell binning with a counting sort (Sec. Methods: "cell filling" one particle per
 // thread; particle data reordered in global memory for cache hits, here in cell order) and the
 // exclusive scans used by the cell and Verlet builds.
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "md_cells.cuh"
 
 namespace mdgb {
@@ -128,6 +132,59 @@ cudaError_t launch_build_cells(const KArgs& a, const uint32_t* gate, cudaStream_
   k_cells_gather<<<gn, B, 0, st>>>(a, gate);
   k_cells_copyback<<<gn, B, 0, st>>>(a, gate);
   return cudaGetLastError();
+}
+
+// ---- Hilbert order of the cells ----------------------------------------------------------------
+//
+// Sec. Methods: particle data are periodically sorted along a Hilbert curve to raise cache hits.
+// Here the curve orders the cells (so the counting sort of md_build_cells produces particles in
+// Hilbert order of their cells): the key of cell (x, y, z) is its index on the Hilbert curve through
+// the 2^b cube enclosing the grid, and cells are ranked by key.  The key follows J. Skilling,
+// "Programming the Hilbert curve", AIP Conf. Proc. 707, 381 (2004): the coordinates are turned into
+// the curve's transposed index by undoing the excess rotations and reflections level by level, Gray
+// coding, and interleaving the bits, most significant level first.
+
+uint64_t hilbert_key3(uint32_t x, uint32_t y, uint32_t z, int bits) {
+  uint32_t X[3] = {x, y, z};
+  const uint32_t top = 1u << (bits - 1);
+  for (uint32_t q = top; q > 1; q >>= 1) {
+    const uint32_t low = q - 1;
+    for (int i = 0; i < 3; i++) {
+      if (X[i] & q) {
+        X[0] ^= low;  // reflect the lower bits of the first axis
+      } else {
+        const uint32_t t = (X[0] ^ X[i]) & low;  // swap the lower bits of axes 0 and i
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  X[1] ^= X[0];
+  X[2] ^= X[1];
+  uint32_t t = 0;
+  for (uint32_t q = top; q > 1; q >>= 1)
+    if (X[2] & q) t ^= q - 1;
+  for (int i = 0; i < 3; i++) X[i] ^= t;
+  uint64_t key = 0;
+  for (int b = bits - 1; b >= 0; b--)
+    for (int i = 0; i < 3; i++) key = (key << 1) | ((X[i] >> b) & 1u);
+  return key;
+}
+
+void hilbert_cell_ranks(const int nc[3], int32_t* rank) {
+  const int m = nc[0] > nc[1] ? (nc[0] > nc[2] ? nc[0] : nc[2]) : (nc[1] > nc[2] ? nc[1] : nc[2]);
+  int bits = 1;
+  while ((1 << bits) < m) bits++;
+  const size_t total = (size_t)nc[0] * nc[1] * nc[2];
+  std::vector<std::pair<uint64_t, int32_t>> keys(total);
+  for (int z = 0; z < nc[2]; z++)
+    for (int y = 0; y < nc[1]; y++)
+      for (int x = 0; x < nc[0]; x++) {
+        const int32_t c = (int32_t)(((size_t)z * nc[1] + y) * nc[0] + x);
+        keys[c] = std::make_pair(hilbert_key3((uint32_t)x, (uint32_t)y, (uint32_t)z, bits), c);
+      }
+  std::sort(keys.begin(), keys.end());
+  for (size_t r = 0; r < total; r++) rank[keys[r].second] = (int32_t)r;
 }
 
 }  // namespace mdgb

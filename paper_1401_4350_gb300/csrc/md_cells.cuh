@@ -53,6 +53,7 @@ __device__ __forceinline__ void cells_assign_one(const KArgs& a, int i) {
   uint4 f = fixed3(p, a);
   int cx = fixed_cell(f.x, a.ncell[0]), cy = fixed_cell(f.y, a.ncell[1]), cz = fixed_cell(f.z, a.ncell[2]);
   int c = (cz * a.ncell[1] + cy) * a.ncell[0] + cx;
+  if (a.cell_rank) c = a.cell_rank[c];
   a.cell_of[i] = c;
   a.rank[i] = atomicAdd(a.count_tmp + c, 1);
 }

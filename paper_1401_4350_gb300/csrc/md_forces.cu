@@ -10,6 +10,13 @@
 // list are grouped by i, so a warp first sums the contributions of each run of equal i with a
 // segmented shuffle reduction and issues one atomic per run; the j side is one atomic per pair.
 //
+// Vertex-based with Newton's third law (the paper's third variant): one thread per particle over a
+// half row; own total in registers, reactions atomically into one of m copies of the partner's
+// accumulators (copy i mod m), copies added to the totals by a second kernel.
+//
+// Edge-based with a per-edge store: pair results written to per-pair slots, then a per-particle
+// pass sums them in a fixed order (deterministic, no atomics).
+//
 // Pair arithmetic.  MD_FP64: positions in FP64, minimum image d -= L rint(d / L).  MD_MIXED:
 // positions as 32-bit fixed-point fractions of the box, so that the difference of two
 // coordinates taken in 32-bit integer arithmetic is the minimum image (wrap-around is the
@@ -90,8 +97,41 @@ __global__ void k_edge_finalize(KArgs a) {
   if (i < a.n) edge_finalize_one(a, i);
 }
 
+template <bool PATCHY, int NP>
+static void launch_newton(const KArgs& a, int block, cudaStream_t st) {
+  const int grid = (a.n + block - 1) / block;
+  if (a.precision == MD_MIXED) k_vertex_newton_mixed<PATCHY, NP><<<grid, block, 0, st>>>(a);
+  else k_vertex_newton_fp64<PATCHY, NP><<<grid, block, 0, st>>>(a);
+}
+
+__global__ void k_newton_finalize(KArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) newton_finalize_one(a, i);
+}
+
+__global__ void k_edge_store_reduce(KArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) edge_store_reduce_one(a, i);
+}
+
+template <bool PATCHY, int NP>
+static void launch_edge_store(const KArgs& a, int block, cudaStream_t st) {
+  int64_t want = (a.max_pairs + block - 1) / block;
+  int64_t cap = (int64_t)sm_count() * (2048 / block);
+  const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  k_edge_store<PATCHY, NP><<<grid, block, 0, st>>>(a);
+}
+
+template <bool PATCHY, int NP>
+static void launch_path(const KArgs& a, int path, int block, cudaStream_t st) {
+  if (path == MD_VERTEX) launch_vertex<PATCHY, NP>(a, block, st);
+  else if (path == MD_EDGE) launch_edge<PATCHY, NP>(a, block, st);
+  else if (path == MD_EDGE_STORE) launch_edge_store<PATCHY, NP>(a, block, st);
+  else launch_newton<PATCHY, NP>(a, block, st);
+}
+
 cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st) {
-  if (block <= 0) block = (path == MD_VERTEX) ? 128 : 256;
+  if (block <= 0) block = (path == MD_EDGE || path == MD_EDGE_STORE) ? 256 : 128;
   if (path == MD_EDGE) {
     const size_t n = (size_t)a.n;
     if (a.precision == MD_MIXED) {
@@ -103,17 +143,18 @@ cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st) 
     }
   }
   if (a.model != MD_PATCHY) {
-    if (path == MD_VERTEX) launch_vertex<false, 1>(a, block, st);
-    else launch_edge<false, 1>(a, block, st);
+    launch_path<false, 1>(a, path, block, st);
   } else {
     switch (a.n_patch) {
-      case 1: if (path == MD_VERTEX) launch_vertex<true, 1>(a, block, st); else launch_edge<true, 1>(a, block, st); break;
-      case 2: if (path == MD_VERTEX) launch_vertex<true, 2>(a, block, st); else launch_edge<true, 2>(a, block, st); break;
-      case 3: if (path == MD_VERTEX) launch_vertex<true, 3>(a, block, st); else launch_edge<true, 3>(a, block, st); break;
-      default: if (path == MD_VERTEX) launch_vertex<true, 4>(a, block, st); else launch_edge<true, 4>(a, block, st); break;
+      case 1: launch_path<true, 1>(a, path, block, st); break;
+      case 2: launch_path<true, 2>(a, path, block, st); break;
+      case 3: launch_path<true, 3>(a, path, block, st); break;
+      default: launch_path<true, 4>(a, path, block, st); break;
     }
   }
   if (path == MD_EDGE && a.precision == MD_MIXED) k_edge_finalize<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+  if (path == MD_VERTEX_NEWTON) k_newton_finalize<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+  if (path == MD_EDGE_STORE) k_edge_store_reduce<<<(a.n + 127) / 128, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

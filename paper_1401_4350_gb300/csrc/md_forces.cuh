@@ -350,13 +350,26 @@ __device__ __forceinline__ void group_reduce(Comp3& F, Comp3& T, float& e, float
 // so a warp reads 512 contiguous bytes per group.  The kernels prefetch the next group while the
 // current one is evaluated and issue the four coordinate gathers of a group together, which keeps
 // enough loads in flight per SM to cover the memory latency.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+constexpr int kListPrefetch = 4;  // groups of the list requested ahead of their use
+
 __device__ __forceinline__ int4 load_group(const int4* nb4, int g, int ng, size_t n) {
   return g < ng ? __ldcs(nb4 + (size_t)g * n) : make_int4(-1, -1, -1, -1);
+}
+
+// The vertex kernels walk the full list; the Newton list is kept in the same storage, so a vertex
+// evaluation after a Newton build records MD_ERR_INVALID instead of using half rows.
+__device__ __forceinline__ bool full_list_current(const KArgs& a) {
+  if (!(a.status[MD_STATUS_LISTS] & MD_LIST_NEWTON)) return true;
+  if (threadIdx.x == 0) record_error(a.status, MD_ERR_INVALID);
+  return false;
 }
 
 // Mixed precision vertex kernel.  PATCHY selects the patchy pair, NP its patch count.
 template <int TPP, bool PATCHY, int NP>
 __device__ __forceinline__ void vertex_mixed_body(const KArgs& a, int gt) {
+  if (!full_list_current(a)) return;
   const int i = gt / TPP, l = gt % TPP;
   const bool valid = i < a.n;
   Comp3 F = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -450,8 +463,220 @@ __device__ __forceinline__ void iso_pair_mixed_u(const KArgs& a, const uint4& si
   t = a.lj_c24_f * sr6 * (2.f * sr6 - 1.f);  // -fs r^2
 }
 
+// ---- isotropic mixed vertex kernel of a cubic box --------------------------------------------
+//
+// The separation d = x_j - x_i is the integer difference of the 32-bit fixed-point coordinates
+// (exact, periodic by wrap-around).  r^2 is the exact 64-bit sum of squares shifted right by
+// r2_shift and converted once (units u^2 2^r2_shift), so it carries one rounding like an FP32
+// product; the components enter the force as FP32 values of the integer differences.  With
+// rn = -1/r^2, s6 = (sigma/r)^6 and s12 = s6^2 the pair adds
+//     F_i += -24 eps (2 s12 - s6) / r^2 d,   E_i += [4 eps (s12 - s6) - V(rc)] / 2,
+//     W_i += 24 eps (2 s12 - s6) / 2,
+// and the kernel accumulates only (2 s12 - s6) / r^2 d, s12, s6 and the pair count, leaving the
+// constant factors to the end.  Two list entries share each packed FP32x2 instruction.
+
+__device__ __forceinline__ float r2_scaled(const KArgs& a, int ix, int iy, int iz) {
+  const unsigned long long s = (unsigned long long)((long long)ix * ix) + (unsigned long long)((long long)iy * iy) +
+                               (unsigned long long)((long long)iz * iz);
+  // beyond the range of a current list the high word saturates: r^2 reads >= 2^31, past any cut-off
+  const unsigned hi = min((unsigned)(s >> 32), a.r2_hi_max);
+  return __uint2float_rn(__funnelshift_r((unsigned)s, hi, a.r2_shift));
+}
+
+// -1/x: the hardware reciprocal of -x refined by one Newton step (the steep core multiplies the
+// reciprocal's relative error by about nine)
+__device__ __forceinline__ float2 neg_rcp2(float2 x) {
+  const float2 yn = make_float2(frcp_approx(-x.x), frcp_approx(-x.y));
+  const float2 e = __ffma2_rn(x, yn, make_float2(1.f, 1.f));
+  return __ffma2_rn(yn, e, yn);
+}
+
+__device__ __forceinline__ float neg_rcp1(float x) {
+  const float yn = frcp_approx(-x);
+  return __fmaf_rn(yn, __fmaf_rn(x, yn, 1.f), yn);
+}
+
+// Kahan step on two independent lanes: s - c is the running sum of each lane
+__device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 term) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 y = __ffma2_rn(c, m1, term);
+  const float2 t = __fadd2_rn(s, y);
+  c = __ffma2_rn(y, m1, __ffma2_rn(s, m1, t));
+  s = t;
+}
+
+struct IsoAcc {
+  float2 fx, fy, fz;  // Kahan sums (two lanes each)
+  float2 cx, cy, cz;  // their compensations
+  float2 s12, s6;     // sums of (sigma/r)^12 and (sigma/r)^6 over the pairs inside the cut-off
+  int nin;            // pairs inside the cut-off
+  float bmin;         // smallest |r^2 - rc^2| seen (band test)
+};
+
+// One group of four list entries (cur) of particle si.  LIVE: some entries may lie past the count.
+template <bool LIVE>
+__device__ __forceinline__ void iso_group(const KArgs& a, const uint4& si, const int4& cur, int lim, unsigned jmax,
+                                          IsoAcc& A) {
+  const unsigned jj[4] = {min((unsigned)cur.x, jmax), min((unsigned)cur.y, jmax), min((unsigned)cur.z, jmax),
+                          min((unsigned)cur.w, jmax)};
+  uint4 sj[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) sj[u] = __ldg(a.fxp + jj[u]);
+  float r2[4], dx[4], dy[4], dz[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const int ix = (int)(sj[u].x - si.x), iy = (int)(sj[u].y - si.y), iz = (int)(sj[u].z - si.z);
+    r2[u] = r2_scaled(a, ix, iy, iz);
+    dx[u] = (float)ix;
+    dy[u] = (float)iy;
+    dz[u] = (float)iz;
+  }
+  const float2 thr2 = make_float2(-a.rwca2_s, -a.rwca2_s);
+  float2 gx, gy, gz;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const float2 x = make_float2(r2[2 * h], r2[2 * h + 1]);
+    const float2 off = __fadd2_rn(x, thr2);
+    A.bmin = fminf(A.bmin, fminf(fabsf(off.x), fabsf(off.y)));
+    const bool in0 = (!LIVE || 2 * h < lim) && x.x < a.rwca2_s;
+    const bool in1 = (!LIVE || 2 * h + 1 < lim) && x.y < a.rwca2_s;
+    float2 rn = neg_rcp2(x);
+    rn.x = in0 ? rn.x : 0.f;  // pairs outside contribute exact zeros from here on
+    rn.y = in1 ? rn.y : 0.f;
+    const float2 sr2 = __fmul2_rn(make_float2(a.nsig2_s, a.nsig2_s), rn);
+    const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
+    const float2 sr12 = __fmul2_rn(sr6, sr6);
+    const float2 qn = __ffma2_rn(sr12, make_float2(-2.f, -2.f), sr6);  // -(2 s12 - s6)
+    const float2 fs = __fmul2_rn(qn, rn);                              // (2 s12 - s6) / r^2
+    const float2 ddx = make_float2(dx[2 * h], dx[2 * h + 1]), ddy = make_float2(dy[2 * h], dy[2 * h + 1]),
+                 ddz = make_float2(dz[2 * h], dz[2 * h + 1]);
+    if (h == 0) {
+      gx = __fmul2_rn(fs, ddx);
+      gy = __fmul2_rn(fs, ddy);
+      gz = __fmul2_rn(fs, ddz);
+    } else {
+      gx = __ffma2_rn(fs, ddx, gx);
+      gy = __ffma2_rn(fs, ddy, gy);
+      gz = __ffma2_rn(fs, ddz, gz);
+    }
+    A.s12 = __fadd2_rn(A.s12, sr12);
+    A.s6 = __fadd2_rn(A.s6, sr6);
+    A.nin += (int)in0 + (int)in1;
+  }
+  kahan_add2(A.fx, A.cx, gx);
+  kahan_add2(A.fy, A.cy, gy);
+  kahan_add2(A.fz, A.cz, gz);
+}
+
+// (s + lo) * (hi + lo') with the product's rounding error kept: FP64 result from FP32 operations
+__device__ __forceinline__ double scale_ff(float s, float lo, float sh, float sl) {
+  const float p = __fmul_rn(s, sh);
+  const float err = __fmaf_rn(s, sh, -p);
+  return (double)p + (double)__fmaf_rn(s, sl, __fmaf_rn(lo, sh, err));
+}
+
+template <int TPP>
+__device__ __forceinline__ void vertex_iso_cubic_body(const KArgs& a, int gt) {
+  if (!full_list_current(a)) return;
+  const int i = gt / TPP, l = gt % TPP;
+  const bool valid = i < a.n;
+  const size_t n = (size_t)a.n;
+  const unsigned jmax = (unsigned)a.n - 1u;
+  IsoAcc A;
+  A.fx = A.fy = A.fz = A.cx = A.cy = A.cz = A.s12 = A.s6 = make_float2(0.f, 0.f);
+  A.nin = 0;
+  A.bmin = 3.0e38f;
+  int cnt = 0;
+  uint4 si = make_uint4(0u, 0u, 0u, 0u);
+  if (valid) {
+    const int4* nb4 = (const int4*)a.nbr + i;
+    si = __ldg(a.fxp + i);
+    cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
+    const int ng = (cnt + 3) >> 2, nfull = cnt >> 2;
+    int4 cur = load_group(nb4, l, ng, n);
+    // the list streams from DRAM: groups further ahead are requested into L2 so that their loads
+    // meet L2 rather than DRAM latency
+#pragma unroll
+    for (int d = 2; d < kListPrefetch; d++)
+      if (l + d * TPP < ng) prefetch_l2(nb4 + (size_t)(l + d * TPP) * n);
+    int g = l;
+    for (; g < nfull; g += TPP) {  // groups of four entries that are all in the list
+      const int4 nxt = load_group(nb4, g + TPP, ng, n);
+      if (g + kListPrefetch * TPP < ng) prefetch_l2(nb4 + (size_t)(g + kListPrefetch * TPP) * n);
+      iso_group<false>(a, si, cur, 4, jmax, A);
+      cur = nxt;
+    }
+    if (g < ng) iso_group<true>(a, si, cur, cnt - 4 * g, jmax, A);  // the partial last group
+  }
+  if (A.bmin <= a.rwca2_band_s) {
+    // pairs near rc: take the side of the exact FP64 definition, re-walking this lane's entries
+    // (groups l, l + TPP, ...) and correcting those whose FP32 decision differs
+    for (int k0 = 4 * l; k0 < cnt; k0 += 4 * TPP)
+      for (int k = k0; k < min(k0 + 4, cnt); k++) {
+        const unsigned j = min((unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n)), jmax);
+        const uint4 sj = __ldg(a.fxp + j);
+        const int ix = (int)(sj.x - si.x), iy = (int)(sj.y - si.y), iz = (int)(sj.z - si.z);
+        const float r2 = r2_scaled(a, ix, iy, iz);
+        if (!(r2 >= a.rwca2_lo_s && r2 < a.rwca2_hi_s)) continue;
+        const bool fp32_in = r2 < a.rwca2_s;
+        const bool exact_in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
+        if (fp32_in == exact_in) continue;
+        const float sgn = exact_in ? 1.f : -1.f;
+        const float rn = neg_rcp1(r2);
+        const float sr2 = __fmul_rn(a.nsig2_s, rn);
+        const float sr6 = __fmul_rn(__fmul_rn(sr2, sr2), sr2);
+        const float sr12 = __fmul_rn(sr6, sr6);
+        const float fs = __fmul_rn(__fmaf_rn(sr12, -2.f, sr6), rn) * sgn;
+        kahan_add(A.fx.x, A.cx.x, fs * (float)ix);
+        kahan_add(A.fy.x, A.cy.x, fs * (float)iy);
+        kahan_add(A.fz.x, A.cz.x, fs * (float)iz);
+        A.s12.x += sgn * sr12;
+        A.s6.x += sgn * sr6;
+        A.nin += exact_in ? 1 : -1;
+      }
+  }
+  // lanes: sum = (s.x - c.x) + (s.y - c.y), kept as an unevaluated pair (S, lo)
+  float S[3], lo[3];
+  {
+    const float2 sv[3] = {A.fx, A.fy, A.fz}, cv[3] = {A.cx, A.cy, A.cz};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      S[c] = __fadd_rn(sv[c].x, sv[c].y);
+      lo[c] = __fsub_rn(two_sum_err(sv[c].x, sv[c].y, S[c]), __fadd_rn(cv[c].x, cv[c].y));
+    }
+  }
+  float s12 = A.s12.x + A.s12.y, s6 = A.s6.x + A.s6.y;
+  int nin = A.nin;
+  if (TPP > 1) {
+#pragma unroll
+    for (int off = TPP / 2; off > 0; off >>= 1) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, S[c], off), l2 = __shfl_xor_sync(0xffffffffu, lo[c], off);
+        comp_merge(S[c], lo[c], s2, l2);
+      }
+      s12 += __shfl_xor_sync(0xffffffffu, s12, off);
+      s6 += __shfl_xor_sync(0xffffffffu, s6, off);
+      nin += __shfl_xor_sync(0xffffffffu, nin, off);
+    }
+  }
+  if (valid && l == 0) {
+    const float e = 0.5f * (a.lj_c4_f * (s12 - s6) - a.lj_shift_f * (float)nin);
+    const float w = 0.5f * a.lj_c24_f * (2.f * s12 - s6);
+    a.force[i] = make_double4_32a(scale_ff(S[0], lo[0], a.fscale_hi, a.fscale_lo),
+                                  scale_ff(S[1], lo[1], a.fscale_hi, a.fscale_lo),
+                                  scale_ff(S[2], lo[2], a.fscale_hi, a.fscale_lo), (double)e);
+    a.virial[i] = (double)w;
+  }
+}
+
 template <int TPP, bool CUBIC>
 __device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
+  if (CUBIC) {
+    vertex_iso_cubic_body<TPP>(a, gt);
+    return;
+  }
+  if (!full_list_current(a)) return;
   const int i = gt / TPP, l = gt % TPP;
   const bool valid = i < a.n;
   float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, e = 0.f, w = 0.f;
@@ -556,6 +781,7 @@ __device__ __forceinline__ void group_reduce_d(double* v, int nv) {
 
 template <int TPP, bool PATCHY, int NP>
 __device__ __forceinline__ void vertex_fp64_body(const KArgs& a, int gt) {
+  if (!full_list_current(a)) return;
   const int i = gt / TPP, l = gt % TPP;
   const bool valid = i < a.n;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // F(3), T(3), e, w
@@ -814,6 +1040,385 @@ __device__ __forceinline__ void edge_finalize_one(const KArgs& a, int i) {
     const float4 th = a.acc[2 * n + i], tl = a.acc[3 * n + i];
     a.torque[i] = make_double4_32a((double)th.x + (double)tl.x, (double)th.y + (double)tl.y,
                                    (double)th.z + (double)tl.z, 0.0);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Vertex kernels with Newton's third law (Sec. Methods): one thread per particle i walks its Newton
+// half row; the thread's own total stays in registers and is written once, while the reaction of
+// every contributing pair goes atomically to copy (i mod m) of the partner's accumulators, so that
+// threads working on common partners spread their atomics over m addresses.  newton_finalize_one
+// then adds the m copies to the totals and clears them for the next evaluation.
+// ------------------------------------------------------------------------------------------------
+
+// Mixed copies: [F hi][m][n], [F lo][m][n] and, patchy, [T hi][m][n], [T lo][m][n] (float4); the
+// .w words hold half pair energies (hi) and half pair virials (lo) as in the edge accumulators.
+__device__ __forceinline__ float4* newton_copy(const KArgs& a, int part, int c) {
+  return (float4*)a.copies + ((size_t)part * a.force_copies + c) * (size_t)a.n;
+}
+
+__device__ __forceinline__ bool newton_list_current(const KArgs& a) {
+  if (a.status[MD_STATUS_LISTS] & MD_LIST_NEWTON) return true;
+  record_error(a.status, MD_ERR_INVALID);
+  return false;
+}
+
+template <bool PATCHY, int NP>
+__device__ __forceinline__ void vertex_newton_mixed_body(const KArgs& a, int i) {
+  if (i >= a.n || !newton_list_current(a)) return;
+  const size_t n = (size_t)a.n;
+  const int c = i % a.force_copies;
+  float4* fhi = newton_copy(a, 0, c);
+  float4* flo = newton_copy(a, 1, c);
+  Comp3 F = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  Comp3 T = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float e = 0.f, w = 0.f;
+  const uint4 si = __ldg(a.fxp + i);
+  const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
+  const int ng = (cnt + 3) >> 2;
+  const int4* nb4 = (const int4*)a.nbr + i;
+  IPatches<(PATCHY ? NP : 1)> Pi;
+  if (PATCHY) Pi = load_ipatches<(PATCHY ? NP : 1)>(a, i);
+  int4 cur = load_group(nb4, 0, ng, n);
+  for (int g = 0; g < ng; g++) {
+    const int4 nxt = load_group(nb4, g + 1, ng, n);
+    int jj[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (4 * g + u >= cnt || (unsigned)jj[u] >= (unsigned)a.n) jj[u] = -1;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int j = jj[u];
+      if (j < 0) continue;
+      const uint4 sj = __ldg(a.fxp + j);
+      const Vec3<float> d = sep_mixed(si, sj, a);
+      const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+      const int3 ds = make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z));
+      PairOut<float> o;
+      o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
+      o.e = o.w = 0.f;
+      if (PATCHY) {
+        if (r2 < a.rc2_f) o = patchy_pair_mixed<(PATCHY ? NP : 1), true>(a, ds, d, r2, Pi, i, j);
+      } else if (a.cubic) {
+        o = iso_pair_cubic(a, ds, i, j);
+      } else {
+        o = iso_pair<float>(a, d, r2, i, j);
+      }
+      const float eh = 0.5f * o.e, wh = 0.5f * o.w;
+      const bool nz = o.F.x != 0.f || o.F.y != 0.f || o.F.z != 0.f || eh != 0.f || wh != 0.f ||
+                      (PATCHY && (o.ti.x != 0.f || o.ti.y != 0.f || o.ti.z != 0.f || o.tj.x != 0.f ||
+                                  o.tj.y != 0.f || o.tj.z != 0.f));
+      if (!nz) continue;  // no interaction, no memory traffic
+      comp_atomic(fhi + j, flo + j, make_float4(-o.F.x, -o.F.y, -o.F.z, eh), wh);
+      if (PATCHY)
+        comp_atomic(newton_copy(a, 2, c) + j, newton_copy(a, 3, c) + j, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f), 0.f);
+      comp_add(F, o.F);
+      if (PATCHY) comp_add(T, o.ti);
+      e += eh;
+      w += wh;
+    }
+    cur = nxt;
+  }
+  a.force[i] = make_double4_32a((double)F.s[0] + (double)F.lo[0], (double)F.s[1] + (double)F.lo[1],
+                                (double)F.s[2] + (double)F.lo[2], (double)e);
+  a.virial[i] = (double)w;
+  if (PATCHY)
+    a.torque[i] = make_double4_32a((double)T.s[0] + (double)T.lo[0], (double)T.s[1] + (double)T.lo[1],
+                                   (double)T.s[2] + (double)T.lo[2], 0.0);
+}
+
+template <bool PATCHY, int NP>
+__global__ void __launch_bounds__(256) k_vertex_newton_mixed(KArgs a) {
+  vertex_newton_mixed_body<PATCHY, NP>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// FP64 copies: forces and half energies double[m][n][4], half virials double[m][n], torques
+// double[m][n][4] (patchy).
+__device__ __forceinline__ double* newton_copy_f64(const KArgs& a, int c) {
+  return (double*)a.copies + (size_t)c * a.n * 4;
+}
+__device__ __forceinline__ double* newton_copy_v64(const KArgs& a, int c) {
+  return (double*)a.copies + (size_t)a.force_copies * a.n * 4 + (size_t)c * a.n;
+}
+__device__ __forceinline__ double* newton_copy_t64(const KArgs& a, int c) {
+  return (double*)a.copies + (size_t)a.force_copies * a.n * 5 + (size_t)c * a.n * 4;
+}
+
+template <bool PATCHY, int NP>
+__device__ __forceinline__ void vertex_newton_fp64_body(const KArgs& a, int i) {
+  if (i >= a.n || !newton_list_current(a)) return;
+  const size_t n = (size_t)a.n;
+  const int c = i % a.force_copies;
+  double* fc = newton_copy_f64(a, c);
+  double* vc = newton_copy_v64(a, c);
+  double* tc = newton_copy_t64(a, c);
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // F(3), T(3), e, w
+  const double4_32a pi = a.pos[i];
+  const int cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
+  const int ng = (cnt + 3) >> 2;
+  const int4* nb4 = (const int4*)a.nbr + i;
+  Patches<double, (PATCHY ? NP : 1)> Pi;
+  if (PATCHY) Pi = load_patches<(PATCHY ? NP : 1)>(a, i, 0.0);
+  int4 cur = load_group(nb4, 0, ng, n);
+  for (int g = 0; g < ng; g++) {
+    const int4 nxt = load_group(nb4, g + 1, ng, n);
+    int jj[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (4 * g + u >= cnt || (unsigned)jj[u] >= (unsigned)a.n) jj[u] = -1;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int j = jj[u];
+      if (j < 0) continue;
+      const Vec3<double> d = sep_fp64(pi, a.pos[j], a);
+      const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+      PairOut<double> o;
+      o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
+      o.e = o.w = 0.0;
+      if (PATCHY) {
+        if (r2 < a.rc2_d) o = patchy_pair<(PATCHY ? NP : 1), true>(a, d, r2, Pi, i, j);
+      } else {
+        o = iso_pair<double>(a, d, r2, i, j);
+      }
+      const double eh = 0.5 * o.e, wh = 0.5 * o.w;
+      const bool nz = o.F.x != 0.0 || o.F.y != 0.0 || o.F.z != 0.0 || eh != 0.0 || wh != 0.0 ||
+                      (PATCHY && (o.ti.x != 0.0 || o.ti.y != 0.0 || o.ti.z != 0.0 || o.tj.x != 0.0 ||
+                                  o.tj.y != 0.0 || o.tj.z != 0.0));
+      if (!nz) continue;
+      double* fj = fc + 4 * (size_t)j;
+      atomicAdd(fj + 0, -o.F.x); atomicAdd(fj + 1, -o.F.y); atomicAdd(fj + 2, -o.F.z); atomicAdd(fj + 3, eh);
+      atomicAdd(vc + j, wh);
+      if (PATCHY) {
+        double* tj = tc + 4 * (size_t)j;
+        atomicAdd(tj + 0, o.tj.x); atomicAdd(tj + 1, o.tj.y); atomicAdd(tj + 2, o.tj.z);
+      }
+      acc[0] += o.F.x; acc[1] += o.F.y; acc[2] += o.F.z;
+      acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z;
+      acc[6] += eh; acc[7] += wh;
+    }
+    cur = nxt;
+  }
+  a.force[i] = make_double4_32a(acc[0], acc[1], acc[2], acc[6]);
+  a.virial[i] = acc[7];
+  if (PATCHY) a.torque[i] = make_double4_32a(acc[3], acc[4], acc[5], 0.0);
+}
+
+template <bool PATCHY, int NP>
+__global__ void __launch_bounds__(256) k_vertex_newton_fp64(KArgs a) {
+  vertex_newton_fp64_body<PATCHY, NP>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// TwoSum step of an FP32 sum s + c (c collects the rounding errors)
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
+  const float t = __fadd_rn(s, v);
+  c = __fadd_rn(c, two_sum_err(s, v, t));
+  s = t;
+}
+
+// Adds the m copies of particle i to its totals (written by the force kernel) and clears them.
+__device__ __forceinline__ void newton_finalize_one(const KArgs& a, int i) {
+  if (!(a.status[MD_STATUS_LISTS] & MD_LIST_NEWTON)) return;  // the force kernel wrote nothing
+  const int m = a.force_copies;
+  const bool patchy = a.model == MD_PATCHY;
+  if (a.precision == MD_MIXED) {
+    float fs[4] = {0.f, 0.f, 0.f, 0.f}, fc[4] = {0.f, 0.f, 0.f, 0.f}, vs = 0.f, vc = 0.f;
+    float ts[3] = {0.f, 0.f, 0.f}, tcm[3] = {0.f, 0.f, 0.f};
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < m; c++) {
+      float4* hp = newton_copy(a, 0, c) + i;
+      float4* lp = newton_copy(a, 1, c) + i;
+      const float4 h = *hp, l = *lp;
+      *hp = z;
+      *lp = z;
+      two_sum_acc(fs[0], fc[0], h.x); two_sum_acc(fs[1], fc[1], h.y); two_sum_acc(fs[2], fc[2], h.z);
+      two_sum_acc(fs[3], fc[3], h.w);
+      fc[0] += l.x; fc[1] += l.y; fc[2] += l.z;
+      two_sum_acc(vs, vc, l.w);
+      if (patchy) {
+        float4* thp = newton_copy(a, 2, c) + i;
+        float4* tlp = newton_copy(a, 3, c) + i;
+        const float4 th = *thp, tl = *tlp;
+        *thp = z;
+        *tlp = z;
+        two_sum_acc(ts[0], tcm[0], th.x); two_sum_acc(ts[1], tcm[1], th.y); two_sum_acc(ts[2], tcm[2], th.z);
+        tcm[0] += tl.x; tcm[1] += tl.y; tcm[2] += tl.z;
+      }
+    }
+    double4_32a F = a.force[i];
+    F.x += (double)fs[0] + (double)fc[0];
+    F.y += (double)fs[1] + (double)fc[1];
+    F.z += (double)fs[2] + (double)fc[2];
+    F.w += (double)fs[3] + (double)fc[3];
+    a.force[i] = F;
+    a.virial[i] += (double)vs + (double)vc;
+    if (patchy) {
+      double4_32a T = a.torque[i];
+      T.x += (double)ts[0] + (double)tcm[0];
+      T.y += (double)ts[1] + (double)tcm[1];
+      T.z += (double)ts[2] + (double)tcm[2];
+      a.torque[i] = T;
+    }
+  } else {
+    double4_32a F = a.force[i];
+    double W = a.virial[i];
+    double4_32a T = patchy ? a.torque[i] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    for (int c = 0; c < m; c++) {
+      double4_32a* fp = (double4_32a*)newton_copy_f64(a, c) + i;
+      double* vp = newton_copy_v64(a, c) + i;
+      const double4_32a f = *fp;
+      F.x += f.x; F.y += f.y; F.z += f.z; F.w += f.w;
+      W += *vp;
+      *fp = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      *vp = 0.0;
+      if (patchy) {
+        double4_32a* tp = (double4_32a*)newton_copy_t64(a, c) + i;
+        const double4_32a t = *tp;
+        T.x += t.x; T.y += t.y; T.z += t.z;
+        *tp = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+      }
+    }
+    a.force[i] = F;
+    a.virial[i] = W;
+    if (patchy) a.torque[i] = T;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Edge-based evaluation with a per-edge store (Sec. Methods, the general form of the edge
+// approach): pass 1, one thread per half-list pair, writes the pair's results to its slot; pass 2,
+// one thread per particle, sums the slots of its own pairs and those where it is the partner
+// (through the by-partner index) in a fixed order.  No atomics, deterministic.
+// Store blocks of max_pairs entries: A = (F_ij, e_ij), B = (tau_i, w_ij), C = (tau_j, 0) (patchy).
+// ------------------------------------------------------------------------------------------------
+
+template <bool PATCHY, int NP>
+__device__ __forceinline__ void edge_store_mixed_one(const KArgs& a, int64_t k) {
+  float4* A = (float4*)a.estore;
+  float4* Bk = A + a.max_pairs;
+  float4* C = A + 2 * a.max_pairs;
+  int2 p = __ldcs(a.pairs + k);
+  PairOut<float> o;
+  o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
+  o.e = o.w = 0.f;
+  if ((unsigned)p.x < (unsigned)a.n && (unsigned)p.y < (unsigned)a.n) {
+    const uint4 si = __ldg(a.fxp + p.x), sj = __ldg(a.fxp + p.y);
+    const Vec3<float> d = sep_mixed(si, sj, a);
+    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    const int3 ds = make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z));
+    if (PATCHY) {
+      if (r2 < a.rc2_f) {
+        const IPatches<(PATCHY ? NP : 1)> Pi = load_ipatches<(PATCHY ? NP : 1)>(a, p.x);
+        o = patchy_pair_mixed<(PATCHY ? NP : 1), true>(a, ds, d, r2, Pi, p.x, p.y);
+      }
+    } else if (a.cubic) {
+      o = iso_pair_cubic(a, ds, p.x, p.y);
+    } else {
+      o = iso_pair<float>(a, d, r2, p.x, p.y);
+    }
+  }
+  __stcs(A + k, make_float4(o.F.x, o.F.y, o.F.z, o.e));
+  __stcs(Bk + k, make_float4(o.ti.x, o.ti.y, o.ti.z, o.w));
+  if (PATCHY) __stcs(C + k, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f));
+}
+
+template <bool PATCHY, int NP>
+__device__ __forceinline__ void edge_store_fp64_one(const KArgs& a, int64_t k) {
+  double4_32a* A = (double4_32a*)a.estore;
+  double4_32a* Bk = A + a.max_pairs;
+  double4_32a* C = A + 2 * a.max_pairs;
+  int2 p = __ldcs(a.pairs + k);
+  PairOut<double> o;
+  o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
+  o.e = o.w = 0.0;
+  if ((unsigned)p.x < (unsigned)a.n && (unsigned)p.y < (unsigned)a.n) {
+    const Vec3<double> d = sep_fp64(a.pos[p.x], a.pos[p.y], a);
+    const double r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    if (PATCHY) {
+      if (r2 < a.rc2_d) {
+        const Patches<double, (PATCHY ? NP : 1)> Pi = load_patches<(PATCHY ? NP : 1)>(a, p.x, 0.0);
+        o = patchy_pair<(PATCHY ? NP : 1), true>(a, d, r2, Pi, p.x, p.y);
+      }
+    } else {
+      o = iso_pair<double>(a, d, r2, p.x, p.y);
+    }
+  }
+  A[k] = make_double4_32a(o.F.x, o.F.y, o.F.z, o.e);
+  Bk[k] = make_double4_32a(o.ti.x, o.ti.y, o.ti.z, o.w);
+  if (PATCHY) C[k] = make_double4_32a(o.tj.x, o.tj.y, o.tj.z, 0.0);
+}
+
+template <bool PATCHY, int NP>
+__global__ void __launch_bounds__(256) k_edge_store(KArgs a) {
+  const int64_t E = min(a.half_start[a.n], a.max_pairs);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+    if (a.precision == MD_MIXED) edge_store_mixed_one<PATCHY, NP>(a, k);
+    else edge_store_fp64_one<PATCHY, NP>(a, k);
+  }
+}
+
+// Pass 2 for particle i: own pairs (+F_ij, tau_i) in list order, then pairs where i is the partner
+// (-F_ij, tau_j) in increasing position; each pair gives half its energy and virial to either side.
+__device__ __forceinline__ void edge_store_reduce_one(const KArgs& a, int i) {
+  const int64_t e0 = a.half_start[i], e1 = min(a.half_start[i + 1], a.max_pairs);
+  const int64_t p0 = a.jstart[i], p1 = a.jstart[i + 1];
+  const bool patchy = a.model == MD_PATCHY;
+  if (a.precision == MD_MIXED) {
+    const float4* A = (const float4*)a.estore;
+    const float4* Bk = A + a.max_pairs;
+    const float4* C = A + 2 * a.max_pairs;
+    Comp3 F = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    Comp3 T = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float e = 0.f, w = 0.f;
+    for (int64_t k = e0; k < e1; k++) {
+      const float4 x = __ldcs(A + k), y = __ldcs(Bk + k);
+      comp_add(F, {x.x, x.y, x.z});
+      if (patchy) comp_add(T, {y.x, y.y, y.z});
+      e += 0.5f * x.w;
+      w += 0.5f * y.w;
+    }
+    for (int64_t t = p0; t < p1; t++) {
+      const int32_t k = a.jedge[t];
+      if (k < 0) continue;
+      const float4 x = A[k], y = Bk[k];
+      comp_add(F, {-x.x, -x.y, -x.z});
+      if (patchy) {
+        const float4 z = C[k];
+        comp_add(T, {z.x, z.y, z.z});
+      }
+      e += 0.5f * x.w;
+      w += 0.5f * y.w;
+    }
+    a.force[i] = make_double4_32a((double)F.s[0] + (double)F.lo[0], (double)F.s[1] + (double)F.lo[1],
+                                  (double)F.s[2] + (double)F.lo[2], (double)e);
+    a.virial[i] = (double)w;
+    if (patchy)
+      a.torque[i] = make_double4_32a((double)T.s[0] + (double)T.lo[0], (double)T.s[1] + (double)T.lo[1],
+                                     (double)T.s[2] + (double)T.lo[2], 0.0);
+  } else {
+    const double4_32a* A = (const double4_32a*)a.estore;
+    const double4_32a* Bk = A + a.max_pairs;
+    const double4_32a* C = A + 2 * a.max_pairs;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = e0; k < e1; k++) {
+      const double4_32a x = A[k], y = Bk[k];
+      acc[0] += x.x; acc[1] += x.y; acc[2] += x.z;
+      acc[3] += y.x; acc[4] += y.y; acc[5] += y.z;
+      acc[6] += 0.5 * x.w; acc[7] += 0.5 * y.w;
+    }
+    for (int64_t t = p0; t < p1; t++) {
+      const int32_t k = a.jedge[t];
+      if (k < 0) continue;
+      const double4_32a x = A[k], y = Bk[k];
+      acc[0] -= x.x; acc[1] -= x.y; acc[2] -= x.z;
+      if (patchy) {
+        const double4_32a z = C[k];
+        acc[3] += z.x; acc[4] += z.y; acc[5] += z.z;
+      }
+      acc[6] += 0.5 * x.w; acc[7] += 0.5 * y.w;
+    }
+    a.force[i] = make_double4_32a(acc[0], acc[1], acc[2], acc[6]);
+    a.virial[i] = acc[7];
+    if (patchy) a.torque[i] = make_double4_32a(acc[3], acc[4], acc[5], 0.0);
   }
 }
 

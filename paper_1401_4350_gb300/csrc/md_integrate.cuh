@@ -8,16 +8,25 @@ namespace mdgb {
 
 constexpr int kIntBlock = 256;
 
-__device__ __forceinline__ float warp_sum(float v) {
+__device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
   return v;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// Warp total of the unevaluated sums s + c of all lanes, with the rounding of every addition kept
+// (TwoSum): FP32 operations only, since FP64 ones are scarce on this GPU.
+__device__ __forceinline__ double warp_sum_ff(float s, float c) {
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-  return v;
+  for (int d = 16; d > 0; d >>= 1) {
+    const float o = __shfl_xor_sync(0xffffffffu, s, d), oc = __shfl_xor_sync(0xffffffffu, c, d);
+    const float t = __fadd_rn(s, o);
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(o, bb));
+    c = __fadd_rn(__fadd_rn(c, oc), err);
+    s = t;
+  }
+  return (double)s + (double)c;
 }
 
 // Quaternion product a (x) b, (w, x, y, z) stored as double4_32a (x=w, y=x, z=y, w=z).
@@ -193,11 +202,13 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
     __shared__ double sred[kIntBlock / 32][4];
     double s0, s1, s2, s3;
     if (mixed) {
-      // kinetic terms in FP32 within the warp; energies and virial arrive as FP64 values
-      s0 = (double)warp_sum(ktf);
-      s1 = (double)warp_sum(krf);
-      s2 = warp_sum(u);
-      s3 = warp_sum(w);
+      // compensated FP32 sums within the warp; U_i and W_i arrive as FP64 values and enter as
+      // (hi, lo) FP32 pairs (exact for the isotropic vertex path, where they are FP32 values)
+      const float uh = (float)u, wh = (float)w;
+      s0 = warp_sum_ff(ktf, 0.f);
+      s1 = patchy ? warp_sum_ff(krf, 0.f) : 0.0;
+      s2 = warp_sum_ff(uh, (float)(u - (double)uh));
+      s3 = warp_sum_ff(wh, (float)(w - (double)wh));
     } else {
       s0 = warp_sum(kt); s1 = warp_sum(kr); s2 = warp_sum(u); s3 = warp_sum(w);
     }

@@ -67,6 +67,14 @@ struct KArgs {
   float inv_unit_f;                      // 1 / u
   float sig2_u, rwca2_u, rwca2_lo_u, rwca2_hi_u;
   float u2_over_delta2;                  // u^2 / delta^2 (patchy, cubic box)
+  // cubic boxes, isotropic mixed vertex kernel: r^2 in units u^2 2^r2_shift, taken from the exact
+  // 64-bit integer sum of squares shifted right by r2_shift (the high word saturated at r2_hi_max)
+  int32_t r2_shift;
+  uint32_t r2_hi_max;
+  float nsig2_s;                         // -sigma^2 in those units
+  float rwca2_s, rwca2_band_s;           // cut-off^2 and the half-width of its FP64-decided band
+  float rwca2_lo_s, rwca2_hi_s;          // the band itself
+  float fscale_hi, fscale_lo;            // -24 eps / (u 2^r2_shift) as an unevaluated FP32 sum
   double rwca2_lo_d, rwca2_hi_d;
   // patchy
   double inv_delta2_d, eps_p_d, pgain_d;  // 1/delta^2, eps_p, 5 eps_p / delta^2
@@ -88,6 +96,7 @@ struct KArgs {
   int32_t* status;
   double* energy;
   int32_t* cell_start;
+  const int32_t* cell_rank;  // Hilbert order: position of each row-major cell id along the curve (else null)
   uint4* fxp;
   uint4* fxp_build;
   void* patch_lab;
@@ -99,6 +108,11 @@ struct KArgs {
   double* virial;        // W_i result
   double4_32a* torque;   // (tau, 0) result, patchy
   float4* acc;           // mixed edge accumulators: F hi [n], F lo [n], tau hi [n], tau lo [n]
+  void* copies;          // Newton-vertex reaction copies (layout of md_ws_layout.copies)
+  int32_t force_copies;  // m
+  void* estore;          // per-edge store (A, B, C blocks of max_pairs entries), edge_store = 1
+  int64_t* jstart;       // by-partner index rows [n + 1]
+  int32_t* jedge;        // by-partner index entries [max_pairs]
   double* trace;
   uint32_t* scr_words;   // SCR_WORDS control words
   double* block_partials;  // [max_blocks][8] FP64 partial sums of the integrate kernels
@@ -123,6 +137,8 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // Launch wrappers (return cudaGetLastError() after the launch).
 cudaError_t launch_build_cells(const KArgs& a, const uint32_t* gate, cudaStream_t st);
+uint64_t hilbert_key3(uint32_t x, uint32_t y, uint32_t z, int bits);
+void hilbert_cell_ranks(const int nc[3], int32_t* rank);
 cudaError_t launch_build_verlet(const KArgs& a, int which, const uint32_t* gate, cudaStream_t st);
 cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st);
 // mode: 0 = first half step (kick + drift), 1 = middle (kick, energies, kick, drift), 2 = last (kick,

@@ -70,6 +70,10 @@ extern "C" int md_build_cells_static(const md_params* p, md_state* s, int32_t* c
                                      void* patch_lab, void* stream) {
   int rc = check_params_only(p);
   if (rc != MD_OK) return rc;
+  if (p->cell_order != MD_ORDER_ROWS) {
+    set_error("md_build_cells_static: only MD_ORDER_ROWS (the Hilbert table lives in a workspace)");
+    return MD_ERR_INVALID;
+  }
   if (p->n > kStaticMaxN) {
     set_error("md_build_cells_static: n = %d exceeds MD_STATIC_MAX_N = %d (use md_build_cells with a workspace)",
               p->n, kStaticMaxN);

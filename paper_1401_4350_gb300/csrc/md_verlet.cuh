@@ -8,7 +8,7 @@ namespace mdgb {
 
 // Builds the full-list row of slot i (i < a.n) and returns its length; the caller reduces the
 // lengths of its warp into MD_STATUS_NEED_NEIGH.
-__device__ __forceinline__ int verlet_full_one(const KArgs& a, int i) {
+__device__ __forceinline__ int verlet_full_one(const KArgs& a, int i, bool newton = false) {
   int cnt = 0;
   {
     const uint4 si = a.fxp[i];
@@ -33,7 +33,8 @@ __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i) {
           int x = ci[0] + dx;
           x += (x < 0) ? a.ncell[0] : 0;
           x -= (x >= a.ncell[0]) ? a.ncell[0] : 0;
-          const int c = (z * a.ncell[1] + y) * a.ncell[0] + x;
+          int c = (z * a.ncell[1] + y) * a.ncell[0] + x;
+          if (a.cell_rank) c = a.cell_rank[c];
           const int b = a.cell_start[c], e = a.cell_start[c + 1];
           for (int j = b; j < e; j++) {
             if (j == i) continue;
@@ -44,6 +45,8 @@ __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i) {
             float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
             bool in = r2 < a.rv2_lo;
             if (!in && r2 < a.rv2_hi) in = exact_r2(a.pos[i], a.pos[j], a) < a.rv2_d;
+            // Newton list: the pair goes to i when i < j and i + j is odd, or i > j and i + j even
+            if (newton) in = in && ((i < j) == (((i + j) & 1) != 0));
             if (in) {
               if (cnt < a.max_neigh) a.nbr[nbr_index(cnt, i, n)] = j;
               cnt++;
@@ -84,6 +87,42 @@ __device__ __forceinline__ void verlet_half_one(const KArgs& a, int i) {
       if (w < a.max_pairs) a.pairs[w] = make_int2(i, j);
       w++;
     }
+  }
+}
+
+// ---- by-partner index of the half list (per-edge store path) ------------------------------------
+// Row j lists the positions k of the half-list pairs (i, j), i < j.  Their number is the part of j's
+// full row below j; positions are placed with atomics and each row is then sorted, so the index, and
+// the summation order that follows it, is deterministic.
+
+__device__ __forceinline__ void jindex_count_one(const KArgs& a, int j) {
+  const int cnt = min(a.nbr_count[j], a.max_neigh);
+  a.count_tmp[j] = cnt - (int)(a.half_start[j + 1] - a.half_start[j]);
+}
+
+// Pair k of the half list into its partner's row (fill counters in a.rank, zeroed before).
+__device__ __forceinline__ void jindex_scatter_one(const KArgs& a, int64_t k) {
+  const int j = a.pairs[k].y;
+  if ((unsigned)j >= (unsigned)a.n) return;
+  const int slot = atomicAdd(a.rank + j, 1);
+  const int64_t w = a.jstart[j] + slot;
+  if (w < a.jstart[j + 1]) a.jedge[w] = (int32_t)k;
+}
+
+// Increasing k (and so increasing i) within row j; rows are short (insertion sort).  Slots that no
+// pair reached (a truncated half list after an overflow) hold -1.
+__device__ __forceinline__ void jindex_sort_one(const KArgs& a, int j) {
+  const int64_t b = a.jstart[j], e = a.jstart[j + 1];
+  const int64_t filled = b + a.rank[j];
+  for (int64_t w = filled; w < e; w++) a.jedge[w] = -1;
+  for (int64_t k = b + 1; k < min(filled, e); k++) {
+    const int32_t v = a.jedge[k];
+    int64_t m = k - 1;
+    while (m >= b && a.jedge[m] > v) {
+      a.jedge[m + 1] = a.jedge[m];
+      m--;
+    }
+    a.jedge[m + 1] = v;
   }
 }
 

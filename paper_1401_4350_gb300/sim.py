@@ -25,7 +25,8 @@ def default_capacities(system: System, slack: float = 1.6):
 
 
 def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, tpp: int = 1, block: int = 0,
-                trace_capacity: int = 0, energy_every: int = 1) -> B.md_params:
+                trace_capacity: int = 0, energy_every: int = 1, force_copies: int = 0,
+                cell_order: int = 0, edge_store: int = 0) -> B.md_params:
     mn, mp = default_capacities(system)
     p = B.md_params()
     p.n = system.n
@@ -38,6 +39,9 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
     p.block_size = block
     p.trace_capacity = trace_capacity
     p.energy_every = energy_every
+    p.force_copies = force_copies
+    p.cell_order = cell_order
+    p.edge_store = edge_store
     for c in range(3):
         p.box[c] = float(system.box[c])
     p.rc, p.skin, p.dt, p.mass, p.inertia = system.rc, system.skin, system.dt, system.mass, system.inertia
@@ -50,9 +54,11 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
 
 class Simulation:
     def __init__(self, system: System, precision: int = B.MD_MIXED, max_neigh=None, max_pairs=None, tpp: int = 1,
-                 block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None, energy_every: int = 1):
+                 block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None, energy_every: int = 1,
+                 force_copies: int = 0, cell_order: int = 0, edge_store: int = 0):
         self.system = system
-        self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity, energy_every)
+        self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity, energy_every,
+                                  force_copies, cell_order, edge_store)
         rc = B.md_check_params(self.params)
         if rc != B.MD_OK:
             raise B.MDError(rc, B.last_error())
@@ -108,6 +114,12 @@ class Simulation:
 
     def forces_edge(self):
         B.md_forces_edge(self.params, self.state(), self.ws, self._st())
+
+    def forces_vertex_newton(self):
+        B.md_forces_vertex_newton(self.params, self.state(), self.ws, self._st())
+
+    def forces_edge_store(self):
+        B.md_forces_edge_store(self.params, self.state(), self.ws, self._st())
 
     def prepare(self, path=B.MD_VERTEX):
         B.md_prepare(self.params, self.state(), self.ws, path, self._st())

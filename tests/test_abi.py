@@ -3,6 +3,7 @@ validates its arguments on the host and lays the workspace out consistently."""
 import ctypes
 import os
 
+import numpy as np
 import pytest
 
 from paper_1401_4350_gb300 import binding as B
@@ -28,7 +29,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_abi_version(lib):
-    assert B.md_abi_version() == 1
+    assert B.md_abi_version() == 2
 
 
 def _lj_params(n=4000, precision=B.MD_MIXED):
@@ -47,7 +48,8 @@ def _lj_params(n=4000, precision=B.MD_MIXED):
     ("skin", 0.0, "skin"),
     ("dt", -1.0, "dt"),
     ("energy_every", -2, "energy_every"),
-    ("reserved", 1, "reserved"),
+    ("force_copies", -1, "force_copies"),
+    ("force_copies", 65, "force_copies"),
 ])
 def test_invalid_params_rejected(lib, field, value, needle):
     p = _lj_params()
@@ -87,7 +89,7 @@ def test_workspace_layout(lib, precision, kind):
     assert L.total == B.md_workspace_bytes(p) > 0
     offs = [getattr(L, f) for f in ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr",
                                     "nbr_count", "half_start", "pairs", "force", "virial", "torque",
-                                    "acc", "trace", "scratch")]
+                                    "acc", "copies", "estore", "jstart", "jedge", "trace", "scratch")]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and len(set(offs)) == len(offs)
     assert L.force_elem == 8
@@ -123,3 +125,102 @@ def test_struct_layouts_match_c(lib, tmp_path):
         assert int(out[st]) == ctypes.sizeof(cls), st
         for nm in fields[st]:
             assert int(out[f"{st}.{nm}"]) == getattr(cls, nm).offset, (st, nm)
+
+
+@pytest.mark.parametrize("precision", [B.MD_FP64, B.MD_MIXED])
+@pytest.mark.parametrize("kind", ["lj", "patchy"])
+def test_newton_copies_region(lib, precision, kind):
+    """force_copies = m reserves m reaction copies per particle (layout documented in md.h)."""
+    s = systems.make_lj(4000, 0.85, seed=5) if kind == "lj" else systems.make_patchy(2000, 0.3, seed=5)
+    p = make_params(s, precision)
+    L0 = B.md_workspace_layout(p)
+    assert L0.estore - L0.copies <= 256  # no copies without force_copies
+    p.force_copies = 16
+    L = B.md_workspace_layout(p)
+    per = (16 * (4 if kind == "patchy" else 2)) if precision == B.MD_MIXED else (32 + 8 + (32 if kind == "patchy" else 0))
+    assert L.estore - L.copies >= 16 * s.n * per
+    assert L.total - L0.total >= 16 * s.n * per - 256
+
+
+def test_newton_path_needs_copies(lib):
+    """The Newton path is refused on the host when the workspace has no force copies."""
+    p = _lj_params()
+    fake = 1 << 20  # aligned non-null addresses: validation fails before any device access
+    st = B.md_state(fake, fake, 0, 0, fake)
+    assert B.load().md_forces_vertex_newton(ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(fake), None) == B.MD_ERR_INVALID
+    assert "force_copies" in B.last_error()
+    assert B.load().md_prepare(ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(fake), 2, None) == B.MD_ERR_INVALID
+    assert B.load().md_prepare(ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(fake), 3, None) == B.MD_ERR_INVALID
+    assert "edge_store" in B.last_error()
+    assert B.load().md_forces_edge_store(ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(fake), None) == B.MD_ERR_INVALID
+    assert B.load().md_prepare(ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(fake), 4, None) == B.MD_ERR_INVALID
+    assert "path must be" in B.last_error()
+
+
+def _grid_params(ncell):
+    p = _lj_params(500)
+    p.n = 200000  # the grid is capped at 4 n + 27 cells; no memory is allocated here
+    rv = p.rc + p.skin
+    for c in range(3):
+        p.box[c] = (ncell[c] + 0.5) * rv
+    p.cell_order = B.MD_ORDER_HILBERT
+    return p
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_hilbert_cell_order_is_a_continuous_curve_on_power_of_two_grids(lib, k):
+    """On a 2^k cube the Hilbert curve visits every cell once, starts in the corner cell, and steps to a
+    face neighbour each time (the defining property of the curve)."""
+    n = 2 ** k
+    p = _grid_params((n, n, n))
+    L = B.md_workspace_layout(p)
+    assert tuple(L.ncell) == (n, n, n)
+    rank = B.md_cell_order(p)
+    assert np.array_equal(np.sort(rank), np.arange(n ** 3))
+    order = np.argsort(rank)
+    xyz = np.stack([order % n, (order // n) % n, order // (n * n)], 1)
+    assert tuple(xyz[0]) == (0, 0, 0)
+    steps = np.abs(np.diff(xyz, axis=0)).sum(1)
+    assert (steps == 1).all()
+
+
+@pytest.mark.parametrize("ncell", [(3, 3, 3), (5, 7, 6), (38, 38, 38), (13, 3, 9)])
+def test_hilbert_cell_order_is_a_local_permutation(lib, ncell):
+    """Any grid: a permutation of the cells whose consecutive cells are close (the curve through the
+    enclosing 2^b cube skips the missing cells); row-major order is the identity."""
+    p = _grid_params(ncell)
+    L = B.md_workspace_layout(p)
+    assert tuple(L.ncell) == ncell
+    rank = B.md_cell_order(p)
+    total = int(np.prod(ncell))
+    assert np.array_equal(np.sort(rank), np.arange(total))
+    order = np.argsort(rank)
+    nx, ny, nz = ncell
+    xyz = np.stack([order % nx, (order // nx) % ny, order // (nx * ny)], 1)
+    steps = np.abs(np.diff(xyz, axis=0)).sum(1)
+    assert steps.mean() < 1.6
+    p.cell_order = B.MD_ORDER_ROWS
+    assert np.array_equal(B.md_cell_order(p), np.arange(total))
+
+
+@pytest.mark.parametrize("precision", [B.MD_FP64, B.MD_MIXED])
+@pytest.mark.parametrize("kind", ["lj", "patchy"])
+def test_edge_store_regions(lib, precision, kind):
+    """edge_store = 1 reserves the A, B (and, patchy, C) blocks of max_pairs entries and the by-partner
+    index; without it the regions are empty."""
+    s = systems.make_lj(4000, 0.85, seed=5) if kind == "lj" else systems.make_patchy(2000, 0.3, seed=5)
+    p = make_params(s, precision)
+    L0 = B.md_workspace_layout(p)
+    assert L0.jedge - L0.estore <= 512
+    p.edge_store = 1
+    L = B.md_workspace_layout(p)
+    elem = 16 if precision == B.MD_MIXED else 32
+    blocks = 3 if kind == "patchy" else 2
+    assert L.jstart - L.estore >= elem * blocks * p.max_pairs
+    assert L.jedge - L.jstart >= 8 * (s.n + 1)
+    assert L.trace - L.jedge >= 4 * p.max_pairs
+    p.edge_store = 2
+    assert B.md_check_params(p) == B.MD_ERR_INVALID
+    p.edge_store = 1
+    p.max_pairs = 1 << 31
+    assert B.md_check_params(p) == B.MD_ERR_INVALID
