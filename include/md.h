@@ -62,7 +62,9 @@ enum {
 enum {
   MD_LJ = 0,      /* Lennard-Jones, Eq. 1, cut and energy-shifted at rc                        */
   MD_WCA = 1,     /* Lennard-Jones cut at 2^(1/6) sigma and shifted by +eps (purely repulsive)  */
-  MD_PATCHY = 2   /* WCA core + patch attraction -eps_p exp(-(r_pp/delta)^10 / 2), cf. Eqs. 2-4 */
+  MD_PATCHY = 2,  /* WCA core + patch attraction -eps_p exp(-(r_pp/delta)^10 / 2), cf. Eqs. 2-4 */
+  MD_PATCHY_POW = 3 /* the paper's patchy form (Eqs. 2-4): (sigma/r)^200 core + the same patch
+                       attraction, each patch pair truncated at r_pp >= patch_rc                */
 };
 
 /* Arithmetic of the pair forces. */
@@ -83,6 +85,16 @@ enum { MD_ORDER_ROWS = 0, MD_ORDER_HILBERT = 1 };
 /* Which neighbour lists md_build_verlet writes.  MD_LIST_NEWTON is the half list of the
  * MD_VERTEX_NEWTON path in the full list's storage (so it replaces the full list). */
 enum { MD_LIST_FULL = 1, MD_LIST_HALF = 2, MD_LIST_BOTH = 3, MD_LIST_NEWTON = 4 };
+
+/* Reported in MD_STATUS_LISTS (not requested): the full list is held in the block-local format, 16-bit
+ * entries indexing the halo of each block of MD_LOCAL_BLOCK slots (see md_ws_layout.local_tab).
+ * md_build_verlet(MD_LIST_FULL) writes it when list_format = MD_FORMAT_LOCAL, for mixed-precision
+ * LJ/WCA in a cubic box with one thread per particle, when the mean list length rv^3 rho 4 pi / 3 is
+ * at least 16. */
+enum { MD_FORMAT_GLOBAL = 0, MD_FORMAT_LOCAL = 1 };
+#define MD_LIST_FULL_LOCAL 8
+#define MD_LOCAL_BLOCK 256
+#define MD_LOCAL_MAX_CELLS 512
 
 #define MD_MAX_PATCH 4
 
@@ -126,6 +138,11 @@ typedef struct md_params {
                                     MD_ORDER_HILBERT (1): along a Hilbert curve through the cells */
   int32_t edge_store;            /* 1: reserve the per-edge force store of MD_EDGE_STORE and build its
                                     by-partner index with the half list; 0: not used              */
+  int32_t list_format;           /* MD_FORMAT_GLOBAL (0): full-list entries are int32 slots;
+                                    MD_FORMAT_LOCAL (1): md_build_verlet(MD_LIST_FULL) writes 16-bit
+                                    halo positions per block of MD_LOCAL_BLOCK slots when the system
+                                    qualifies (see MD_LIST_FULL_LOCAL), else int32 slots            */
+  int32_t reserved;              /* must be 0                                                     */
   double box[3];                 /* periodic box edges; each must exceed 2 rv                    */
   double rc;                     /* centre-centre cut-off (LJ: 2.5 sigma; WCA: 2^(1/6) sigma)    */
   double skin;                   /* Verlet skin rs > 0; rv = rc + rs                             */
@@ -135,6 +152,16 @@ typedef struct md_params {
   double eps, sigma;             /* Lennard-Jones parameters                                     */
   double eps_p, delta;           /* patchy: patch strength and range                            */
   double patch[MD_MAX_PATCH][3]; /* patchy: body-frame patch-site offsets from the centre        */
+  double patch_rc;               /* MD_PATCHY_POW: patch-pair cut-off (> 0); ignored otherwise    */
+  double kT;                     /* thermostat temperature (thermostat_every > 0)                */
+  double thermostat_prob;        /* probability that a particle's momenta are redrawn per thermostat step */
+  int32_t thermostat_every;      /* 0: NVE.  Else md_step_verlet redraws, at the start of every step
+                                    s > 0 with s % thermostat_every == 0, each particle's velocity
+                                    (and angular momentum) with probability thermostat_prob from the
+                                    Maxwell-Boltzmann distribution at kT (Sec. Methods: Brownian
+                                    dynamics, NVT).  Random numbers: Philox4x32-10 with counter
+                                    (s, original id, stream 0/1, 0) and key (seed, 0), Box-Muller.  */
+  uint32_t seed;                 /* key of the thermostat's random numbers                       */
 } md_params;
 
 /* Primary state: FP64 device arrays owned by the caller, [n][4] each. */
@@ -157,7 +184,9 @@ typedef struct md_ws_layout {
   size_t fxp;            /* uint32[n][4]: positions as fractions of the box edge times 2^32   */
   size_t fxp_build;      /* uint32[n][4]: the same at the last Verlet build                   */
   size_t patch_lab;      /* float[n][MD_MAX_PATCH][4]: lab-frame patch sites (patchy, mixed)  */
-  size_t nbr;            /* int32[ceil(max_neigh/4)][n][4]: full list; entry k of slot i at ((k/4)*n+i)*4+k%4 */
+  size_t nbr;            /* int32[ceil(max_neigh/4)][n][4]: full list; entry k of slot i at ((k/4)*n+i)*4+k%4.
+                            Block-local format: uint16 at the same entry position; the Newton list:
+                            the same layout with the rows of md_forces_vertex_newton              */
   size_t nbr_count;      /* int32[n]: full-list length per slot                               */
   size_t half_start;     /* int64[n + 1]: half-list row offsets                               */
   size_t pairs;          /* int32[max_pairs][2]: half list (i, j), i < j, sorted by i          */
@@ -176,6 +205,11 @@ typedef struct md_ws_layout {
   size_t jstart;         /* int64[n + 1]: rows of the by-partner index (edge_store = 1)          */
   size_t jedge;          /* int32[max_pairs]: half-list positions k with pairs[k].j = i, row i in
                             increasing partner order (edge_store = 1)                           */
+  size_t local_tab;      /* block-local full list: per block of MD_LOCAL_BLOCK slots an int32[4]
+                            header (U cells, H halo slots, status, 0) and int32[MD_LOCAL_MAX_CELLS][2]
+                            (first slot of the cell, its offset in the halo) in halo order; entry v
+                            of a row is slot first + (v - offset) of the cell whose range holds v.
+                            Empty unless the format can be chosen                                */
   size_t trace;          /* double[trace_capacity][4]: (step, K, U, W) rows of md_step_verlet */
   size_t scratch;        /* internal scratch                                                  */
 } md_ws_layout;

@@ -9,6 +9,9 @@ Functions (each follows the passage cited in ``md_oracle.c``):
   forces(pos, model, quat=None, use_cells=True)   -> F, T, E, (U, W, n_pairs_in_rc)
   pairs(pos, box, rv, use_cells=True)             -> (N_pairs, 2) int array, i < j, sorted
   run_nve(pos, vel, model, dt, nsteps, ...)       -> per-step {K_trans, K_rot, U, W}
+  run(pos, vel, model, dt, nsteps, thermostat=.., step0=..) -> the same with the momentum-refresh thermostat
+  philox4x32(ctr, key)                            -> Philox4x32-10 output words
+  thermostat_draw(seed, step, particle)           -> (selection uniform, six normals)
   cell_dims(box, rv)                              -> cells per axis the oracle uses
 """
 from __future__ import annotations
@@ -24,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "md_oracle.c")
 _LIB = os.path.join(_HERE, "_md_oracle.so")
 
-LJ, WCA, PATCHY = 0, 1, 2
+LJ, WCA, PATCHY, PATCHY_POW = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -40,12 +43,33 @@ def build(force: bool = False) -> str:
 class _Model(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("n_patch", ctypes.c_int32), ("box", ctypes.c_double * 3),
                 ("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("rc", ctypes.c_double),
-                ("eps_p", ctypes.c_double), ("delta", ctypes.c_double), ("patch", (ctypes.c_double * 3) * 8)]
+                ("eps_p", ctypes.c_double), ("delta", ctypes.c_double), ("patch", (ctypes.c_double * 3) * 8),
+                ("patch_rc", ctypes.c_double)]
+
+
+class _Thermostat(ctypes.Structure):
+    _fields_ = [("every", ctypes.c_int32), ("seed", ctypes.c_uint32), ("prob", ctypes.c_double),
+                ("kT", ctypes.c_double)]
+
+
+@dataclass
+class Thermostat:
+    """Momentum refresh: at steps s > 0 with s % every == 0 each particle is redrawn with probability prob."""
+    every: int
+    prob: float
+    kT: float
+    seed: int = 0
+
+    def to_c(self) -> _Thermostat:
+        t = _Thermostat()
+        t.every, t.seed, t.prob, t.kT = int(self.every), int(self.seed) & 0xFFFFFFFF, float(self.prob), float(self.kT)
+        return t
 
 
 @dataclass
 class Model:
-    """Pair model: LJ (rc = 2.5 sigma), WCA, or patchy (WCA core + patch attraction)."""
+    """Pair model: LJ (rc = 2.5 sigma), WCA, patchy (WCA core + patch attraction), or the paper's patchy
+    form PATCHY_POW ((sigma/r)^200 core + patch attraction truncated at patch_rc)."""
     kind: int
     box: tuple
     rc: float
@@ -54,6 +78,7 @@ class Model:
     eps_p: float = 1.0
     delta: float = 0.12
     patches: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    patch_rc: float = 0.0
 
     def to_c(self) -> _Model:
         m = _Model()
@@ -62,6 +87,7 @@ class Model:
         for c in range(3):
             m.box[c] = float(self.box[c])
         m.eps, m.sigma, m.rc, m.eps_p, m.delta = self.eps, self.sigma, self.rc, self.eps_p, self.delta
+        m.patch_rc = self.patch_rc
         for a, p in enumerate(np.asarray(self.patches, dtype=np.float64)):
             for c in range(3):
                 m.patch[a][c] = float(p[c])
@@ -96,6 +122,15 @@ def _load():
         lib.oracle_run_nve.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.POINTER(_Model), ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
         lib.oracle_run_nve.restype = ctypes.c_int
+        lib.oracle_run.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.POINTER(_Model), ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp,
+                                   ctypes.POINTER(_Thermostat), ctypes.c_int]
+        lib.oracle_run.restype = ctypes.c_int
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        lib.oracle_philox4x32.argtypes = [u32p, u32p, u32p]
+        lib.oracle_philox4x32.restype = None
+        lib.oracle_thermostat_draw.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, dp, dp]
+        lib.oracle_thermostat_draw.restype = None
         _lib = lib
     return _lib
 
@@ -119,7 +154,7 @@ def forces(pos, model: Model, quat=None, use_cells: bool = True):
     F = np.zeros((n, 3)); T = np.zeros((n, 3)); E = np.zeros(n); tot = np.zeros(3)
     m = model.to_c()
     rc = _load().oracle_forces(n, _dp(pos), _dp(q), ctypes.byref(m), int(use_cells), _dp(F),
-                               _dp(T) if model.kind == PATCHY else None, _dp(E), _dp(tot))
+                               _dp(T) if model.kind in (PATCHY, PATCHY_POW) else None, _dp(E), _dp(tot))
     if rc != 0:
         raise MemoryError("oracle_forces failed")
     return F, T, E, (tot[0], tot[1], int(tot[2]))
@@ -167,3 +202,37 @@ def run_nve(pos, vel, model: Model, dt: float, nsteps: int, mass: float = 1.0, i
     if rc != 0:
         raise MemoryError("oracle_run_nve failed")
     return pos, vel, q, L, trace
+
+
+def run(pos, vel, model: Model, dt: float, nsteps: int, mass: float = 1.0, inertia: float = 0.1,
+        quat=None, angmom=None, use_cells: bool = True, thermostat: Thermostat | None = None, step0: int = 0):
+    """Velocity Verlet with the optional momentum-refresh thermostat, steps numbered from step0."""
+    n = len(pos)
+    pos = _c64(pos, (n, 3)).copy(); vel = _c64(vel, (n, 3)).copy()
+    q = _c64(quat, (n, 4)).copy() if quat is not None else None
+    L = _c64(angmom, (n, 3)).copy() if angmom is not None else None
+    trace = np.zeros((nsteps + 1, 4))
+    m = model.to_c()
+    th = thermostat.to_c() if thermostat is not None else None
+    rc = _load().oracle_run(n, _dp(pos), _dp(vel), _dp(q), _dp(L), ctypes.byref(m), float(dt), float(mass),
+                            float(inertia), int(nsteps), int(use_cells), _dp(trace),
+                            ctypes.byref(th) if th is not None else None, int(step0))
+    if rc != 0:
+        raise MemoryError("oracle_run failed")
+    return pos, vel, q, L, trace
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of counter ctr[4] and key key[2] (uint32 words)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32); k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    p = ctypes.POINTER(ctypes.c_uint32)
+    _load().oracle_philox4x32(c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
+    return out
+
+
+def thermostat_draw(seed: int, step: int, particle: int):
+    """The thermostat's selection uniform and six standard normals for one particle and step."""
+    u = np.zeros(1); nrm = np.zeros(6)
+    _load().oracle_thermostat_draw(int(seed) & 0xFFFFFFFF, int(step), int(particle), _dp(u), _dp(nrm))
+    return float(u[0]), nrm

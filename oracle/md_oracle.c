@@ -25,9 +25,19 @@
  *    -eps_p exp(-(r_pp/delta)^10 / 2), all applied only when the centre distance
  *    is below rc (the attraction of Sec. Models, Eq. 4, with the minus sign in
  *    the exponent that the printed equation lost, n = 10, and three patches);
+ *  - the paper's own patchy form (Sec. Models, Eqs. 3-4) is a (sigma/r)^200
+ *    centre repulsion plus the same patch attraction, here truncated where a
+ *    patch pair is farther apart than patch_rc (0.18 sigma, the range the paper
+ *    quotes for this model), with both terms applied below the centre cut-off;
  *  - each particle is given half of every pair energy it takes part in;
  *  - integration is velocity Verlet; rotations of an isotropic rigid body are
- *    exact: q <- exp(omega dt / 2) (x) q with omega = L / I, then renormalised.
+ *    exact: q <- exp(omega dt / 2) (x) q with omega = L / I, then renormalised;
+ *  - the thermostat (Sec. Methods: Brownian dynamics in the NVT ensemble) redraws,
+ *    at the start of every step s > 0 that is a multiple of `every`, the linear
+ *    (and angular) momentum of each particle with probability p from the
+ *    Maxwell-Boltzmann distribution at kT.  The random numbers come from the
+ *    counter-based generator Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ *    counter (s, particle, stream, 0), key (seed, 0), and Box-Muller normals.
  */
 #include <math.h>
 #include <stdint.h>
@@ -37,17 +47,28 @@
 #define OR_LJ 0
 #define OR_WCA 1
 #define OR_PATCHY 2
+#define OR_PATCHY_POW 3
+#define OR_POW_CORE 200 /* exponent of the centre repulsion of the paper's patchy model (Eq. 3) */
 
 /* Model description handed in from the tests (a flat struct of plain types). */
 typedef struct {
-  int32_t model;        /* OR_LJ, OR_WCA or OR_PATCHY                          */
+  int32_t model;        /* OR_LJ, OR_WCA, OR_PATCHY or OR_PATCHY_POW           */
   int32_t n_patch;      /* patches per particle (patchy only, <= 8)             */
   double box[3];        /* periodic box edges                                   */
   double eps, sigma;    /* Lennard-Jones well depth and diameter                */
   double rc;            /* centre-centre cut-off                                */
   double eps_p, delta;  /* patch strength and range (patchy only)               */
   double patch[8][3];   /* body-frame patch-site offsets from the centre        */
+  double patch_rc;      /* OR_PATCHY_POW: patch pairs at r_ab >= patch_rc do not interact */
 } or_model;
+
+/* Thermostat of or_run (every = 0: none). */
+typedef struct {
+  int32_t every;        /* steps between momentum refreshes                     */
+  uint32_t seed;        /* generator key                                        */
+  double prob;          /* probability that a particle is refreshed             */
+  double kT;            /* temperature                                          */
+} or_thermostat;
 
 /* ------------------------------------------------------------------------- */
 /* Geometry                                                                    */
@@ -100,6 +121,14 @@ static double lj_energy(double eps, double sigma, double r2) {
   return 4.0 * eps * (sr12 - sr6);
 }
 
+/* Centre repulsion of the paper's patchy model (Eq. 3): energy (sigma/r)^200 and
+ * fs with F_i = fs * d. */
+static void pow_core(const or_model* m, double r2, double* e, double* fs) {
+  double r = sqrt(r2);
+  *e = pow(m->sigma / r, OR_POW_CORE);
+  *fs = -OR_POW_CORE * (*e) / r2;
+}
+
 /* Cut-off used for the isotropic part of each model. */
 static double iso_cutoff(const or_model* m) {
   if (m->model == OR_LJ) return m->rc;
@@ -133,10 +162,11 @@ static int pair_terms(const or_model* m, const double* d, double Ri[3][3], doubl
   *e = 0.0; *w = 0.0;
   if (!(r2 < m->rc * m->rc)) return 0;
   double eiso, fs;
-  iso_pair(m, r2, &eiso, &fs);
+  if (m->model == OR_PATCHY_POW) pow_core(m, r2, &eiso, &fs);
+  else iso_pair(m, r2, &eiso, &fs);
   for (int c = 0; c < 3; c++) fi[c] = fs * d[c];
   *e = eiso;
-  if (m->model == OR_PATCHY) {
+  if (m->model == OR_PATCHY || m->model == OR_PATCHY_POW) {
     double pa[8][3], pb[8][3];
     for (int a = 0; a < m->n_patch; a++) { mat_vec(Ri, m->patch[a], pa[a]); mat_vec(Rj, m->patch[a], pb[a]); }
     double d2 = m->delta * m->delta;
@@ -145,6 +175,7 @@ static int pair_terms(const or_model* m, const double* d, double Ri[3][3], doubl
         /* separation of patch site b on j from patch site a on i */
         double s[3];
         for (int c = 0; c < 3; c++) s[c] = d[c] + pb[b][c] - pa[a][c];
+        if (m->model == OR_PATCHY_POW && !(norm2(s) < m->patch_rc * m->patch_rc)) continue;
         double q = norm2(s) / d2;               /* (r_ab / delta)^2 */
         double q5 = q * q * q * q * q;          /* (r_ab / delta)^10 */
         double ex = exp(-0.5 * q5);
@@ -255,7 +286,10 @@ static void force_visit(int i, int j, void* vctx) {
   const or_model* m = fc->m;
   double d[3], Ri[3][3], Rj[3][3], fi[3], ti[3], tj[3], e, w;
   min_image(fc->pos + 3 * i, fc->pos + 3 * j, m->box, d);
-  if (m->model == OR_PATCHY) { quat_to_rot(fc->quat + 4 * i, Ri); quat_to_rot(fc->quat + 4 * j, Rj); }
+  if (m->model == OR_PATCHY || m->model == OR_PATCHY_POW) {
+    quat_to_rot(fc->quat + 4 * i, Ri);
+    quat_to_rot(fc->quat + 4 * j, Rj);
+  }
   if (!pair_terms(m, d, Ri, Rj, fi, ti, tj, &e, &w)) return;
   fc->n_interacting++;
   for (int c = 0; c < 3; c++) { fc->F[3 * i + c] += fi[c]; fc->F[3 * j + c] -= fi[c]; }
@@ -359,16 +393,65 @@ static void rotate_quat(double* q, const double* omega, double dt) {
   for (int k = 0; k < 4; k++) q[k] /= nq;
 }
 
-/* nsteps of NVE velocity Verlet.  pos/vel [n][3]; quat [n][4] and angmom [n][3]
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy */
+/* as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications whose high  */
+/* halves are mixed with the other counter words and the round key; the key is */
+/* bumped by the two Weyl constants between rounds.                            */
+/* ------------------------------------------------------------------------- */
+
+void oracle_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; r++) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* A 32-bit word as a uniform number in (0, 1). */
+static double unit_open(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+/* Two standard normals from two words (Box-Muller). */
+static void box_muller(uint32_t a, uint32_t b, double* n0, double* n1) {
+  double r = sqrt(-2.0 * log(unit_open(a)));
+  double t = 6.283185307179586476925286766559 * unit_open(b); /* 2 pi */
+  *n0 = r * cos(t);
+  *n1 = r * sin(t);
+}
+
+/* The thermostat's draws for particle `id` at step s: selection uniform and six normals
+ * (three for the velocity, three for the angular momentum). */
+void oracle_thermostat_draw(uint32_t seed, uint32_t s, uint32_t id, double* u, double nrm[6]) {
+  uint32_t key[2] = {seed, 0u}, a[4], b[4];
+  uint32_t ca[4] = {s, id, 0u, 0u}, cb[4] = {s, id, 1u, 0u};
+  oracle_philox4x32(ca, key, a);
+  oracle_philox4x32(cb, key, b);
+  *u = unit_open(a[0]);
+  box_muller(a[1], a[2], &nrm[0], &nrm[1]);
+  box_muller(b[0], b[1], &nrm[2], &nrm[3]);
+  box_muller(b[2], b[3], &nrm[4], &nrm[5]);
+}
+
+/* nsteps of velocity Verlet.  pos/vel [n][3]; quat [n][4] and angmom [n][3]
  * (lab-frame angular momentum) for patchy, else NULL.  Positions are wrapped
  * into [0, L) after each drift.  trace (if not NULL) gets nsteps+1 rows of
- * {K_trans, K_rot, U, W}.  Forces are recomputed from scratch every step. */
-int oracle_run_nve(int n, double* pos, double* vel, double* quat, double* angmom, const or_model* m,
-                   double dt, double mass, double inertia, int nsteps, int use_cells, double* trace) {
+ * {K_trans, K_rot, U, W}.  Forces are recomputed from scratch every step.
+ * th (may be NULL) is the momentum-refresh thermostat; step numbers start at
+ * step0, so that a run continued in pieces draws the same numbers. */
+int oracle_run(int n, double* pos, double* vel, double* quat, double* angmom, const or_model* m,
+               double dt, double mass, double inertia, int nsteps, int use_cells, double* trace,
+               const or_thermostat* th, int step0) {
   double* F = (double*)calloc(3 * (size_t)n + 1, sizeof(double));
   double* T = (double*)calloc(3 * (size_t)n + 1, sizeof(double));
   double* E = (double*)calloc((size_t)n + 1, sizeof(double));
-  int patchy = (m->model == OR_PATCHY);
+  int patchy = (m->model == OR_PATCHY || m->model == OR_PATCHY_POW);
   double tot[3];
   if (!F || !T || !E) { free(F); free(T); free(E); return -1; }
   if (oracle_forces(n, pos, quat, m, use_cells, F, patchy ? T : NULL, E, tot)) { free(F); free(T); free(E); return -1; }
@@ -382,6 +465,16 @@ int oracle_run_nve(int n, double* pos, double* vel, double* quat, double* angmom
       trace[4 * s + 0] = kt; trace[4 * s + 1] = kr; trace[4 * s + 2] = tot[0]; trace[4 * s + 3] = tot[1];
     }
     if (s == nsteps) break;
+    int step = step0 + s;
+    if (th && th->every > 0 && step > 0 && step % th->every == 0) {
+      for (int i = 0; i < n; i++) {
+        double u, nrm[6];
+        oracle_thermostat_draw(th->seed, (uint32_t)step, (uint32_t)i, &u, nrm);
+        if (!(u < th->prob)) continue;
+        for (int c = 0; c < 3; c++) vel[3 * i + c] = sqrt(th->kT / mass) * nrm[c];
+        if (patchy) for (int c = 0; c < 3; c++) angmom[3 * i + c] = sqrt(th->kT * inertia) * nrm[3 + c];
+      }
+    }
     for (int i = 0; i < n; i++) {
       for (int c = 0; c < 3; c++) {
         vel[3 * i + c] += 0.5 * dt * F[3 * i + c] / mass;
@@ -402,4 +495,10 @@ int oracle_run_nve(int n, double* pos, double* vel, double* quat, double* angmom
   }
   free(F); free(T); free(E);
   return 0;
+}
+
+/* NVE run (no thermostat) from step 0. */
+int oracle_run_nve(int n, double* pos, double* vel, double* quat, double* angmom, const or_model* m,
+                   double dt, double mass, double inertia, int nsteps, int use_cells, double* trace) {
+  return oracle_run(n, pos, vel, quat, angmom, m, dt, mass, inertia, nsteps, use_cells, trace, NULL, 0);
 }

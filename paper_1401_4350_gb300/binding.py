@@ -18,11 +18,13 @@ LIB_PATH = os.path.join(PKG, "libmdgb.so")
 HEADER = os.path.join(ROOT, "include", "md.h")
 
 MD_OK, MD_ERR_INVALID, MD_ERR_CUDA, MD_ERR_NEIGH_OVERFLOW, MD_ERR_NONFINITE, MD_ERR_TIMEOUT, MD_ERR_UNSUPPORTED = range(7)
-MD_LJ, MD_WCA, MD_PATCHY = 0, 1, 2
+MD_LJ, MD_WCA, MD_PATCHY, MD_PATCHY_POW = 0, 1, 2, 3
 MD_FP64, MD_MIXED = 0, 1
 MD_VERTEX, MD_EDGE, MD_VERTEX_NEWTON, MD_EDGE_STORE = 0, 1, 2, 3
 MD_ORDER_ROWS, MD_ORDER_HILBERT = 0, 1
 MD_LIST_FULL, MD_LIST_HALF, MD_LIST_BOTH, MD_LIST_NEWTON = 1, 2, 3, 4
+MD_LIST_FULL_LOCAL, MD_LOCAL_BLOCK, MD_LOCAL_MAX_CELLS = 8, 256, 512
+MD_FORMAT_GLOBAL, MD_FORMAT_LOCAL = 0, 1
 MD_MAX_PATCH = 4
 MD_STATUS_CODE, MD_STATUS_NEED_NEIGH, MD_STATUS_NEED_PAIRS_LO, MD_STATUS_NEED_PAIRS_HI = 0, 1, 2, 3
 MD_STATUS_REBUILDS, MD_STATUS_STEPS, MD_STATUS_LISTS, MD_STATUS_WORDS = 4, 5, 6, 16
@@ -35,11 +37,14 @@ class md_params(ctypes.Structure):
                 ("threads_per_particle", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("trace_capacity", ctypes.c_int32), ("energy_every", ctypes.c_int32), ("force_copies", ctypes.c_int32),
                 ("cell_order", ctypes.c_int32), ("edge_store", ctypes.c_int32),
+                ("list_format", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("box", ctypes.c_double * 3), ("rc", ctypes.c_double),
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double), ("mass", ctypes.c_double),
                 ("inertia", ctypes.c_double), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("eps_p", ctypes.c_double), ("delta", ctypes.c_double),
-                ("patch", (ctypes.c_double * 3) * MD_MAX_PATCH)]
+                ("patch", (ctypes.c_double * 3) * MD_MAX_PATCH), ("patch_rc", ctypes.c_double),
+                ("kT", ctypes.c_double), ("thermostat_prob", ctypes.c_double),
+                ("thermostat_every", ctypes.c_int32), ("seed", ctypes.c_uint32)]
 
 
 class md_state(ctypes.Structure):
@@ -51,7 +56,8 @@ class md_ws_layout(ctypes.Structure):
     _fields_ = [("total", ctypes.c_size_t), ("ncell", ctypes.c_int32 * 3), ("force_elem", ctypes.c_int32)] + [
         (name, ctypes.c_size_t) for name in
         ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr", "nbr_count", "half_start",
-         "pairs", "force", "virial", "torque", "acc", "copies", "estore", "jstart", "jedge", "trace", "scratch")]
+         "pairs", "force", "virial", "torque", "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace",
+         "scratch")]
 
 
 class MDError(RuntimeError):

@@ -55,7 +55,7 @@ static void cell_dims(const md_params* p, int nc[3]) {
 static int check(const md_params* p) {
   if (!p) { set_error("params is NULL"); return MD_ERR_INVALID; }
   if (p->n < 1) { set_error("n must be >= 1 (got %d)", p->n); return MD_ERR_INVALID; }
-  if (p->model < MD_LJ || p->model > MD_PATCHY) { set_error("unknown model %d", p->model); return MD_ERR_INVALID; }
+  if (p->model < MD_LJ || p->model > MD_PATCHY_POW) { set_error("unknown model %d", p->model); return MD_ERR_INVALID; }
   if (p->precision != MD_FP64 && p->precision != MD_MIXED) { set_error("unknown precision %d", p->precision); return MD_ERR_INVALID; }
   if (p->max_neigh < 1) { set_error("max_neigh must be >= 1"); return MD_ERR_INVALID; }
   if (p->max_pairs < 1) { set_error("max_pairs must be >= 1"); return MD_ERR_INVALID; }
@@ -85,29 +85,57 @@ static int check(const md_params* p) {
     return MD_ERR_INVALID;
   }
   if (p->edge_store != 0 && p->edge_store != 1) { set_error("edge_store must be 0 or 1"); return MD_ERR_INVALID; }
+  if (p->list_format != MD_FORMAT_GLOBAL && p->list_format != MD_FORMAT_LOCAL) {
+    set_error("list_format must be MD_FORMAT_GLOBAL or MD_FORMAT_LOCAL");
+    return MD_ERR_INVALID;
+  }
+  if (p->reserved != 0) { set_error("reserved must be 0"); return MD_ERR_INVALID; }
   if (p->edge_store && p->max_pairs >= (int64_t)1 << 31) {
     set_error("edge_store needs max_pairs < 2^31 (32-bit positions in the by-partner index)");
     return MD_ERR_INVALID;
   }
-  if (p->model == MD_PATCHY) {
+  if (is_patchy(p->model)) {
     if (p->n_patch < 1 || p->n_patch > MD_MAX_PATCH) { set_error("n_patch must be in 1..%d", MD_MAX_PATCH); return MD_ERR_INVALID; }
     if (!(p->inertia > 0.0) || !(p->delta > 0.0)) { set_error("inertia and delta must be > 0"); return MD_ERR_INVALID; }
   }
+  if (p->model == MD_PATCHY_POW && !(p->patch_rc > 0.0)) { set_error("MD_PATCHY_POW needs patch_rc > 0"); return MD_ERR_INVALID; }
+  if (p->thermostat_every < 0) { set_error("thermostat_every must be >= 0"); return MD_ERR_INVALID; }
+  if (p->thermostat_every > 0 && (!(p->kT > 0.0) || !(p->thermostat_prob >= 0.0 && p->thermostat_prob <= 1.0))) {
+    set_error("the thermostat needs kT > 0 and thermostat_prob in [0, 1]");
+    return MD_ERR_INVALID;
+  }
   if ((double)p->n * (double)p->max_neigh > 9.0e18) { set_error("n * max_neigh too large"); return MD_ERR_INVALID; }
   return MD_OK;
+}
+
+// Whether md_build_verlet(MD_LIST_FULL) builds the block-local full list: mixed-precision LJ/WCA in a
+// cubic box, one thread per particle, a cell grid of at least 3 per axis, and lists long enough (mean
+// at least 16) that staging each block's halo in shared memory beats gathering every entry.
+static bool local_list_eligible(const md_params* p) {
+  if (p->list_format != MD_FORMAT_LOCAL) return false;
+  if (p->precision != MD_MIXED || (p->model != MD_LJ && p->model != MD_WCA)) return false;
+  if (!(p->box[0] == p->box[1] && p->box[1] == p->box[2])) return false;
+  if (p->threads_per_particle != 1 || (p->block_size != 0 && p->block_size != MD_LOCAL_BLOCK)) return false;
+  if (p->max_neigh > 65535) return false;
+  int nc[3];
+  cell_dims(p, nc);
+  if (nc[0] < 3 || nc[1] < 3 || nc[2] < 3) return false;
+  const double rv = p->rc + p->skin;
+  const double nbar = 4.18879020478639 * rv * rv * rv * (double)p->n / (p->box[0] * p->box[1] * p->box[2]);
+  return nbar >= 16.0;
 }
 
 // Bytes of the per-edge store (0 unless edge_store): blocks A, B and, patchy, C of max_pairs entries.
 static size_t estore_bytes(const md_params* p) {
   if (!p->edge_store) return 0;
   const size_t elem = p->precision == MD_MIXED ? 16 : 32;
-  return elem * (size_t)p->max_pairs * (p->model == MD_PATCHY ? 3 : 2);
+  return elem * (size_t)p->max_pairs * (is_patchy(p->model) ? 3 : 2);
 }
 
 // Bytes of the Newton-vertex reaction copies (0 when force_copies is 0).
 static size_t copies_bytes(const md_params* p) {
   const size_t m = (size_t)p->force_copies, n = (size_t)p->n;
-  const bool patchy = p->model == MD_PATCHY;
+  const bool patchy = is_patchy(p->model);
   return p->precision == MD_MIXED ? 16 * n * m * (patchy ? 4 : 2) : m * n * (32 + 8 + (patchy ? 32 : 0));
 }
 
@@ -124,7 +152,7 @@ static void make_layout(const md_params* p, Layout* L) {
   const size_t n = (size_t)p->n;
   const size_t ncell = (size_t)nc[0] * nc[1] * nc[2];
   const size_t fe = p->precision == MD_MIXED ? 4 : 8;  // patch sites: int4 (mixed) or double4
-  const bool patchy = p->model == MD_PATCHY;
+  const bool patchy = is_patchy(p->model);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -152,6 +180,7 @@ static void make_layout(const md_params* p, Layout* L) {
   P.estore = take(estore_bytes(p));
   P.jstart = take(p->edge_store ? sizeof(int64_t) * (n + 1) : 0);
   P.jedge = take(p->edge_store ? sizeof(int32_t) * (size_t)p->max_pairs : 0);
+  P.local_tab = take(local_list_eligible(p) ? sizeof(int32_t) * kLocalRec * ((n + MD_LOCAL_BLOCK - 1) / MD_LOCAL_BLOCK) : 0);
   P.trace = take(sizeof(double) * 4 * (size_t)p->trace_capacity);
   P.scratch = off;
   L->scr_words = take(sizeof(uint32_t) * SCR_WORDS);
@@ -181,7 +210,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.precision = p->precision;
   a.max_neigh = p->max_neigh;
   a.max_pairs = p->max_pairs;
-  a.n_patch = p->model == MD_PATCHY ? p->n_patch : 0;
+  a.n_patch = is_patchy(p->model) ? p->n_patch : 0;
   a.tpp = p->threads_per_particle;
   a.trace_capacity = p->trace_capacity;
   a.energy_every = p->energy_every > 1 ? p->energy_every : 1;
@@ -216,7 +245,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     a.rwca2_u = f32(a.rwca2_d / u2);
     a.rwca2_lo_u = f32(a.rwca2_d * (1.0 - 1e-5) / u2);
     a.rwca2_hi_u = f32(a.rwca2_d * (1.0 + 1e-5) / u2);
-    if (p->model == MD_PATCHY) a.u2_over_delta2 = f32(u2 / (p->delta * p->delta));
+    if (is_patchy(p->model)) a.u2_over_delta2 = f32(u2 / (p->delta * p->delta));
     // Scaled units of the isotropic vertex kernel.  A pair of a current list is closer than
     // rv + skin (each particle moves less than skin/2 between builds), so the shift leaves the
     // largest such r^2 below 2^31 and keeps more than 24 bits of r^2 for every r > (rv + skin) / 6.
@@ -244,7 +273,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.lj_c4_f = f32(a.lj_c4_d);
   a.lj_c24_f = f32(a.lj_c24_d);
   a.lj_shift_f = f32(a.lj_shift_d);
-  if (p->model == MD_PATCHY) {
+  if (is_patchy(p->model)) {
     a.inv_delta2_d = 1.0 / (p->delta * p->delta);
     a.eps_p_d = p->eps_p;
     a.pgain_d = 5.0 * p->eps_p / (p->delta * p->delta);
@@ -261,11 +290,27 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     }
     // every patch term is exactly zero once (r_ab / delta)^10 exceeds 177.4 (FP32: exp2 argument
     // below -128, flushed) or 1600 (FP64: exp argument below -800, underflow)
-    const double reach_f = 2.0 * R + p->delta * pow(128.0 * 2.0 * log(2.0), 0.1);
-    const double reach_d = 2.0 * R + p->delta * pow(1600.0, 0.1);
+    double reach_f = 2.0 * R + p->delta * pow(128.0 * 2.0 * log(2.0), 0.1);
+    double reach_d = 2.0 * R + p->delta * pow(1600.0, 0.1);
+    a.patch_qcut_f = 3.0e38f;
+    a.patch_qcut_d = 1.0e300;
+    if (p->model == MD_PATCHY_POW) {
+      // truncated patch pairs: nothing beyond r_ab = patch_rc, so no centre pair beyond 2 R + patch_rc
+      a.pow_core = 1;
+      const double q = (p->patch_rc / p->delta) * (p->patch_rc / p->delta);
+      a.patch_qcut_d = q;
+      a.patch_qcut_f = f32(q);
+      if (2.0 * R + p->patch_rc < reach_f) reach_f = 2.0 * R + p->patch_rc;
+      if (2.0 * R + p->patch_rc < reach_d) reach_d = 2.0 * R + p->patch_rc;
+    }
     a.patch_reach2_f = f32(reach_f * reach_f);
     a.patch_reach2_d = reach_d * reach_d;
   }
+  a.thermo_every = p->thermostat_every;
+  a.seed = p->seed;
+  a.thermo_prob = p->thermostat_prob;
+  a.sigma_v = p->thermostat_every > 0 ? sqrt(p->kT / p->mass) : 0.0;
+  a.sigma_l = p->thermostat_every > 0 ? sqrt(p->kT * p->inertia) : 0.0;
   a.dt = p->dt;
   a.mass = p->mass;
   a.inv_mass = 1.0 / p->mass;
@@ -301,6 +346,8 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.acc = (float4*)(w + L.pub.acc);
   a.copies = (void*)(w + L.pub.copies);
   a.force_copies = p->force_copies;
+  a.local_ok = local_list_eligible(p) ? 1 : 0;
+  a.local_tab = a.local_ok ? (int32_t*)(w + L.pub.local_tab) : nullptr;
   a.estore = p->edge_store ? (void*)(w + L.pub.estore) : nullptr;
   a.jstart = p->edge_store ? (int64_t*)(w + L.pub.jstart) : nullptr;
   a.jedge = p->edge_store ? (int32_t*)(w + L.pub.jedge) : nullptr;
@@ -328,7 +375,7 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
   a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
   a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
-  a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr;
+  a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr; a.local_ok = 0; a.local_tab = nullptr;
   a.scr_words = nullptr; a.block_partials = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;
   a.count_tmp = nullptr; a.block_sums = nullptr; a.tmp_d4 = nullptr; a.tmp_i = nullptr; a.cell_rank = nullptr;
   return a;
@@ -352,7 +399,7 @@ KArgs replica_kernel_args(const md_params* p, const md_state* s, void* ws) {
 
 static int check_state(const md_params* p, const md_state* s, const void* ws) {
   if (!s || !s->pos || !s->vel || !s->id) { set_error("state arrays pos, vel and id are required"); return MD_ERR_INVALID; }
-  if (p->model == MD_PATCHY && (!s->quat || !s->angmom)) { set_error("patchy model needs quat and angmom"); return MD_ERR_INVALID; }
+  if (is_patchy(p->model) && (!s->quat || !s->angmom)) { set_error("patchy model needs quat and angmom"); return MD_ERR_INVALID; }
   if (!ws) { set_error("workspace is NULL"); return MD_ERR_INVALID; }
   if (((uintptr_t)ws) & 255) { set_error("workspace must be 256-byte aligned"); return MD_ERR_INVALID; }
   if (((uintptr_t)s->pos | (uintptr_t)s->vel) & 31) { set_error("pos and vel must be 32-byte aligned"); return MD_ERR_INVALID; }

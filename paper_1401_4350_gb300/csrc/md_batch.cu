@@ -408,12 +408,13 @@ static int check_batch_params(const md_params* reps, int nrep) {
   for (int r = 0; r < nrep; r++) {
     int rc = check_params_only(&reps[r]);
     if (rc != MD_OK) return rc;
-    if (reps[r].precision != MD_MIXED || reps[r].model == MD_PATCHY) {
+    if (reps[r].precision != MD_MIXED || is_patchy(reps[r].model)) {
       set_error("batch: replica %d: the batched path supports mixed-precision LJ and WCA replicas", r);
       return MD_ERR_INVALID;
     }
-    if (reps[r].cell_order != MD_ORDER_ROWS || reps[r].force_copies != 0 || reps[r].edge_store != 0) {
-      set_error("batch: replica %d: cell_order, force_copies and edge_store must be 0 in a batch", r);
+    if (reps[r].cell_order != MD_ORDER_ROWS || reps[r].force_copies != 0 || reps[r].edge_store != 0 ||
+        reps[r].thermostat_every != 0) {
+      set_error("batch: replica %d: cell_order, force_copies, edge_store and thermostat_every must be 0 in a batch", r);
       return MD_ERR_INVALID;
     }
   }

@@ -81,7 +81,7 @@ __device__ __forceinline__ void cells_gather_one(const KArgs& a, int s) {
   const size_t n = (size_t)a.n;
   a.tmp_d4[s] = a.pos[o];
   a.tmp_d4[n + s] = a.vel[o];
-  if (a.model == MD_PATCHY) {
+  if (is_patchy(a.model)) {
     a.tmp_d4[2 * n + s] = a.quat[o];
     a.tmp_d4[3 * n + s] = a.angmom[o];
   }
@@ -93,7 +93,7 @@ __device__ __forceinline__ void cells_copyback_one(const KArgs& a, int s) {
   double4_32a p = a.tmp_d4[s];
   a.pos[s] = p;
   a.vel[s] = a.tmp_d4[n + s];
-  if (a.model == MD_PATCHY) {
+  if (is_patchy(a.model)) {
     double4_32a q = a.tmp_d4[2 * n + s];
     a.quat[s] = q;
     a.angmom[s] = a.tmp_d4[3 * n + s];

@@ -52,7 +52,13 @@ static void launch_vertex(const KArgs& a, int block, cudaStream_t st) {
   if (a.precision == MD_MIXED && !PATCHY) {
     if (a.cubic) {
       switch (a.tpp) {
-        case 1: k_vertex_iso_mixed<1, true><<<grid, block, 0, st>>>(a); break;
+        case 1:
+          if (a.local_ok)  // either list format: the kernel reads which one the status records
+            k_vertex_iso_mixed<1, true><<<(a.n + MD_LOCAL_BLOCK - 1) / MD_LOCAL_BLOCK, MD_LOCAL_BLOCK,
+                                          sizeof(uint4) * kLocalSmem, st>>>(a);
+          else
+            k_vertex_iso_mixed<1, true><<<grid, block, 0, st>>>(a);
+          break;
         case 2: k_vertex_iso_mixed<2, true><<<grid, block, 0, st>>>(a); break;
         case 4: k_vertex_iso_mixed<4, true><<<grid, block, 0, st>>>(a); break;
         default: k_vertex_iso_mixed<8, true><<<grid, block, 0, st>>>(a); break;
@@ -135,14 +141,14 @@ cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st) 
   if (path == MD_EDGE) {
     const size_t n = (size_t)a.n;
     if (a.precision == MD_MIXED) {
-      cudaMemsetAsync(a.acc, 0, sizeof(float4) * n * (a.model == MD_PATCHY ? 4 : 2), st);
+      cudaMemsetAsync(a.acc, 0, sizeof(float4) * n * (is_patchy(a.model) ? 4 : 2), st);
     } else {
       cudaMemsetAsync(a.force, 0, sizeof(double4_32a) * n, st);
       cudaMemsetAsync(a.virial, 0, sizeof(double) * n, st);
-      if (a.model == MD_PATCHY) cudaMemsetAsync(a.torque, 0, sizeof(double4_32a) * n, st);
+      if (is_patchy(a.model)) cudaMemsetAsync(a.torque, 0, sizeof(double4_32a) * n, st);
     }
   }
-  if (a.model != MD_PATCHY) {
+  if (!is_patchy(a.model)) {
     launch_path<false, 1>(a, path, block, st);
   } else {
     switch (a.n_patch) {

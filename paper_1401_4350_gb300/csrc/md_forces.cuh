@@ -175,6 +175,15 @@ __device__ __forceinline__ PairOut<float> iso_pair_cubic(const KArgs& a, const i
   return o;
 }
 
+// Centre repulsion of MD_PATCHY_POW (Sec. Models, Eq. 3): V = (sigma/r)^200 by repeated squaring of
+// (sigma/r)^2; fs with F_i = fs d, d = x_j - x_i.
+__device__ __forceinline__ void pow_core_terms(const KArgs& a, double r2, double& fs, double& pe) {
+  const double s2 = a.sig2_d / r2;  // (sigma/r)^2; names below are powers of sigma/r
+  const double s4 = s2 * s2, s8 = s4 * s4, s16 = s8 * s8, s32 = s16 * s16, s64 = s32 * s32, s128 = s64 * s64;
+  pe = s128 * s64 * s8;  // (sigma/r)^200
+  fs = -200.0 * pe / r2;
+}
+
 // Patchy pair: WCA core + sum over patch pairs of -eps_p exp(-(r_ab/delta)^10 / 2), applied when the
 // centre distance is below rc.  Patch terms are skipped when the centre distance is beyond the
 // reach at which every term has underflowed to zero in this precision (exact).
@@ -185,7 +194,12 @@ __device__ __forceinline__ PairOut<double> patchy_pair(const KArgs& a, const Vec
   o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
   o.e = o.w = 0.0;
   if (!(r2 < a.rc2_d)) return o;
-  if (iso_inside<double>(a, r2, i, j)) {
+  if (a.pow_core) {
+    double fs, pe;
+    pow_core_terms(a, r2, fs, pe);
+    o.F = {fs * d.x, fs * d.y, fs * d.z};
+    o.e = pe;
+  } else if (iso_inside<double>(a, r2, i, j)) {
     double fs, pe;
     lj_terms(a, r2, fs, pe);
     o.F = {fs * d.x, fs * d.y, fs * d.z};
@@ -204,6 +218,7 @@ __device__ __forceinline__ PairOut<double> patchy_pair(const KArgs& a, const Vec
       for (int b = 0; b < NP; b++) {
         const Vec3<double> s = {base.x + Pj.p[b].x, base.y + Pj.p[b].y, base.z + Pj.p[b].z};
         const double q = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_d;
+        if (!(q < a.patch_qcut_d)) continue;  // truncated patch pair (MD_PATCHY_POW)
         const double q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
         const double ex = exp(-0.5 * q5);
         o.e -= a.eps_p_d * ex;
@@ -240,7 +255,16 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
   o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
   o.e = o.w = 0.f;
   if (!(r2 < a.rc2_f)) return o;
-  if (a.cubic) {
+  if (a.pow_core) {
+    // (sigma/r)^200 multiplies the relative error of r by 200: even the 2^-33 L quantisation of the
+    // fixed-point coordinates would show, so this term is FP64 from the FP64 positions; only its
+    // result is rounded to FP32
+    const Vec3<double> dd = sep_fp64(a.pos[i], a.pos[j], a);
+    double fs, pe;
+    pow_core_terms(a, dd.x * dd.x + dd.y * dd.y + dd.z * dd.z, fs, pe);
+    o.F = {(float)(fs * dd.x), (float)(fs * dd.y), (float)(fs * dd.z)};
+    o.e = (float)pe;
+  } else if (a.cubic) {
     const PairOut<float> c = iso_pair_cubic(a, ds, i, j);
     o.F = c.F;
     o.e = c.e;
@@ -275,6 +299,7 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
         } else {
           q = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_f;
         }
+        if (!(q < a.patch_qcut_f)) continue;  // truncated patch pair (MD_PATCHY_POW)
         const float q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
         const float ex = fexp2_approx(a.half_log2e_f * q5);
         o.e -= a.eps_p_f * ex;
@@ -358,10 +383,10 @@ __device__ __forceinline__ int4 load_group(const int4* nb4, int g, int ng, size_
   return g < ng ? __ldcs(nb4 + (size_t)g * n) : make_int4(-1, -1, -1, -1);
 }
 
-// The vertex kernels walk the full list; the Newton list is kept in the same storage, so a vertex
-// evaluation after a Newton build records MD_ERR_INVALID instead of using half rows.
+// The vertex kernels walk the full list.  The Newton list and the block-local format share its storage,
+// so a kernel that cannot read what was built records MD_ERR_INVALID instead of misreading it.
 __device__ __forceinline__ bool full_list_current(const KArgs& a) {
-  if (!(a.status[MD_STATUS_LISTS] & MD_LIST_NEWTON)) return true;
+  if (!(a.status[MD_STATUS_LISTS] & (MD_LIST_NEWTON | MD_LIST_FULL_LOCAL))) return true;
   if (threadIdx.x == 0) record_error(a.status, MD_ERR_INVALID);
   return false;
 }
@@ -514,14 +539,61 @@ struct IsoAcc {
 };
 
 // One group of four list entries (cur) of particle si.  LIVE: some entries may lie past the count.
-template <bool LIVE>
-__device__ __forceinline__ void iso_group(const KArgs& a, const uint4& si, const int4& cur, int lim, unsigned jmax,
+// Where the entries of a row and the coordinates they name come from.
+// Global format: int32 slots, groups of four per int4; coordinates gathered from fxp.
+struct GlobalRows {
+  const int4* nb4;
+  unsigned jmax;
+  __device__ __forceinline__ int4 group(int g, int ng, size_t n) const { return load_group(nb4, g, ng, n); }
+  __device__ __forceinline__ void prefetch(int g, size_t n) const { prefetch_l2(nb4 + (size_t)g * n); }
+  // an index can only be out of range in a list that was never built: clamp, never fault
+  __device__ __forceinline__ uint4 coords(const KArgs& a, unsigned v) const { return __ldg(a.fxp + min(v, jmax)); }
+  __device__ __forceinline__ unsigned slot(const KArgs&, unsigned v) const { return min(v, jmax); }
+  __device__ __forceinline__ unsigned entry(const KArgs& a, int k, int i, size_t n) const {
+    return (unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n));
+  }
+};
+
+// Block-local format: uint16 halo positions, groups of four per 8 bytes; coordinates from the block's
+// halo staged in shared memory (or, for a halo too large to stage, from fxp through the cell table).
+struct LocalRows {
+  const uint2* nb2;
+  const uint4* halo;     // shared memory, or null
+  const int32_t* tab;    // the block's record: header + (first slot, halo offset) per cell
+  int U, H;
+  unsigned jmax;
+  __device__ __forceinline__ int4 group(int g, int ng, size_t n) const {
+    if (g >= ng) return make_int4(0, 0, 0, 0);
+    const uint2 w = __ldcs(nb2 + (size_t)g * n);
+    return make_int4((int)(w.x & 0xffffu), (int)(w.x >> 16), (int)(w.y & 0xffffu), (int)(w.y >> 16));
+  }
+  __device__ __forceinline__ void prefetch(int g, size_t n) const { prefetch_l2(nb2 + (size_t)g * n); }
+  __device__ __forceinline__ unsigned slot(const KArgs&, unsigned v) const {
+    v = min(v, (unsigned)max(H - 1, 0));
+    int lo = 0, hi = U - 1;  // last cell whose offset is <= v
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if ((unsigned)tab[4 + 2 * mid + 1] <= v) lo = mid;
+      else hi = mid - 1;
+    }
+    return min((unsigned)(tab[4 + 2 * lo] + (int)(v - (unsigned)tab[4 + 2 * lo + 1])), jmax);
+  }
+  __device__ __forceinline__ uint4 coords(const KArgs& a, unsigned v) const {
+    return halo ? halo[min(v, (unsigned)max(H - 1, 0))] : __ldg(a.fxp + slot(a, v));
+  }
+  __device__ __forceinline__ unsigned entry(const KArgs& a, int k, int i, size_t n) const {
+    return (unsigned)((const uint16_t*)a.nbr)[nbr_index(k, i, n)];
+  }
+};
+
+template <bool LIVE, class Rows>
+__device__ __forceinline__ void iso_group(const KArgs& a, const uint4& si, const int4& cur, int lim, const Rows& R,
                                           IsoAcc& A) {
-  const unsigned jj[4] = {min((unsigned)cur.x, jmax), min((unsigned)cur.y, jmax), min((unsigned)cur.z, jmax),
-                          min((unsigned)cur.w, jmax)};
   uint4 sj[4];
-#pragma unroll
-  for (int u = 0; u < 4; u++) sj[u] = __ldg(a.fxp + jj[u]);
+  sj[0] = R.coords(a, (unsigned)cur.x);
+  sj[1] = R.coords(a, (unsigned)cur.y);
+  sj[2] = R.coords(a, (unsigned)cur.z);
+  sj[3] = R.coords(a, (unsigned)cur.w);
   float r2[4], dx[4], dy[4], dz[4];
 #pragma unroll
   for (int u = 0; u < 4; u++) {
@@ -575,13 +647,11 @@ __device__ __forceinline__ double scale_ff(float s, float lo, float sh, float sl
   return (double)p + (double)__fmaf_rn(s, sl, __fmaf_rn(lo, sh, err));
 }
 
-template <int TPP>
-__device__ __forceinline__ void vertex_iso_cubic_body(const KArgs& a, int gt) {
-  if (!full_list_current(a)) return;
+template <int TPP, class Rows>
+__device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R) {
   const int i = gt / TPP, l = gt % TPP;
   const bool valid = i < a.n;
   const size_t n = (size_t)a.n;
-  const unsigned jmax = (unsigned)a.n - 1u;
   IsoAcc A;
   A.fx = A.fy = A.fz = A.cx = A.cy = A.cz = A.s12 = A.s6 = make_float2(0.f, 0.f);
   A.nin = 0;
@@ -589,35 +659,35 @@ __device__ __forceinline__ void vertex_iso_cubic_body(const KArgs& a, int gt) {
   int cnt = 0;
   uint4 si = make_uint4(0u, 0u, 0u, 0u);
   if (valid) {
-    const int4* nb4 = (const int4*)a.nbr + i;
     si = __ldg(a.fxp + i);
     cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
     const int ng = (cnt + 3) >> 2, nfull = cnt >> 2;
-    int4 cur = load_group(nb4, l, ng, n);
+    int4 cur = R.group(l, ng, n);
     // the list streams from DRAM: groups further ahead are requested into L2 so that their loads
     // meet L2 rather than DRAM latency
 #pragma unroll
     for (int d = 2; d < kListPrefetch; d++)
-      if (l + d * TPP < ng) prefetch_l2(nb4 + (size_t)(l + d * TPP) * n);
+      if (l + d * TPP < ng) R.prefetch(l + d * TPP, n);
     int g = l;
     for (; g < nfull; g += TPP) {  // groups of four entries that are all in the list
-      const int4 nxt = load_group(nb4, g + TPP, ng, n);
-      if (g + kListPrefetch * TPP < ng) prefetch_l2(nb4 + (size_t)(g + kListPrefetch * TPP) * n);
-      iso_group<false>(a, si, cur, 4, jmax, A);
+      const int4 nxt = R.group(g + TPP, ng, n);
+      if (g + kListPrefetch * TPP < ng) R.prefetch(g + kListPrefetch * TPP, n);
+      iso_group<false>(a, si, cur, 4, R, A);
       cur = nxt;
     }
-    if (g < ng) iso_group<true>(a, si, cur, cnt - 4 * g, jmax, A);  // the partial last group
+    if (g < ng) iso_group<true>(a, si, cur, cnt - 4 * g, R, A);  // the partial last group
   }
   if (A.bmin <= a.rwca2_band_s) {
     // pairs near rc: take the side of the exact FP64 definition, re-walking this lane's entries
     // (groups l, l + TPP, ...) and correcting those whose FP32 decision differs
     for (int k0 = 4 * l; k0 < cnt; k0 += 4 * TPP)
       for (int k = k0; k < min(k0 + 4, cnt); k++) {
-        const unsigned j = min((unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n)), jmax);
-        const uint4 sj = __ldg(a.fxp + j);
+        const unsigned v = R.entry(a, k, i, n);
+        const uint4 sj = R.coords(a, v);
         const int ix = (int)(sj.x - si.x), iy = (int)(sj.y - si.y), iz = (int)(sj.z - si.z);
         const float r2 = r2_scaled(a, ix, iy, iz);
         if (!(r2 >= a.rwca2_lo_s && r2 < a.rwca2_hi_s)) continue;
+        const unsigned j = R.slot(a, v);
         const bool fp32_in = r2 < a.rwca2_s;
         const bool exact_in = exact_r2(a.pos[i], a.pos[j], a) < a.rwca2_d;
         if (fp32_in == exact_in) continue;
@@ -668,6 +738,42 @@ __device__ __forceinline__ void vertex_iso_cubic_body(const KArgs& a, int gt) {
                                   scale_ff(S[2], lo[2], a.fscale_hi, a.fscale_lo), (double)e);
     a.virial[i] = (double)w;
   }
+}
+
+template <int TPP>
+__device__ __forceinline__ void vertex_iso_cubic_body(const KArgs& a, int gt) {
+  if (!full_list_current(a)) return;
+  GlobalRows R;
+  R.nb4 = (const int4*)a.nbr + min(gt / TPP, a.n - 1);
+  R.jmax = (unsigned)a.n - 1u;
+  vertex_iso_cubic_rows<TPP>(a, gt, R);
+}
+
+// The block-local list: the block (MD_LOCAL_BLOCK threads, one per slot) first stages its halo's
+// coordinates in shared memory, cell by cell, one warp per cell.
+__device__ __forceinline__ void vertex_iso_local_body(const KArgs& a, uint4* halo_smem) {
+  const int t = threadIdx.x, b = blockIdx.x;
+  const int i = b * MD_LOCAL_BLOCK + t;
+  const int32_t* tab = a.local_tab + (size_t)b * kLocalRec;
+  LocalRows R;
+  R.tab = tab;
+  R.U = min(max(tab[0], 0), MD_LOCAL_MAX_CELLS);
+  R.H = max(tab[1], 0);
+  R.jmax = (unsigned)a.n - 1u;
+  R.nb2 = (const uint2*)a.nbr + min(i, a.n - 1);
+  const bool staged = R.H <= kLocalSmem && tab[2] == 0;
+  R.halo = staged ? halo_smem : nullptr;
+  if (staged) {
+    const int w = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
+    for (int k = w; k < R.U; k += nw) {
+      const int first = tab[4 + 2 * k], off = tab[4 + 2 * k + 1];
+      const int end = (k + 1 < R.U) ? tab[4 + 2 * (k + 1) + 1] : R.H;
+      for (int q = lane; q < end - off; q += 32)
+        halo_smem[off + q] = __ldg(a.fxp + min((unsigned)(first + q), R.jmax));
+    }
+  }
+  __syncthreads();
+  vertex_iso_cubic_rows<1>(a, i, R);
 }
 
 template <int TPP, bool CUBIC>
@@ -769,6 +875,12 @@ __device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
 
 template <int TPP, bool CUBIC>
 __global__ void __launch_bounds__(256, 4) k_vertex_iso_mixed(KArgs a) {
+  if (TPP == 1 && CUBIC && a.local_ok && (a.status[MD_STATUS_LISTS] & MD_LIST_FULL_LOCAL)) {
+    // launched with MD_LOCAL_BLOCK threads and kLocalSmem halo slots of dynamic shared memory
+    extern __shared__ uint4 halo_smem[];
+    vertex_iso_local_body(a, halo_smem);
+    return;
+  }
   vertex_iso_mixed_body<TPP, CUBIC>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -1036,7 +1148,7 @@ __device__ __forceinline__ void edge_finalize_one(const KArgs& a, int i) {
   a.force[i] = make_double4_32a((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y,
                                 (double)hi.z + (double)lo.z, (double)hi.w);
   a.virial[i] = (double)lo.w;
-  if (a.model == MD_PATCHY) {
+  if (is_patchy(a.model)) {
     const float4 th = a.acc[2 * n + i], tl = a.acc[3 * n + i];
     a.torque[i] = make_double4_32a((double)th.x + (double)tl.x, (double)th.y + (double)tl.y,
                                    (double)th.z + (double)tl.z, 0.0);
@@ -1219,7 +1331,7 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
 __device__ __forceinline__ void newton_finalize_one(const KArgs& a, int i) {
   if (!(a.status[MD_STATUS_LISTS] & MD_LIST_NEWTON)) return;  // the force kernel wrote nothing
   const int m = a.force_copies;
-  const bool patchy = a.model == MD_PATCHY;
+  const bool patchy = is_patchy(a.model);
   if (a.precision == MD_MIXED) {
     float fs[4] = {0.f, 0.f, 0.f, 0.f}, fc[4] = {0.f, 0.f, 0.f, 0.f}, vs = 0.f, vc = 0.f;
     float ts[3] = {0.f, 0.f, 0.f}, tcm[3] = {0.f, 0.f, 0.f};
@@ -1361,7 +1473,7 @@ __global__ void __launch_bounds__(256) k_edge_store(KArgs a) {
 __device__ __forceinline__ void edge_store_reduce_one(const KArgs& a, int i) {
   const int64_t e0 = a.half_start[i], e1 = min(a.half_start[i + 1], a.max_pairs);
   const int64_t p0 = a.jstart[i], p1 = a.jstart[i + 1];
-  const bool patchy = a.model == MD_PATCHY;
+  const bool patchy = is_patchy(a.model);
   if (a.precision == MD_MIXED) {
     const float4* A = (const float4*)a.estore;
     const float4* Bk = A + a.max_pairs;

@@ -39,7 +39,7 @@ __global__ void k_get_forces(KArgs a, double4_32a* fout, double4_32a* tout) {
   fout[i] = a.force[i];
   if (tout) {
     double4_32a t = make_double4_32a(0.0, 0.0, 0.0, a.virial[i]);
-    if (a.model == MD_PATCHY) {
+    if (is_patchy(a.model)) {
       const double4_32a tt = a.torque[i];
       t.x = tt.x; t.y = tt.y; t.z = tt.z;
     }

@@ -84,6 +84,59 @@ __device__ __forceinline__ unsigned long long* energy_accumulators(const KArgs& 
   return (unsigned long long*)a.block_partials;
 }
 
+// ---- thermostat: momentum refresh with counter-based random numbers ------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64-bit products whose
+// high halves are mixed with the other counter words and the round key, the key advanced by two Weyl
+// constants per round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double unit_open(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+// Two standard normals from two words (Box-Muller)
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& n0, double& n1) {
+  const double r = sqrt(-2.0 * log(unit_open(a)));
+  double sn, cs;
+  sincos(6.283185307179586476925286766559 * unit_open(b), &sn, &cs);
+  n0 = r * cs;
+  n1 = r * sn;
+}
+
+// The step whose opening half kick this launch performs (FIRST: the counter as it stands; MIDDLE:
+// one more, since the closing kick of the previous step is fused in).
+__device__ __forceinline__ bool thermostat_step(const KArgs& a, int mode, uint32_t& s) {
+  if (a.thermo_every <= 0 || (mode != 0 && mode != 1)) return false;
+  const int st = a.status[MD_STATUS_STEPS] + (mode == 1 ? 1 : 0);
+  s = (uint32_t)st;
+  return st > 0 && st % a.thermo_every == 0;
+}
+
+// Whether particle `id` is refreshed at step s; if so its new velocity (and angular momentum) in v, l.
+__device__ __forceinline__ bool thermostat_draw(const KArgs& a, uint32_t s, uint32_t id, double v[3], double l[3]) {
+  const uint2 key = make_uint2(a.seed, 0u);
+  const uint4 r0 = philox4x32_10(make_uint4(s, id, 0u, 0u), key);
+  if (!(unit_open(r0.x) < a.thermo_prob)) return false;
+  const uint4 r1 = philox4x32_10(make_uint4(s, id, 1u, 0u), key);
+  double n[6];
+  box_muller(r0.y, r0.z, n[0], n[1]);
+  box_muller(r1.x, r1.y, n[2], n[3]);
+  box_muller(r1.z, r1.w, n[4], n[5]);
+  for (int c = 0; c < 3; c++) {
+    v[c] = a.sigma_v * n[c];
+    l[c] = a.sigma_l * n[3 + c];
+  }
+  return true;
+}
+
 // Whether this launch reduces energies: always for LAST and ENERGY, for MIDDLE when the step it
 // completes is a multiple of energy_every.  The step counter is read before k_step_decide advances it.
 __device__ __forceinline__ bool energy_step(const KArgs& a, int mode) {
@@ -98,14 +151,18 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
   const bool valid = i < a.n;
   const bool drift = (mode == 0 || mode == 1);
   const bool energies = energy_step(a, mode);
-  const bool patchy = a.model == MD_PATCHY;
+  const bool patchy = is_patchy(a.model);
   const bool mixed = a.precision == MD_MIXED;
   double kt = 0.0, kr = 0.0, u = 0.0, w = 0.0;  // per-particle energy terms (FP64 values)
   float ktf = 0.f, krf = 0.f;                    // mixed: kinetic terms in FP32
   float disp2 = 0.f;
+  uint32_t tstep = 0;
+  const bool thermo = thermostat_step(a, mode, tstep);
   if (valid) {
     double4_32a v = a.vel[i];
     const double4_32a F = a.force[i];
+    double vn[3], ln[3];
+    const bool refresh = thermo && thermostat_draw(a, tstep, (uint32_t)a.id[i], vn, ln);
     if (energies) {
       u = F.w;
       w = a.virial[i];
@@ -118,9 +175,23 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
                       vz = (float)v.z + (float)F.z * a.half_dt_over_m_f;
           ktf = a.half_mass_f * (vx * vx + vy * vy + vz * vz);
         }
-        v.x = fma(F.x, a.dt_over_m, v.x);
-        v.y = fma(F.y, a.dt_over_m, v.y);
-        v.z = fma(F.z, a.dt_over_m, v.z);
+        if (refresh) {  // the refreshed velocity replaces v_n; then the opening half kick
+          v.x = fma(F.x, a.half_dt_over_m, vn[0]);
+          v.y = fma(F.y, a.half_dt_over_m, vn[1]);
+          v.z = fma(F.z, a.half_dt_over_m, vn[2]);
+        } else {
+          v.x = fma(F.x, a.dt_over_m, v.x);
+          v.y = fma(F.y, a.dt_over_m, v.y);
+          v.z = fma(F.z, a.dt_over_m, v.z);
+        }
+      } else if (refresh) {
+        v.x = fma(F.x, a.half_dt_over_m, v.x);
+        v.y = fma(F.y, a.half_dt_over_m, v.y);
+        v.z = fma(F.z, a.half_dt_over_m, v.z);
+        kt = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+        v.x = fma(F.x, a.half_dt_over_m, vn[0]);
+        v.y = fma(F.y, a.half_dt_over_m, vn[1]);
+        v.z = fma(F.z, a.half_dt_over_m, vn[2]);
       } else {
         v.x = fma(F.x, a.half_dt_over_m, v.x);
         v.y = fma(F.y, a.half_dt_over_m, v.y);
@@ -131,6 +202,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
         v.z = fma(F.z, a.half_dt_over_m, v.z);
       }
     } else if (mode == 0 || mode == 2) {
+      if (refresh) v = make_double4_32a(vn[0], vn[1], vn[2], v.w);  // FIRST: redraw, then kick
       v.x = fma(F.x, a.half_dt_over_m, v.x);
       v.y = fma(F.y, a.half_dt_over_m, v.y);
       v.z = fma(F.z, a.half_dt_over_m, v.z);
@@ -156,8 +228,10 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
         } else {
           kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
         }
+        if (refresh) L = make_double4_32a(ln[0], ln[1], ln[2], L.w);
         L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
       } else if (mode == 0 || mode == 2) {
+        if (refresh) L = make_double4_32a(ln[0], ln[1], ln[2], L.w);
         L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
       }
       if (mode == 2 || mode == 3) {

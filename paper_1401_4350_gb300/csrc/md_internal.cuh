@@ -32,6 +32,13 @@ enum {
   SCR_WORDS = 64
 };
 
+// Block-local full list: per block of MD_LOCAL_BLOCK slots, int32 words [4 header][2 * MD_LOCAL_MAX_CELLS].
+constexpr int kLocalRec = 4 + 2 * MD_LOCAL_MAX_CELLS;
+constexpr int kLocalSmem = 3072;  // halo slots staged in shared memory (48 KB of uint4)
+
+// Models with orientations, patch sites and torques.
+__host__ __device__ __forceinline__ bool is_patchy(int model) { return model == MD_PATCHY || model == MD_PATCHY_POW; }
+
 // Everything a kernel needs, passed by value.
 struct KArgs {
   int32_t n;
@@ -83,6 +90,13 @@ struct KArgs {
   double patch_reach2_d;                  // centre distance^2 beyond which every patch term vanishes
   float patch_reach2_f;
   double patch_body[MD_MAX_PATCH][3];
+  int32_t pow_core;                       // MD_PATCHY_POW: (sigma/r)^200 centre repulsion instead of WCA
+  float patch_qcut_f;                     // MD_PATCHY_POW: (patch_rc / delta)^2 (3e38: no cut-off)
+  double patch_qcut_d;
+  // thermostat (momentum refresh)
+  int32_t thermo_every;
+  uint32_t seed;
+  double thermo_prob, sigma_v, sigma_l;   // probability, sqrt(kT / m), sqrt(kT I)
   // integration
   double dt, inv_mass, half_dt_over_m, dt_over_m, mass, inertia, inv_inertia;
   float dt_over_m_f, half_dt_over_m_f, dt_f, inv_inertia_f, half_mass_f;
@@ -110,6 +124,8 @@ struct KArgs {
   float4* acc;           // mixed edge accumulators: F hi [n], F lo [n], tau hi [n], tau lo [n]
   void* copies;          // Newton-vertex reaction copies (layout of md_ws_layout.copies)
   int32_t force_copies;  // m
+  int32_t local_ok;      // the block-local full list may be built (see local_list_eligible)
+  int32_t* local_tab;    // block-local full list: per block a header int4 + int2[MD_LOCAL_MAX_CELLS]
   void* estore;          // per-edge store (A, B, C blocks of max_pairs entries), edge_store = 1
   int64_t* jstart;       // by-partner index rows [n + 1]
   int32_t* jedge;        // by-partner index entries [max_pairs]

@@ -79,11 +79,11 @@ extern "C" int md_build_cells_static(const md_params* p, md_state* s, int32_t* c
               p->n, kStaticMaxN);
     return MD_ERR_INVALID;
   }
-  if (!s || !s->pos || !s->vel || !s->id || (p->model == MD_PATCHY && (!s->quat || !s->angmom))) {
+  if (!s || !s->pos || !s->vel || !s->id || (is_patchy(p->model) && (!s->quat || !s->angmom))) {
     set_error("md_build_cells_static: state arrays pos, vel, id (and quat, angmom for patchy) are required");
     return MD_ERR_INVALID;
   }
-  if (!cell_start || !fxp || (p->model == MD_PATCHY && !patch_lab)) {
+  if (!cell_start || !fxp || (is_patchy(p->model) && !patch_lab)) {
     set_error("md_build_cells_static: cell_start and fxp (and patch_lab for patchy) are required");
     return MD_ERR_INVALID;
   }

@@ -8,6 +8,18 @@ namespace mdgb {
 
 // Builds the full-list row of slot i (i < a.n) and returns its length; the caller reduces the
 // lengths of its warp into MD_STATUS_NEED_NEIGH.
+// Whether j is a Verlet neighbour of i: FP32 filter on the fixed-point separation, and the exact FP64
+// decision of the definition inside a relative band of 1e-5 around rv^2.
+__device__ __forceinline__ bool verlet_candidate_in(const KArgs& a, const uint4& si, const uint4& sj, int i, int j) {
+  const float ddx = (float)(int)(sj.x - si.x) * a.fxp_unit[0];
+  const float ddy = (float)(int)(sj.y - si.y) * a.fxp_unit[1];
+  const float ddz = (float)(int)(sj.z - si.z) * a.fxp_unit[2];
+  const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  bool in = r2 < a.rv2_lo;
+  if (!in && r2 < a.rv2_hi) in = exact_r2(a.pos[i], a.pos[j], a) < a.rv2_d;
+  return in;
+}
+
 __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i, bool newton = false) {
   int cnt = 0;
   {
@@ -38,13 +50,7 @@ __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i, bool newto
           const int b = a.cell_start[c], e = a.cell_start[c + 1];
           for (int j = b; j < e; j++) {
             if (j == i) continue;
-            const uint4 sj = a.fxp[j];
-            float ddx = (float)(int)(sj.x - si.x) * a.fxp_unit[0];
-            float ddy = (float)(int)(sj.y - si.y) * a.fxp_unit[1];
-            float ddz = (float)(int)(sj.z - si.z) * a.fxp_unit[2];
-            float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            bool in = r2 < a.rv2_lo;
-            if (!in && r2 < a.rv2_hi) in = exact_r2(a.pos[i], a.pos[j], a) < a.rv2_d;
+            bool in = verlet_candidate_in(a, si, a.fxp[j], i, j);
             // Newton list: the pair goes to i when i < j and i + j is odd, or i > j and i + j even
             if (newton) in = in && ((i < j) == (((i + j) & 1) != 0));
             if (in) {
@@ -124,6 +130,86 @@ __device__ __forceinline__ void jindex_sort_one(const KArgs& a, int j) {
     }
     a.jedge[m + 1] = v;
   }
+}
+
+// ---- block-local full list ----------------------------------------------------------------------
+// For a block of MD_LOCAL_BLOCK consecutive slots, the halo is the union of the cells neighbouring the
+// block's particles, laid out cell after cell in increasing slot order; each list entry is the 16-bit
+// position of the neighbour in that halo.  Pass 1 collects the distinct neighbour cells of the block in
+// a shared hash set, pass 2 orders them by first slot and assigns halo offsets, pass 3 writes every
+// particle's row (same membership test as the global list, same row order).
+
+constexpr int kLocalHash = 2 * MD_LOCAL_MAX_CELLS;
+
+struct LocalBuildSmem {
+  int key[kLocalHash];            // cell id or -1
+  int slot[kLocalHash];           // its index in ucell
+  int ucell[MD_LOCAL_MAX_CELLS];  // distinct neighbour cells (row-major ids)
+  int ustart[MD_LOCAL_MAX_CELLS], ucount[MD_LOCAL_MAX_CELLS], uoff[MD_LOCAL_MAX_CELLS], order[MD_LOCAL_MAX_CELLS];
+  int nuniq;
+  int overflow;
+  int total;
+};
+
+__device__ __forceinline__ int cell_rank_of(const KArgs& a, int c) { return a.cell_rank ? a.cell_rank[c] : c; }
+
+// Visits the (up to) 27 neighbour cells of the cell holding fixed-point position si.
+template <class F>
+__device__ __forceinline__ void for_neighbour_cells(const KArgs& a, const uint4& si, F f) {
+  const int ci[3] = {fixed_cell(si.x, a.ncell[0]), fixed_cell(si.y, a.ncell[1]), fixed_cell(si.z, a.ncell[2])};
+  for (int dz = -1; dz <= 1; dz++) {
+    int z = ci[2] + dz;
+    z += (z < 0) ? a.ncell[2] : 0;
+    z -= (z >= a.ncell[2]) ? a.ncell[2] : 0;
+    for (int dy = -1; dy <= 1; dy++) {
+      int y = ci[1] + dy;
+      y += (y < 0) ? a.ncell[1] : 0;
+      y -= (y >= a.ncell[1]) ? a.ncell[1] : 0;
+      for (int dx = -1; dx <= 1; dx++) {
+        int x = ci[0] + dx;
+        x += (x < 0) ? a.ncell[0] : 0;
+        x -= (x >= a.ncell[0]) ? a.ncell[0] : 0;
+        f((z * a.ncell[1] + y) * a.ncell[0] + x);
+      }
+    }
+  }
+}
+
+// Shared hash set of cell ids: returns the cell's index in ucell, inserting it if `insert`
+// (-1 if absent or if the set is full).  Probing is bounded by the table size.
+__device__ __forceinline__ int local_cell_slot(LocalBuildSmem& S, int c, bool insert) {
+  int h = (int)(((unsigned)c * 2654435761u) >> 22) & (kLocalHash - 1);
+  for (int probe = 0; probe < kLocalHash; probe++) {
+    int k = S.key[h];
+    if (k == c) {
+      int u;
+      // an inserter publishes slot[h] after winning the key; wait (bounded) for it
+      for (int w = 0; w < 1 << 16; w++) {
+        u = ((volatile int*)S.slot)[h];
+        if (u >= 0) return u < MD_LOCAL_MAX_CELLS ? u : -1;
+      }
+      return -1;
+    }
+    if (k == -1) {
+      if (!insert) return -1;
+      k = atomicCAS(&S.key[h], -1, c);
+      if (k == -1) {
+        const int u = atomicAdd(&S.nuniq, 1);
+        if (u < MD_LOCAL_MAX_CELLS) {
+          S.ucell[u] = c;
+          atomicExch(&S.slot[h], u);
+          return u;
+        }
+        S.overflow = 1;
+        atomicExch(&S.slot[h], MD_LOCAL_MAX_CELLS);  // marks the entry as unusable
+        return -1;
+      }
+      if (k == c) continue;  // re-read the slot on the next probe of the same h
+    }
+    h = (h + 1) & (kLocalHash - 1);
+  }
+  S.overflow = 1;
+  return -1;
 }
 
 }  // namespace mdgb

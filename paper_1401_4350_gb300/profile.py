@@ -35,6 +35,7 @@ def main(argv=None):
     ap.add_argument("--what", default="forces", choices=["forces", "build", "step"])
     ap.add_argument("--tpp", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--order", default="rows", choices=["rows", "hilbert"])
     a = ap.parse_args(argv)
     mdbuild.build()
     B.load()
@@ -42,7 +43,7 @@ def main(argv=None):
     s = WORKLOADS[a.workload]()
     prec = B.MD_MIXED if a.precision == "mixed" else B.MD_FP64
     path = B.MD_VERTEX if a.path == "vertex" else B.MD_EDGE
-    sim = Simulation(s, prec, tpp=a.tpp)
+    sim = Simulation(s, prec, tpp=a.tpp, cell_order=B.MD_ORDER_HILBERT if a.order == "hilbert" else B.MD_ORDER_ROWS)
     sim.prepare(path)
     if a.what == "forces":
         fn = sim.forces_vertex if path == B.MD_VERTEX else sim.forces_edge
@@ -64,7 +65,20 @@ def main(argv=None):
         times.append(e0.elapsed_time(e1))
     status = sim.status()
     assert status[B.MD_STATUS_CODE] == 0, status
-    print(f"{a.workload} {a.precision} {a.path} {a.what}: median {statistics.median(times):.4f} ms over {a.reps}")
+    entries = int(sim.view("nbr_count", torch.int32, s.n).sum().item())
+    print(f"{a.workload} {a.precision} {a.path} {a.what}: median {statistics.median(times):.4f} ms over {a.reps}; "
+          f"n={s.n} list_entries={entries} kernel_sources_sha256={source_digest()}")
+
+
+def source_digest() -> str:
+    """sha256 of the force-kernel sources (the same digest bench.py checks before it quotes a capture)."""
+    import hashlib
+    import os
+    h = hashlib.sha256()
+    for f in ("md_forces.cuh", "md_forces.cu", "md_internal.cuh"):
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 if __name__ == "__main__":

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import binding as B
-from .systems import System, LJ, WCA, PATCHY
+from .systems import System, LJ, WCA, PATCHY, PATCHY_POW, PATCHY_KINDS
 
 
 def default_capacities(system: System, slack: float = 1.6):
@@ -26,15 +26,15 @@ def default_capacities(system: System, slack: float = 1.6):
 
 def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, tpp: int = 1, block: int = 0,
                 trace_capacity: int = 0, energy_every: int = 1, force_copies: int = 0,
-                cell_order: int = 0, edge_store: int = 0) -> B.md_params:
+                cell_order: int = 0, edge_store: int = 0, list_format: int = 0) -> B.md_params:
     mn, mp = default_capacities(system)
     p = B.md_params()
     p.n = system.n
-    p.model = {LJ: B.MD_LJ, WCA: B.MD_WCA, PATCHY: B.MD_PATCHY}[system.kind]
+    p.model = {LJ: B.MD_LJ, WCA: B.MD_WCA, PATCHY: B.MD_PATCHY, PATCHY_POW: B.MD_PATCHY_POW}[system.kind]
     p.precision = precision
     p.max_neigh = int(max_neigh or mn)
     p.max_pairs = int(max_pairs or mp)
-    p.n_patch = len(system.patches) if system.kind == PATCHY else 0
+    p.n_patch = len(system.patches) if system.kind in PATCHY_KINDS else 0
     p.threads_per_particle = tpp
     p.block_size = block
     p.trace_capacity = trace_capacity
@@ -42,6 +42,7 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
     p.force_copies = force_copies
     p.cell_order = cell_order
     p.edge_store = edge_store
+    p.list_format = list_format
     for c in range(3):
         p.box[c] = float(system.box[c])
     p.rc, p.skin, p.dt, p.mass, p.inertia = system.rc, system.skin, system.dt, system.mass, system.inertia
@@ -49,16 +50,21 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
     for a, v in enumerate(np.asarray(system.patches)):
         for c in range(3):
             p.patch[a][c] = float(v[c])
+    p.patch_rc = float(system.patch_rc)
+    p.kT = float(system.temperature)
+    p.thermostat_every = int(system.thermostat_every)
+    p.thermostat_prob = float(system.thermostat_prob)
+    p.seed = int(system.seed) & 0xFFFFFFFF
     return p
 
 
 class Simulation:
     def __init__(self, system: System, precision: int = B.MD_MIXED, max_neigh=None, max_pairs=None, tpp: int = 1,
                  block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None, energy_every: int = 1,
-                 force_copies: int = 0, cell_order: int = 0, edge_store: int = 0):
+                 force_copies: int = 0, cell_order: int = 0, edge_store: int = 0, list_format: int = 0):
         self.system = system
         self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity, energy_every,
-                                  force_copies, cell_order, edge_store)
+                                  force_copies, cell_order, edge_store, list_format)
         rc = B.md_check_params(self.params)
         if rc != B.MD_OK:
             raise B.MDError(rc, B.last_error())
@@ -69,8 +75,8 @@ class Simulation:
         f64 = dict(dtype=torch.float64, device=self.device)
         self.pos = torch.zeros((n, 4), **f64)
         self.vel = torch.zeros((n, 4), **f64)
-        self.quat = torch.zeros((n, 4), **f64) if system.kind == PATCHY else None
-        self.angmom = torch.zeros((n, 4), **f64) if system.kind == PATCHY else None
+        self.quat = torch.zeros((n, 4), **f64) if system.kind in PATCHY_KINDS else None
+        self.angmom = torch.zeros((n, 4), **f64) if system.kind in PATCHY_KINDS else None
         self.id = torch.arange(n, dtype=torch.int32, device=self.device)
         self.ws = torch.empty(int(self.layout.total), dtype=torch.uint8, device=self.device)
         assert self.ws.data_ptr() % 256 == 0
@@ -145,7 +151,7 @@ class Simulation:
         inv[self._order()] = torch.arange(n, device=self.device)
         fo = fo[inv].cpu().numpy()
         to = to[inv].cpu().numpy()
-        T = to[:, :3] if self.system.kind == PATCHY else None
+        T = to[:, :3] if self.system.kind in PATCHY_KINDS else None
         return fo[:, :3], fo[:, 3], T, to[:, 3]
 
     def positions(self):
@@ -185,6 +191,37 @@ class Simulation:
         a, b = torch.minimum(oi, oj), torch.maximum(oi, oj)
         key = a * n + b
         key, counts = torch.unique(key, return_counts=True)
+        return (torch.stack([key // n, key % n], 1).cpu().numpy(), counts.cpu().numpy(), int(mask.sum()))
+
+    def local_list_pairs(self):
+        """Like full_list_pairs, for a full list held in the block-local format: each uint16 entry is a halo
+        position, mapped to a slot through its block's cell table (first slot, halo offset)."""
+        n = self.system.n
+        cnt = self.view("nbr_count", torch.int32, n).long()
+        cap = self.params.max_neigh
+        ng = (cap + 3) // 4
+        raw = self.view("nbr", torch.int16, ng * n * 4).view(ng, n, 4).permute(0, 2, 1).reshape(ng * 4, n)[:cap]
+        loc = raw.long() & 0xFFFF
+        nblk = (n + B.MD_LOCAL_BLOCK - 1) // B.MD_LOCAL_BLOCK
+        rec = 4 + 2 * B.MD_LOCAL_MAX_CELLS
+        tab = self.ws[self.layout.local_tab:self.layout.local_tab + 4 * rec * nblk].view(torch.int32).view(nblk, rec)
+        U = tab[:, 0].long()
+        first = tab[:, 4::2].long()
+        off = tab[:, 5::2].long()
+        big = torch.iinfo(torch.int64).max
+        cell_idx = torch.arange(B.MD_LOCAL_MAX_CELLS, device=self.device)[None, :]
+        off_masked = torch.where(cell_idx < U[:, None], off, torch.full_like(off, big))
+        k = torch.arange(cap, device=self.device)[:, None]
+        mask = k < cnt[None, :]
+        ii = torch.arange(n, device=self.device)[None, :].expand(cap, n)[mask]
+        v = loc[mask]
+        blk = ii // B.MD_LOCAL_BLOCK
+        u = torch.searchsorted(off_masked[blk], v[:, None], right=True).squeeze(1) - 1
+        jj = first[blk, u] + (v - off[blk, u])
+        ids = self._order()
+        oi, oj = ids[ii], ids[jj]
+        a, b = torch.minimum(oi, oj), torch.maximum(oi, oj)
+        key, counts = torch.unique(a * n + b, return_counts=True)
         return (torch.stack([key // n, key % n], 1).cpu().numpy(), counts.cpu().numpy(), int(mask.sum()))
 
     def half_list_pairs(self):

@@ -19,6 +19,11 @@ velocities and orientations.  The recipes:
   motion removed, rescaled so that the kinetic energy is (3N - 3) T / 2.
 * Patchy orientations: normalised 4-D Gaussians (uniform unit quaternions);
   angular momenta N(0, T I) per lab-frame component, rescaled to 3N T / 2.
+* The paper's patchy form (Sec. Models): two patch sites at the poles of the body z axis,
+  0.5 sigma from the centre (M = 2); same placement and orientation recipes as above.
+* Thermostat settings (the paper's Brownian NVT runs, Sec. Methods): momenta of each
+  particle redrawn with probability 0.1 every 100 steps (a reading: the paper does not
+  give them); the kT of each system is its temperature.
 * Random numbers: numpy PCG64 seeded per system (1000 + configuration index;
   replica r of the batch uses 5000 + r).
 """
@@ -29,7 +34,8 @@ from typing import Optional
 
 import numpy as np
 
-LJ, WCA, PATCHY = 0, 1, 2
+LJ, WCA, PATCHY, PATCHY_POW = 0, 1, 2, 3
+PATCHY_KINDS = (PATCHY, PATCHY_POW)
 WCA_RC = 2.0 ** (1.0 / 6.0)
 
 # Three patch sites 120 degrees apart in the body xy-plane, 0.5 sigma from the centre.
@@ -37,6 +43,8 @@ PATCH_DIRS = np.array([[1.0, 0.0, 0.0],
                        [-0.5, np.sqrt(3.0) / 2.0, 0.0],
                        [-0.5, -np.sqrt(3.0) / 2.0, 0.0]])
 PATCH_RADIUS = 0.5
+# The paper's patchy model: M = 2 sites at the poles.
+PATCH_DIRS_POLAR = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
 
 
 @dataclass
@@ -60,6 +68,10 @@ class System:
     delta: float = 0.12
     patches: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
     name: str = ""
+    patch_rc: float = 0.0           # PATCHY_POW: patch-pair cut-off
+    thermostat_every: int = 0       # momentum refresh every so many steps (0: NVE)
+    thermostat_prob: float = 0.0
+    seed: int = 0
 
     @property
     def n(self) -> int:
@@ -157,6 +169,29 @@ def make_patchy(n: int, rho: float = 0.3, temperature: float = 0.15, seed: int =
         L *= np.sqrt(0.5 * 3 * n * temperature / krot)
     return System(PATCHY, pos, vel, box, rc, skin, dt, temperature, quat=quat, angmom=L, inertia=inertia,
                   patches=PATCH_DIRS * PATCH_RADIUS, name=f"patchy_n{n}_rho{rho}")
+
+
+def make_patchy_pow(n: int, rho: float = 0.3, temperature: float = 0.15, seed: int = 1005, rc: float = 1.18,
+                    patch_rc: float = 0.18, skin: float = 0.2, dt: float = 0.001, inertia: float = 0.1,
+                    thermostat_every: int = 100, thermostat_prob: float = 0.1) -> System:
+    """The paper's patchy form: (sigma/r)^200 core, two polar patches, patch pairs cut at 0.18 sigma
+    (so no centre pair beyond 1 + 0.18 sigma interacts), Brownian momentum refresh at kT."""
+    s = make_patchy(n, rho, temperature, seed, rc, skin, dt, inertia)
+    s.kind = PATCHY_POW
+    s.patches = PATCH_DIRS_POLAR * PATCH_RADIUS
+    s.patch_rc = patch_rc
+    s.thermostat_every, s.thermostat_prob, s.seed = thermostat_every, thermostat_prob, seed
+    s.name = f"patchy_pow_n{n}_rho{rho}"
+    return s
+
+
+def make_lj_nvt(n: int, rho: float, temperature: float = 1.8, seed: int = 1006, thermostat_every: int = 100,
+                thermostat_prob: float = 0.1) -> System:
+    """Lennard-Jones at the paper's state points (kT = 1.8) with the Brownian momentum refresh."""
+    s = make_lj(n, rho, temperature, seed)
+    s.thermostat_every, s.thermostat_prob, s.seed = thermostat_every, thermostat_prob, seed
+    s.name = f"lj_nvt_n{n}_rho{rho}"
+    return s
 
 
 def batch_specs(n_replicas: int = 512, seed: int = 1004):

@@ -50,6 +50,10 @@ def _lj_params(n=4000, precision=B.MD_MIXED):
     ("energy_every", -2, "energy_every"),
     ("force_copies", -1, "force_copies"),
     ("force_copies", 65, "force_copies"),
+    ("list_format", 2, "list_format"),
+    ("reserved", 1, "reserved"),
+    ("cell_order", 2, "cell_order"),
+    ("thermostat_every", -1, "thermostat_every"),
 ])
 def test_invalid_params_rejected(lib, field, value, needle):
     p = _lj_params()
@@ -89,7 +93,7 @@ def test_workspace_layout(lib, precision, kind):
     assert L.total == B.md_workspace_bytes(p) > 0
     offs = [getattr(L, f) for f in ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr",
                                     "nbr_count", "half_start", "pairs", "force", "virial", "torque",
-                                    "acc", "copies", "estore", "jstart", "jedge", "trace", "scratch")]
+                                    "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace", "scratch")]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and len(set(offs)) == len(offs)
     assert L.force_elem == 8
@@ -218,7 +222,7 @@ def test_edge_store_regions(lib, precision, kind):
     blocks = 3 if kind == "patchy" else 2
     assert L.jstart - L.estore >= elem * blocks * p.max_pairs
     assert L.jedge - L.jstart >= 8 * (s.n + 1)
-    assert L.trace - L.jedge >= 4 * p.max_pairs
+    assert L.local_tab - L.jedge >= 4 * p.max_pairs
     p.edge_store = 2
     assert B.md_check_params(p) == B.MD_ERR_INVALID
     p.edge_store = 1

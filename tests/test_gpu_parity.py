@@ -36,7 +36,7 @@ def Sim(*a, **k):
 
 def model_of(s):
     return oracle.Model(s.kind, tuple(s.box), s.rc, eps=s.eps, sigma=s.sigma, eps_p=s.eps_p, delta=s.delta,
-                        patches=s.patches)
+                        patches=s.patches, patch_rc=s.patch_rc)
 
 
 _cache = {}
