@@ -27,9 +27,29 @@ METRIC = "MD steps/s & pair-evals/s: vertex vs edge, mixed vs FP64 plain, on 1 G
 WORKLOAD = "lj_fluid_n1048576_rho0.85_T1.0_rc2.5_skin0.3_dt0.001"
 
 
+def replica_max(dist, x: float, device=None) -> float:
+    """Max of x over the ranks (the job's time is its slowest rank's); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, max_ms: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
+def make_system_seed(rank: int = 0) -> int:
+    """Seed of rank r's replica of the workload (each rank runs an independent system)."""
+    return 1001 + rank
+
+
 def make_system(rank: int = 0):
     from paper_1401_4350_gb300 import systems
-    return systems.make_lj(1_048_576, 0.85, 1.0, seed=1001 + rank)
+    return systems.make_lj(1_048_576, 0.85, 1.0, seed=make_system_seed(rank))
 
 
 # ------------------------------------------------------------------------------------------------
@@ -130,11 +150,7 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(dist, x, dev)
 
     def time_steps(sim, path, k, sampler=None):
         st0 = sim.status()
@@ -219,8 +235,8 @@ def run_ours(args, rank, world, dist):
     del sim
     torch.cuda.empty_cache()
 
-    # ---- the other decompositions / precisions on the same workload ----
-    if not args.no_variants:
+    # ---- the other decompositions / precisions on the same workload (one GPU only) ----
+    if not args.no_variants and world == 1:
         NW, ES = B.MD_VERTEX_NEWTON, B.MD_EDGE_STORE
         HIL = {"cell_order": B.MD_ORDER_HILBERT}
         for name, path, precision, k, opts in (
@@ -258,7 +274,7 @@ def run_ours(args, rank, world, dist):
                 "algorithmic_bytes_per_launch": alg, "force_kernel_ms": force_ms,
                 "force_share_of_step": force_ms / step_ms,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
-    value = world * args.steps / (ms * 1e-3)
+    value = job_throughput(world, args.steps, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -278,9 +294,9 @@ def run_ours(args, rank, world, dist):
         "clocks": clocks,
         "graph": not args.direct,
     }
-    if not args.no_batch:
+    if not args.no_batch and world == 1:
         line["batch"] = run_batch()
-    if not args.no_sweep:
+    if not args.no_sweep and world == 1:
         line["density_sweep"] = run_density_sweep()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system)

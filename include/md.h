@@ -322,6 +322,17 @@ int md_forces_vertex_newton(const md_params* p, md_state* s, void* ws, void* str
 int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, int32_t path, int32_t use_graph,
                    void* stream);
 
+/*
+ * md_autotune_system -- picks the fastest decomposition for this system on this GPU (generalising the
+ * paper's conclusion that the better path depends on the model and the density into a measurement):
+ * bins the particles, then for each candidate builds its lists and times five force evaluations
+ * (median, CUDA events on `stream`; the call synchronises): vertex with 1, 2, 4 and 8 threads per
+ * particle, edge, MD_VERTEX_NEWTON (when force_copies >= 1) and MD_EDGE_STORE (when edge_store = 1).
+ * Writes the winner to *path_out and p->threads_per_particle, leaves lists and forces prepared for it,
+ * and, if ms_out is not NULL, the seven median times in milliseconds (-1: candidate not available).
+ */
+int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, float* ms_out, void* stream);
+
 /* md_build_cells + md_build_verlet(lists for `path`) + the forces of `path`. */
 int md_prepare(const md_params* p, md_state* s, void* ws, int32_t path, void* stream);
 

@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
         "md_forces_edge": ([_P, _S, _V, _V], ctypes.c_int),
         "md_forces_vertex_newton": ([_P, _S, _V, _V], ctypes.c_int),
         "md_forces_edge_store": ([_P, _S, _V, _V], ctypes.c_int),
+        "md_autotune_system": ([_P, _S, _V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _V],
+                               ctypes.c_int),
         "md_step_verlet": ([_P, _S, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _V], ctypes.c_int),
         "md_prepare": ([_P, _S, _V, ctypes.c_int32, _V], ctypes.c_int),
         "md_get_forces": ([_P, _V, _V, _V, _V], ctypes.c_int),
@@ -192,6 +194,15 @@ def md_forces_edge(p, s, ws, stream=None):
 
 def md_forces_edge_store(p, s, ws, stream=None):
     return _check(load().md_forces_edge_store(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
+
+
+def md_autotune_system(p, s, ws, stream=None):
+    """(path, threads_per_particle, median ms of the seven candidates); p.threads_per_particle is updated."""
+    path = ctypes.c_int32(0)
+    ms = (ctypes.c_float * 7)()
+    _check(load().md_autotune_system(ctypes.byref(p), ctypes.byref(s), _ptr(ws), ctypes.byref(path), ms,
+                                     _stream(stream)))
+    return int(path.value), int(p.threads_per_particle), [float(x) for x in ms]
 
 
 def md_forces_vertex_newton(p, s, ws, stream=None):

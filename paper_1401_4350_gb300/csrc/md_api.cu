@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -718,6 +719,66 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
   }
   if (e == cudaSuccess) e = launch_integrate(a, 2, 0, 0ULL, st);
   return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_step_verlet");
+}
+
+int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, float* ms_out, void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc != MD_OK) return rc;
+  if (!path_out) { set_error("path_out is NULL"); return MD_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, ws, L);
+  cudaError_t e = launch_build_cells(a, nullptr, st);
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  // candidates: vertex with 1/2/4/8 threads per particle, edge, and the Newton and per-edge-store
+  // paths when the workspace has room for them
+  const int cand_path[7] = {MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_EDGE, MD_VERTEX_NEWTON, MD_EDGE_STORE};
+  const int cand_tpp[7] = {1, 2, 4, 8, 1, 1, 1};
+  float best = 3.0e38f;
+  int best_k = 0;
+  for (int k = 0; k < 7 && e == cudaSuccess; k++) {
+    float ms = -1.0f;
+    const bool usable = (cand_path[k] != MD_VERTEX_NEWTON || p->force_copies >= 1) &&
+                        (cand_path[k] != MD_EDGE_STORE || p->edge_store);
+    if (usable) {
+      md_params q = *p;
+      q.threads_per_particle = cand_tpp[k];
+      q.list_format = MD_FORMAT_GLOBAL;  // the workspace was laid out for p; timings use int32 lists
+      KArgs b = make_args(&q, s, ws, L);  // the layout does not depend on threads_per_particle
+      e = launch_build_verlet(b, list_kind(cand_path[k]), nullptr, st);
+      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_forces(b, cand_path[k], q.block_size, st);
+      float reps[5];
+      for (int r = 0; r < 5 && e == cudaSuccess; r++) {
+        e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess) e = launch_forces(b, cand_path[k], q.block_size, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&reps[r], ev[0], ev[1]);
+      }
+      if (e == cudaSuccess) {
+        std::sort(reps, reps + 5);
+        ms = reps[2];
+        if (ms < best) { best = ms; best_k = k; }
+      }
+    }
+    if (ms_out) ms_out[k] = ms;
+  }
+  if (e == cudaSuccess) {
+    // leave the workspace prepared for the choice
+    p->threads_per_particle = cand_tpp[best_k];
+    KArgs b = make_args(p, s, ws, L);
+    e = launch_build_verlet(b, list_kind(cand_path[best_k]), nullptr, st);
+    if (e == cudaSuccess) e = launch_forces(b, cand_path[best_k], p->block_size, st);
+    if (e == cudaSuccess) e = launch_integrate(b, 3, 0, 0ULL, st);  // energies, as md_prepare
+    *path_out = cand_path[best_k];
+  }
+  for (int k = 0; k < 2; k++)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_autotune_system");
 }
 
 int md_get_forces(const md_params* p, const void* ws, double* force_out, double* torque_out, void* stream) {

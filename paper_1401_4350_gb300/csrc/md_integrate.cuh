@@ -76,7 +76,12 @@ __device__ __forceinline__ double4_32a rotate(const KArgs& a, const double4_32a&
   return make_double4_32a(r.x / nq, r.y / nq, r.z / nq, r.w / nq);
 }
 
-__device__ __forceinline__ bool finite3(const double4_32a& p) { return isfinite(p.x) && isfinite(p.y) && isfinite(p.z); }
+// Finite iff the exponent field is not all ones; tested on the high words with integer operations
+// (the FP64 pipe is the scarce one in this kernel).
+__device__ __forceinline__ bool finite3(const double4_32a& p) {
+  const unsigned e = 0x7ff00000u;
+  return ((__double2hiint(p.x) & e) != e) & ((__double2hiint(p.y) & e) != e) & ((__double2hiint(p.z) & e) != e);
+}
 
 // The four energy accumulators (K_trans, K_rot, U, W) as 64-bit fixed-point words in 2^-32 units,
 // kept in the first 32 bytes of the block-partials scratch.

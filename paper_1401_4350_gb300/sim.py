@@ -127,6 +127,11 @@ class Simulation:
     def forces_edge_store(self):
         B.md_forces_edge_store(self.params, self.state(), self.ws, self._st())
 
+    def autotune(self):
+        """Choose the fastest path (and threads per particle) by timing every available candidate;
+        returns (path, threads_per_particle, median ms per candidate).  Lists and forces stay prepared."""
+        return B.md_autotune_system(self.params, self.state(), self.ws, self._st())
+
     def prepare(self, path=B.MD_VERTEX):
         B.md_prepare(self.params, self.state(), self.ws, path, self._st())
 
