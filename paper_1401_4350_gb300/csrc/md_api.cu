@@ -230,6 +230,14 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.rv2_d = rv * rv;
   a.rv2_lo = f32(a.rv2_d * (1.0 - 1e-5));
   a.rv2_hi = f32(a.rv2_d * (1.0 + 1e-5));
+  {
+    // integer separations differ from the FP64 ones by at most one unit per axis (two roundings of
+    // half a unit), so |r_u^2 - (r/u)^2| <= 2 sqrt(3) r/u + 3: a relative band of 4 / (rv/u) (+1e-9)
+    // around (rv/u)^2 holds every pair whose integer test could disagree with the FP64 definition
+    const double u = p->box[0] / 4294967296.0, rvu = rv / u, rel = 4.0 / rvu + 1e-9;
+    a.rv2_lo_u = (unsigned long long)floor(rvu * rvu * (1.0 - rel));
+    a.rv2_hi_u = (unsigned long long)ceil(rvu * rvu * (1.0 + rel));
+  }
   a.disp_thr2 = f32(0.25 * p->skin * p->skin * (1.0 - 1e-4));
   const double riso = p->model == MD_LJ ? p->rc : pow(2.0, 1.0 / 6.0) * p->sigma;
   a.rwca2_d = riso * riso;

@@ -9,27 +9,30 @@
 //   2 LAST  : v += F dt/2m, energies
 //   3 ENERGY: energies of the current state only
 // After a drift each thread refreshes the fixed-point coordinates (and patch sites) used by the
-// pair kernels and its squared displacement since the last Verlet build; k_step_decide then turns
-// the largest one into the rebuild decision (max > (skin/2)^2) and forms the FP64 energy totals.
+// pair kernels and its squared displacement since the last Verlet build; the last block to finish
+// turns the largest one into the rebuild decision (max > (skin/2)^2) and forms the FP64 energy totals.
 #include "md_integrate.cuh"
 
 namespace mdgb {
 
-__global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a, int mode) {
+// The integrate phase and, in the last block to finish, the step decision (one launch per phase).
+__global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a, int mode, int use_cond, unsigned long long cond_handle) {
   integrate_body(a, mode, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
-}
-
-__global__ void __launch_bounds__(32) k_step_decide(KArgs a, int mode, int nblocks, int use_cond,
-                                                     unsigned long long cond_handle) {
-  step_decide_body(a, mode, nblocks, use_cond, cond_handle);
+  __shared__ bool last;
+  __threadfence();  // this block's accumulator and displacement atomics before its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.scr_words + SCR_TICKET, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) a.scr_words[SCR_TICKET] = 0u;
+  if (threadIdx.x < 32) step_decide_body(a, mode, gridDim.x, use_cond, cond_handle);
 }
 
 int integrate_blocks(const KArgs& a) { return (a.n + kIntBlock - 1) / kIntBlock; }
 
 cudaError_t launch_integrate(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle, cudaStream_t st) {
-  const int nb = integrate_blocks(a);
-  k_integrate<<<nb, kIntBlock, 0, st>>>(a, mode);
-  k_step_decide<<<1, 32, 0, st>>>(a, mode, nb, use_cond, cond_handle);
+  k_integrate<<<integrate_blocks(a), kIntBlock, 0, st>>>(a, mode, use_cond, cond_handle);
   return cudaGetLastError();
 }
 

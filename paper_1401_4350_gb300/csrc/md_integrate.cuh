@@ -143,7 +143,7 @@ __device__ __forceinline__ bool thermostat_draw(const KArgs& a, uint32_t s, uint
 }
 
 // Whether this launch reduces energies: always for LAST and ENERGY, for MIDDLE when the step it
-// completes is a multiple of energy_every.  The step counter is read before k_step_decide advances it.
+// completes is a multiple of energy_every.  The step counter is read before the step decision advances it.
 __device__ __forceinline__ bool energy_step(const KArgs& a, int mode) {
   if (mode == 2 || mode == 3) return true;
   if (mode != 1) return false;
@@ -271,7 +271,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
       if (!(disp2 == disp2)) disp2 = 3.0e38f;  // NaN: force a rebuild (and the error is recorded)
     }
   }
-  // ---- per-block reductions; the totals are formed by k_step_decide ----
+  // ---- per-block reductions; the totals are formed by the step decision ----
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (drift) {
     const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
@@ -303,8 +303,8 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
   }
 }
 
-// After k_integrate: totals of the block partials in a fixed order (FP64), the trace row, the step
-// counter, and the rebuild decision (largest displacement since the build against (skin/2)^2), which
+// Run by the last block of an integrate launch (or the batch's per-replica decide): the FP64 energy
+// totals from the fixed-point accumulators, the trace row, the step counter, and the rebuild decision (largest displacement since the build against (skin/2)^2), which
 // sets the gate word for the gated rebuild kernels and, inside a graph, the IF node's condition.
 __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int nblocks, int use_cond,
                                                  unsigned long long cond_handle) {
@@ -315,10 +315,8 @@ __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int n
     if (threadIdx.x == 0) {
       unsigned long long* acc = energy_accumulators(a);
       double v[4];
-      for (int c = 0; c < 4; c++) {
-        v[c] = (double)(long long)acc[c] * (1.0 / 4294967296.0);
-        acc[c] = 0ULL;
-      }
+      for (int c = 0; c < 4; c++)  // read and clear at L2: the blocks' atomics landed there
+        v[c] = (double)(long long)atomicExch(acc + c, 0ULL) * (1.0 / 4294967296.0);
       const double K = v[0], KR = v[1], U = v[2], W = v[3];
       a.energy[MD_ENERGY_U] = U;
       a.energy[MD_ENERGY_KT] = K;
@@ -335,8 +333,7 @@ __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int n
   if (threadIdx.x == 0) {
     if (mode == 1 || mode == 2) a.status[MD_STATUS_STEPS] += 1;
     if (drift) {
-      const unsigned m = a.scr_words[SCR_DISPMAX];
-      a.scr_words[SCR_DISPMAX] = 0u;
+      const unsigned m = atomicExch(a.scr_words + SCR_DISPMAX, 0u);
       const unsigned g = __uint_as_float(m) > a.disp_thr2 ? 1u : 0u;
       a.scr_words[SCR_GATE] = g;
       a.status[MD_STATUS_REBUILDS] += (int)g;

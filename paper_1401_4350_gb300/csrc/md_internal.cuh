@@ -60,6 +60,9 @@ struct KArgs {
   double rc2_d, rv2_d;
   float rc2_f;
   float rv2_lo, rv2_hi;  // FP32 filter band of the Verlet build
+  // cubic boxes: the same decision on the exact integer r^2 of the fixed-point separation, with the
+  // band around rv^2 only as wide as the fixed-point rounding of the positions can move r^2
+  unsigned long long rv2_lo_u, rv2_hi_u;
   float disp_thr2;       // (skin/2)^2, slightly reduced: conservative rebuild trigger
   // Lennard-Jones constants (FP64 and FP32 copies)
   double sig2_d, lj_c4_d, lj_shift_d, lj_c24_d;  // 4 eps, V(rc_iso), 24 eps

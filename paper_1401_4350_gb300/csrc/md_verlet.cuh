@@ -8,9 +8,18 @@ namespace mdgb {
 
 // Builds the full-list row of slot i (i < a.n) and returns its length; the caller reduces the
 // lengths of its warp into MD_STATUS_NEED_NEIGH.
-// Whether j is a Verlet neighbour of i: FP32 filter on the fixed-point separation, and the exact FP64
-// decision of the definition inside a relative band of 1e-5 around rv^2.
+// Whether j is a Verlet neighbour of i: a filter on the fixed-point separation (exact integer r^2 in a
+// cubic box, FP32 otherwise), and the exact FP64 decision of the definition inside the band around rv^2
+// where the filter could disagree with it.
 __device__ __forceinline__ bool verlet_candidate_in(const KArgs& a, const uint4& si, const uint4& sj, int i, int j) {
+  if (a.cubic) {  // exact integer r^2; only the narrow rounding band asks the FP64 definition
+    const int ix = (int)(sj.x - si.x), iy = (int)(sj.y - si.y), iz = (int)(sj.z - si.z);
+    const unsigned long long s = (unsigned long long)((long long)ix * ix) + (unsigned long long)((long long)iy * iy) +
+                                 (unsigned long long)((long long)iz * iz);
+    if (s < a.rv2_lo_u) return true;
+    if (s >= a.rv2_hi_u) return false;
+    return exact_r2(a.pos[i], a.pos[j], a) < a.rv2_d;
+  }
   const float ddx = (float)(int)(sj.x - si.x) * a.fxp_unit[0];
   const float ddy = (float)(int)(sj.y - si.y) * a.fxp_unit[1];
   const float ddz = (float)(int)(sj.z - si.z) * a.fxp_unit[2];

@@ -36,6 +36,7 @@ def main(argv=None):
     ap.add_argument("--tpp", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--order", default="rows", choices=["rows", "hilbert"])
+    ap.add_argument("--equilibrate", type=int, default=0, help="MD steps (graph) before the timed launches")
     a = ap.parse_args(argv)
     mdbuild.build()
     B.load()
@@ -45,6 +46,9 @@ def main(argv=None):
     path = B.MD_VERTEX if a.path == "vertex" else B.MD_EDGE
     sim = Simulation(s, prec, tpp=a.tpp, cell_order=B.MD_ORDER_HILBERT if a.order == "hilbert" else B.MD_ORDER_ROWS)
     sim.prepare(path)
+    if a.equilibrate > 0:  # time the liquid rather than the initial lattice
+        sim.step(a.equilibrate, path, use_graph=True)
+        torch.cuda.synchronize()
     if a.what == "forces":
         fn = sim.forces_vertex if path == B.MD_VERTEX else sim.forces_edge
     elif a.what == "build":
@@ -55,6 +59,8 @@ def main(argv=None):
         def fn():
             sim.step(1, path, use_graph=False)
     st = torch.cuda.current_stream()
+    fn()  # warm-up launch
+    torch.cuda.synchronize()
     times = []
     for _ in range(a.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
