@@ -162,19 +162,21 @@ struct LocalBuildSmem {
 
 __device__ __forceinline__ int cell_rank_of(const KArgs& a, int c) { return a.cell_rank ? a.cell_rank[c] : c; }
 
-// Visits the (up to) 27 neighbour cells of the cell holding fixed-point position si.
+// Visits the (up to) 27 neighbour cells of the cell holding fixed-point position si, in the order of
+// verlet_full_one (an axis with fewer than three cells is a single cell, visited once).
 template <class F>
 __device__ __forceinline__ void for_neighbour_cells(const KArgs& a, const uint4& si, F f) {
   const int ci[3] = {fixed_cell(si.x, a.ncell[0]), fixed_cell(si.y, a.ncell[1]), fixed_cell(si.z, a.ncell[2])};
-  for (int dz = -1; dz <= 1; dz++) {
+  const int rz = a.ncell[2] >= 3 ? 1 : 0, ry = a.ncell[1] >= 3 ? 1 : 0, rx = a.ncell[0] >= 3 ? 1 : 0;
+  for (int dz = -rz; dz <= rz; dz++) {
     int z = ci[2] + dz;
     z += (z < 0) ? a.ncell[2] : 0;
     z -= (z >= a.ncell[2]) ? a.ncell[2] : 0;
-    for (int dy = -1; dy <= 1; dy++) {
+    for (int dy = -ry; dy <= ry; dy++) {
       int y = ci[1] + dy;
       y += (y < 0) ? a.ncell[1] : 0;
       y -= (y >= a.ncell[1]) ? a.ncell[1] : 0;
-      for (int dx = -1; dx <= 1; dx++) {
+      for (int dx = -rx; dx <= rx; dx++) {
         int x = ci[0] + dx;
         x += (x < 0) ? a.ncell[0] : 0;
         x -= (x >= a.ncell[0]) ? a.ncell[0] : 0;
