@@ -382,7 +382,7 @@ int md_release_graphs(const void* ws);
 size_t md_batch_workspace_bytes(const md_params* reps, int32_t nrep);
 size_t md_batch_replica_offset(const md_params* reps, int32_t nrep, int32_t r); /* (size_t)-1 if invalid */
 /* Records the batch, uploads its tables and clears every replica's status words.  path[r] is
- * MD_VERTEX or MD_EDGE (NULL: all MD_VERTEX); threads per particle from reps[r]. */
+ * MD_VERTEX, MD_EDGE or, for replicas with force_copies >= 1, MD_VERTEX_NEWTON (NULL: all MD_VERTEX); threads per particle from reps[r]. */
 int md_batch_init(const md_params* reps, int32_t nrep, const md_state* s, void* ws, const int32_t* path,
                   void* stream);
 /* Cells, lists (half lists for edge replicas), forces and step-0 energies of every replica. */
@@ -401,9 +401,10 @@ int md_batch_release(const void* ws);
 /*
  * md_autotune -- chooses each replica's decomposition by measurement.  Replicas are grouped by
  * model, mean neighbours per particle (from the lists, octave buckets) and size (octave buckets);
- * for every group each candidate (vertex with 1, 2 or 4 threads per particle, edge) is timed in the
- * batched force kernel on that group alone, and the fastest is kept (and remembered for later calls
- * with the same group key).  Leaves the batch prepared with the chosen configuration and returns it
+ * for every group each candidate (vertex with 1, 2 or 4 threads per particle, edge, and, when the
+ * group's replicas have force_copies >= 1, vertex with Newton's third law on rebuilt lists) is timed
+ * in the batched force kernel on that group alone, and the fastest is kept (and remembered for later
+ * calls with the same group key).  Leaves the batch prepared with the chosen configuration and returns it
  * in path_out / tpp_out (either may be NULL).  Synchronises the stream.
  */
 int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream);

@@ -36,7 +36,7 @@ constexpr int kBEdgePairs = 512;    // pairs per edge force item
 constexpr int kBGrid = 4;           // persistent blocks per SM
 
 // per-replica force kinds
-enum { KIND_V1 = 0, KIND_V2 = 1, KIND_V4 = 2, KIND_V8 = 3, KIND_EDGE = 8, KIND_CUBIC = 16 };
+enum { KIND_V1 = 0, KIND_V2 = 1, KIND_V4 = 2, KIND_V8 = 3, KIND_EDGE = 8, KIND_CUBIC = 16, KIND_NEWTON = 32 };
 
 enum { CTL_DECIDE_TICKET = 0, CTL_FORCE_COUNTER = 1, CTL_FORCE_TICKET = 2, CTL_RB_COUNT = 3, CTL_RB_CHUNKS = 4,
        CTL_WORDS = 64 };
@@ -103,6 +103,9 @@ __global__ void k_b_init(BatchDev b) {
   for (int k = t; k < ka.trace_capacity * 4; k += blockDim.x) ka.trace[k] = 0.0;
   for (int k = t; k < ka.n; k += blockDim.x) ka.nbr_count[k] = 0;
   for (int k = t; k <= ka.n; k += blockDim.x) ka.half_start[k] = 0;
+  // Newton reaction copies (mixed, isotropic: force hi and lo blocks of m copies)
+  for (size_t k = t; k < (size_t)2 * ka.force_copies * ka.n; k += blockDim.x)
+    ((float4*)ka.copies)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (blockIdx.x == 0 && t < CTL_WORDS) b.ctl[t] = 0u;
 }
 
@@ -216,11 +219,11 @@ __global__ void __launch_bounds__(kBChunk) k_b_rb_chunks(BatchDev b) {
     if (PHASE == RB_GATHER) { if (in) cells_gather_one(ka, i); }
     if (PHASE == RB_COPYBACK) { if (in) cells_copyback_one(ka, i); }
     if (PHASE == RB_VERLET) {
-      const int cnt = in ? verlet_full_one(ka, i) : 0;
+      const int cnt = in ? verlet_full_one(ka, i, (b.kind[r] & KIND_NEWTON) != 0) : 0;
       verlet_note_length(ka, cnt);
     }
-    if (PHASE == RB_HALF) {
-      if (in && (b.all_half || (b.kind[r] & KIND_EDGE))) verlet_half_one(ka, i);
+    if (PHASE == RB_HALF) {  // from a full list only
+      if (in && !(b.kind[r] & KIND_NEWTON) && (b.all_half || (b.kind[r] & KIND_EDGE))) verlet_half_one(ka, i);
     }
   }
 }
@@ -239,14 +242,17 @@ __global__ void __launch_bounds__(1024) k_b_rb_replica(BatchDev b) {
     for (int c = threadIdx.x; c < ka.ncell_total; c += blockDim.x) ka.count_tmp[c] = 0;
     if (threadIdx.x == 0) {
       ka.status[MD_STATUS_NEED_NEIGH] = 0;
-      ka.status[MD_STATUS_LISTS] = MD_LIST_FULL | ((b.all_half || (b.kind[r] & KIND_EDGE)) ? MD_LIST_HALF : 0);
+      ka.status[MD_STATUS_LISTS] = (b.kind[r] & KIND_NEWTON)
+                                       ? MD_LIST_NEWTON
+                                       : MD_LIST_FULL | ((b.all_half || (b.kind[r] & KIND_EDGE)) ? MD_LIST_HALF : 0);
     }
   }
   if (PHASE == RBR_CELLSCAN) block_scan_array<int32_t>(ka.count_tmp, ka.cell_start, ka.ncell_total);
   if (PHASE == RBR_SORT)
     for (int c = threadIdx.x; c < ka.ncell_total; c += blockDim.x) cells_sort_one(ka, c);
   if (PHASE == RBR_HALFSCAN) {
-    if (b.all_half || (b.kind[r] & KIND_EDGE)) block_scan_array<int64_t>(ka.count_tmp, ka.half_start, ka.n);
+    if (!(b.kind[r] & KIND_NEWTON) && (b.all_half || (b.kind[r] & KIND_EDGE)))
+      block_scan_array<int64_t>(ka.count_tmp, ka.half_start, ka.n);
   }
 }
 
@@ -257,13 +263,15 @@ __global__ void __launch_bounds__(kBChunk) k_b_edge_acc(BatchDev b) {
   __shared__ KArgs ka;
   const int item = blockIdx.x;
   const int r = b.integ_rep[item];
-  if (!(b.kind[r] & KIND_EDGE)) return;
+  if (!(b.kind[r] & (KIND_EDGE | KIND_NEWTON))) return;
   const int chunk = item - b.integ_first[r];
   load_kargs(ka, b.table + r);
   __syncthreads();
   const int i = chunk * kBChunk + threadIdx.x;
   if (i >= ka.n) return;
-  if (ZERO) {
+  if (b.kind[r] & KIND_NEWTON) {  // the copies are cleared by their finalize
+    if (!ZERO) newton_finalize_one(ka, i);
+  } else if (ZERO) {
     const size_t n = (size_t)ka.n;
     ka.acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     ka.acc[n + i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -292,7 +300,9 @@ __global__ void __launch_bounds__(kBForce) k_b_forces(BatchDev b) {
     __syncthreads();
     const int kind = b.kind[r];
     const int gt = local * kBForce + threadIdx.x;
-    if (kind & KIND_EDGE) {
+    if (kind & KIND_NEWTON) {
+      vertex_newton_mixed_body<false, 1>(ka, gt);
+    } else if (kind & KIND_EDGE) {
       const int64_t E = min(ka.half_start[ka.n], ka.max_pairs);
       const int64_t first = (int64_t)local * kBEdgePairs;
       if (first < E)
@@ -395,6 +405,7 @@ static void ctl_layout(int nrep, int integ_items, int force_items_cap, CtlLayout
 
 static int force_items_of(const md_params& p, int path, int tpp) {
   if (path == MD_EDGE) return (int)((p.max_pairs + kBEdgePairs - 1) / kBEdgePairs);
+  if (path == MD_VERTEX_NEWTON) tpp = 1;
   return (int)(((int64_t)p.n * tpp + kBForce - 1) / kBForce);
 }
 
@@ -412,9 +423,9 @@ static int check_batch_params(const md_params* reps, int nrep) {
       set_error("batch: replica %d: the batched path supports mixed-precision LJ and WCA replicas", r);
       return MD_ERR_INVALID;
     }
-    if (reps[r].cell_order != MD_ORDER_ROWS || reps[r].force_copies != 0 || reps[r].edge_store != 0 ||
-        reps[r].thermostat_every != 0) {
-      set_error("batch: replica %d: cell_order, force_copies, edge_store and thermostat_every must be 0 in a batch", r);
+    if (reps[r].cell_order != MD_ORDER_ROWS || reps[r].edge_store != 0 || reps[r].thermostat_every != 0 ||
+        reps[r].list_format != MD_FORMAT_GLOBAL) {
+      set_error("batch: replica %d: cell_order, edge_store, thermostat_every and list_format must be 0 in a batch", r);
       return MD_ERR_INVALID;
     }
   }
@@ -440,6 +451,7 @@ static size_t batch_bytes(const md_params* reps, int nrep, std::vector<size_t>* 
 static int kind_of(const md_params& p, int path, int tpp) {
   const bool cubic = p.box[0] == p.box[1] && p.box[1] == p.box[2];
   if (path == MD_EDGE) return KIND_EDGE;
+  if (path == MD_VERTEX_NEWTON) return KIND_NEWTON;
   const int t = tpp == 1 ? KIND_V1 : tpp == 2 ? KIND_V2 : tpp == 4 ? KIND_V4 : KIND_V8;
   return t | (cubic ? KIND_CUBIC : 0);
 }
@@ -600,7 +612,11 @@ int md_batch_init(const md_params* reps, int32_t nrep, const md_state* s, void* 
   for (int r = 0; r < nrep; r++) {
     h->off[r + 1] = h->off[r] + reps[r].n;
     const int pr = path ? path[r] : MD_VERTEX;
-    if (pr != MD_VERTEX && pr != MD_EDGE) { delete h; set_error("batch: path[%d] must be MD_VERTEX or MD_EDGE", r); return MD_ERR_INVALID; }
+    if (pr != MD_VERTEX && pr != MD_EDGE && !(pr == MD_VERTEX_NEWTON && reps[r].force_copies >= 1)) {
+      delete h;
+      set_error("batch: path[%d] must be MD_VERTEX, MD_EDGE or (with force_copies >= 1) MD_VERTEX_NEWTON", r);
+      return MD_ERR_INVALID;
+    }
     h->path[r] = pr;
     h->tpp[r] = reps[r].threads_per_particle;
   }
@@ -717,7 +733,11 @@ int md_batch_set_config(void* ws, const int32_t* path, const int32_t* tpp, void*
   BatchHost* h = need_batch(ws);
   if (!h) return MD_ERR_INVALID;
   for (int r = 0; r < h->nrep; r++) {
-    if (path && path[r] != MD_VERTEX && path[r] != MD_EDGE) { set_error("path[%d] invalid", r); return MD_ERR_INVALID; }
+    if (path && path[r] != MD_VERTEX && path[r] != MD_EDGE &&
+        !(path[r] == MD_VERTEX_NEWTON && h->reps[r].force_copies >= 1)) {
+      set_error("path[%d] invalid", r);
+      return MD_ERR_INVALID;
+    }
     if (tpp && tpp[r] != 1 && tpp[r] != 2 && tpp[r] != 4 && tpp[r] != 8) { set_error("tpp[%d] invalid", r); return MD_ERR_INVALID; }
   }
   for (int r = 0; r < h->nrep; r++) {
@@ -738,7 +758,7 @@ int md_batch_get_config(const void* ws, int32_t* path, int32_t* tpp) {
 }
 
 // Decompositions remembered across calls: (model, neighbour octave, size octave) -> (path, tpp).
-static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 static std::mutex g_tune_mu;
 
 int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream) {
@@ -746,10 +766,14 @@ int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream) {
   if (!h) return MD_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   const int R = h->nrep;
-  // both lists for every replica, so that any candidate can run without a rebuild
+  // full and half lists for every replica, so that the vertex and edge candidates run without a
+  // rebuild (replicas configured for the Newton path start from full lists too)
   h->dev.all_half = 1;
-  drop_graphs(h);
-  int rc = md_batch_prepare(ws, stream);
+  for (int r = 0; r < R; r++)
+    if (h->path[r] == MD_VERTEX_NEWTON) { h->path[r] = MD_VERTEX; h->tpp[r] = 1; }
+  int rc = upload_config(h, st);
+  if (rc != MD_OK) return rc;
+  rc = md_batch_prepare(ws, stream);
   if (rc != MD_OK) return rc;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "md_autotune");
@@ -762,14 +786,17 @@ int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream) {
     const double pairs = (double)words[MD_STATUS_NEED_PAIRS_LO] + (double)words[MD_STATUS_NEED_PAIRS_HI] * 2147483648.0;
     nbar[r] = 2.0 * pairs / (double)h->reps[r].n;
   }
-  std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+  // groups: model, octave of neighbours per particle, octave of N, and whether the Newton path is open
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
   for (int r = 0; r < R; r++) {
     const int nb = (int)floor(log2(std::max(nbar[r], 0.5)) + 8.0);
     const int ns = (int)floor(log2((double)h->reps[r].n));
-    groups[std::make_tuple(h->reps[r].model, nb, ns)].push_back(r);
+    groups[std::make_tuple(h->reps[r].model, nb, ns, h->reps[r].force_copies >= 1 ? 1 : 0)].push_back(r);
   }
-  const int cand_path[4] = {MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_EDGE};
-  const int cand_tpp[4] = {1, 2, 4, 1};
+  // vertex with 1/2/4 threads per particle and edge run on the lists built above; the Newton path
+  // (replicas with force copies) needs its own rows, so its probe rebuilds the lists first
+  const int cand_path[5] = {MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_EDGE, MD_VERTEX_NEWTON};
+  const int cand_tpp[5] = {1, 2, 4, 1, 1};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -785,10 +812,18 @@ int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream) {
       std::vector<int> only(R, 0);
       for (int r : kv.second) only[r] = 1;
       float best_ms = 1e30f;
-      for (int c = 0; c < 4; c++) {
+      bool lists_changed = false;
+      for (int c = 0; c < 5; c++) {
+        if (cand_path[c] == MD_VERTEX_NEWTON && std::get<3>(kv.first) == 0) continue;  // no force copies
         for (int r : kv.second) { h->path[r] = cand_path[c]; h->tpp[r] = cand_tpp[c]; }
         rc = upload_config(h, st, &only);
         if (rc != MD_OK) break;
+        if (cand_path[c] == MD_VERTEX_NEWTON) {  // Newton rows for the group (every replica is rebuilt)
+          rc = md_batch_prepare(ws, stream);
+          if (rc == MD_OK) rc = upload_config(h, st, &only);
+          if (rc != MD_OK) break;
+          lists_changed = true;
+        }
         std::vector<float> ms;
         for (int rep = 0; rep < 4; rep++) {
           cudaEventRecord(e0, st);
@@ -808,6 +843,12 @@ int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream) {
         }
       }
       if (rc != MD_OK) break;
+      if (lists_changed) {  // back to full and half lists for the groups still to probe
+        for (int r : kv.second) { h->path[r] = best.first; h->tpp[r] = best.second; }
+        rc = upload_config(h, st, &only);
+        if (rc == MD_OK) rc = md_batch_prepare(ws, stream);
+        if (rc != MD_OK) break;
+      }
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune_cache[kv.first] = best;
     }

@@ -32,7 +32,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="lj524288", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--path", default="vertex", choices=["vertex", "edge"])
-    ap.add_argument("--what", default="forces", choices=["forces", "build", "step"])
+    ap.add_argument("--what", default="forces", choices=["forces", "build", "step", "steps3"])
     ap.add_argument("--tpp", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--order", default="rows", choices=["rows", "hilbert"])
@@ -55,9 +55,12 @@ def main(argv=None):
         def fn():
             sim.build_cells()
             sim.build_verlet(B.MD_LIST_BOTH if path == B.MD_EDGE else B.MD_LIST_FULL)
-    else:
+    elif a.what == "step":
         def fn():
             sim.step(1, path, use_graph=False)
+    else:  # three steps: the integrate launches are FIRST, MIDDLE, MIDDLE, LAST
+        def fn():
+            sim.step(3, path, use_graph=False)
     st = torch.cuda.current_stream()
     fn()  # warm-up launch
     torch.cuda.synchronize()

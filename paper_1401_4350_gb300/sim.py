@@ -251,11 +251,12 @@ class BatchSimulation:
     """
 
     def __init__(self, system_list, paths=None, tpps=None, trace_capacity: int = 0, energy_every: int = 1,
-                 device: str = "cuda", stream=None):
+                 device: str = "cuda", stream=None, force_copies: int = 0):
         self.systems = list(system_list)
         tpps = tpps or [1] * len(self.systems)
         self.params = [make_params(s, B.MD_MIXED, tpp=int(t), trace_capacity=trace_capacity,
-                                   energy_every=energy_every) for s, t in zip(self.systems, tpps)]
+                                   energy_every=energy_every, force_copies=force_copies)
+                       for s, t in zip(self.systems, tpps)]
         self.nrep = len(self.systems)
         self.counts = [s.n for s in self.systems]
         self.offsets = np.concatenate([[0], np.cumsum(self.counts)]).astype(np.int64)

@@ -135,3 +135,60 @@ def test_batch_rejects_what_it_does_not_batch():
     assert "mixed-precision LJ and WCA" in B.last_error()
     q = make_params(systems.make_lj(500, 0.9, seed=4), B.MD_FP64)
     assert B.md_batch_workspace_bytes([q]) == 0
+
+
+NW = B.MD_VERTEX_NEWTON
+
+
+def _newton_replicas():
+    specs = [(systems.LJ, 900, 0.8, NW, 1), (systems.LJ, 1600, 0.5, V, 2), (systems.WCA, 1200, 0.2, NW, 1),
+             (systems.LJ, 2500, 0.85, E, 1), (systems.LJ, 3100, 0.7, NW, 1)]
+    return [(systems.make_replica(kind, n, rho, seed=7200 + k), path, tpp)
+            for k, (kind, n, rho, path, tpp) in enumerate(specs)]
+
+
+def test_batch_newton_replicas_match_single_system_and_oracle():
+    """Replicas on the Newton-vertex path (force copies in their sub-workspaces) next to vertex and edge
+    replicas: forces equal the single-system Newton path up to the order of the atomic additions, and
+    the oracle; 60 steps stay on the single-system trajectory."""
+    from paper_1401_4350_gb300.sim import Simulation
+    reps = _newton_replicas()
+    bs = _batch(reps, force_copies=2)
+    bs.prepare()
+    singles = []
+    for r, (s, path, tpp) in enumerate(reps):
+        assert bs.replica_status(r)[B.MD_STATUS_CODE] == 0
+        F, Ei, Wi = bs.replica_forces(r)
+        sim = Simulation(s, B.MD_MIXED, tpp=tpp, force_copies=2)
+        sim.prepare(path)
+        Fs, _, _, _ = sim.forces()
+        np.testing.assert_allclose(F, Fs, atol=1e-6 * max(1.0, np.abs(Fs).max()))
+        Fr, _, _, _ = oracle.forces(s.pos, oracle.Model(s.kind, tuple(s.box), s.rc), use_cells=s.n > 1500)
+        _check(F, Fr, f"replica {r}")
+        singles.append(sim)
+    bs.step(60)
+    for r, (s, path, tpp) in enumerate(reps):
+        assert bs.replica_status(r)[B.MD_STATUS_CODE] == 0
+        singles[r].step(60, path, True)
+        pos, _ = bs.replica_positions(r)
+        pos_s, _ = singles[r].positions()
+        d = pos - pos_s
+        d -= s.box * np.rint(d / s.box)
+        assert np.abs(d).max() < 1e-6, f"replica {r}"
+    bs.release()
+
+
+def test_autotune_includes_the_newton_path_when_copies_exist():
+    reps = _newton_replicas()
+    bs = _batch(reps, force_copies=1)
+    paths, tpps = bs.autotune()
+    assert all(p in (V, E, NW) for p in paths)
+    assert all(t == 1 for p, t in zip(paths, tpps) if p != V)
+    for r, (s, _, _) in enumerate(reps):
+        assert bs.replica_status(r)[B.MD_STATUS_CODE] == 0
+        F, _, _ = bs.replica_forces(r)
+        Fr, _, _, _ = oracle.forces(s.pos, oracle.Model(s.kind, tuple(s.box), s.rc), use_cells=s.n > 1500)
+        _check(F, Fr, f"replica {r} (path {paths[r]}, tpp {tpps[r]})")
+    bs.step(20)
+    assert all(bs.replica_status(r)[B.MD_STATUS_CODE] == 0 for r in range(len(reps)))
+    bs.release()
