@@ -15,8 +15,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Warp total of the unevaluated sums s + c of all lanes, with the rounding of every addition kept
-// (TwoSum): FP32 operations only, since FP64 ones are scarce on this GPU.
-__device__ __forceinline__ double warp_sum_ff(float s, float c) {
+// (TwoSum), left in every lane's (s, c): FP32 operations only, since FP64 ones are scarce on this GPU
+// (about 1.7 per clock per SM) and this runs for every particle.
+__device__ __forceinline__ void warp_sum_ff(float& s, float& c) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     const float o = __shfl_xor_sync(0xffffffffu, s, d), oc = __shfl_xor_sync(0xffffffffu, c, d);
@@ -26,7 +27,6 @@ __device__ __forceinline__ double warp_sum_ff(float s, float c) {
     c = __fadd_rn(__fadd_rn(c, oc), err);
     s = t;
   }
-  return (double)s + (double)c;
 }
 
 // Quaternion product a (x) b, (w, x, y, z) stored as double4_32a (x=w, y=x, z=y, w=z).
@@ -279,23 +279,24 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
   }
   if (energies) {
     __shared__ double sred[kIntBlock / 32][4];
-    double s0, s1, s2, s3;
+    __shared__ float sredf[kIntBlock / 32][4][2];
     if (mixed) {
-      // compensated FP32 sums within the warp; U_i and W_i arrive as FP64 values and enter as
-      // (hi, lo) FP32 pairs (exact for the isotropic vertex path, where they are FP32 values)
-      const float uh = (float)u, wh = (float)w;
-      s0 = warp_sum_ff(ktf, 0.f);
-      s1 = patchy ? warp_sum_ff(krf, 0.f) : 0.0;
-      s2 = warp_sum_ff(uh, (float)(u - (double)uh));
-      s3 = warp_sum_ff(wh, (float)(w - (double)wh));
+      // compensated FP32 sums within the warp, (sum, error) per warp into shared memory; U_i and W_i
+      // of the mixed paths are FP32 values stored in FP64 words, so they enter as FP32
+      float s[4] = {ktf, patchy ? krf : 0.f, (float)u, (float)w}, c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 4; k++) warp_sum_ff(s[k], c[k]);
+      if (lane == 0)
+        for (int k = 0; k < 4; k++) { sredf[wid][k][0] = s[k]; sredf[wid][k][1] = c[k]; }
     } else {
-      s0 = warp_sum(kt); s1 = warp_sum(kr); s2 = warp_sum(u); s3 = warp_sum(w);
+      const double s0 = warp_sum(kt), s1 = warp_sum(kr), s2 = warp_sum(u), s3 = warp_sum(w);
+      if (lane == 0) { sred[wid][0] = s0; sred[wid][1] = s1; sred[wid][2] = s2; sred[wid][3] = s3; }
     }
-    if (lane == 0) { sred[wid][0] = s0; sred[wid][1] = s1; sred[wid][2] = s2; sred[wid][3] = s3; }
     __syncthreads();
     if (threadIdx.x < 4) {
       double t = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sred[k][threadIdx.x];
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++)
+        t += mixed ? (double)sredf[k][threadIdx.x][0] + (double)sredf[k][threadIdx.x][1] : sred[k][threadIdx.x];
       // block sum -> 64-bit fixed point (2^-32 units): integer atomics make the total exact and
       // independent of the order in which blocks finish
       atomicAdd(energy_accumulators(a) + threadIdx.x, (unsigned long long)llrint(t * 4294967296.0));
