@@ -288,9 +288,9 @@ def run_ours(args, rank, world, dist):
         "variants": results,
         "roofline": roofline,
         "e2e": e2e,
-        # per step: integrate + decide + forces; a rebuild adds 9 cell and 2 Verlet kernels; the last
-        # half kick of a call adds integrate + decide
-        "gpu_launches": 3 * args.steps + 2 + 11 * rebuilds,
+        # per step: integrate (its last block decides) + forces; a rebuild adds 9 cell and 2 Verlet
+        # kernels; the last half kick of a call adds one integrate
+        "gpu_launches": 2 * args.steps + 1 + 11 * rebuilds,
         "clocks": clocks,
         "graph": not args.direct,
     }
