@@ -14,7 +14,7 @@
  * energy.  Everything is IEEE FP64, compiled with -ffp-contract=off so that the
  * expression order written here is the order evaluated.
  *
- * Readings of the paper this file follows (each is listed in the design doc):
+ * Readings of the paper this file follows:
  *  - minimum image per axis: d -= L * nearbyint(d / L)  (round half to even);
  *  - squared distance summed x, then y, then z, no fused multiply-add;
  *  - cut-offs are strict: a pair interacts iff r^2 < rc^2, and is a Verlet

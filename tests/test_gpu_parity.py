@@ -1,6 +1,6 @@
 """GPU parity of libmdgb against the FP64 oracle (called through the C ABI).
 
-Tolerances (written here, derived in the design doc):
+Tolerances (written here):
   * pair sets: bit-exact as sorted sets of original-id pairs;
   * MD_FP64 forces, torques and per-particle energies: |x - x_ref| <= 1e-12 max(|x_ref|, x_rms) per
     component (summation order differs: edge atomics, vertex list order);
@@ -96,10 +96,12 @@ def check_mixed(x, ref, what, over_nonzero=False):
 
 
 def run_forces(s, precision, path, tpp=1, block=0):
-    sim = Sim(s, precision, tpp=tpp, block=block)
+    sim = Sim(s, precision, tpp=tpp, block=block, force_copies=2 if path == B.MD_VERTEX_NEWTON else 0,
+              edge_store=1 if path == B.MD_EDGE_STORE else 0)
     sim.build_cells()
-    sim.build_verlet(B.MD_LIST_BOTH)
-    (sim.forces_vertex if path == B.MD_VERTEX else sim.forces_edge)()
+    sim.build_verlet(B.MD_LIST_NEWTON if path == B.MD_VERTEX_NEWTON else B.MD_LIST_BOTH)
+    {B.MD_VERTEX: sim.forces_vertex, B.MD_EDGE: sim.forces_edge, B.MD_VERTEX_NEWTON: sim.forces_vertex_newton,
+     B.MD_EDGE_STORE: sim.forces_edge_store}[path]()
     st = sim.status()
     assert st[B.MD_STATUS_CODE] == 0, st
     return sim, sim.forces()
@@ -231,7 +233,7 @@ def test_block_sizes(block, path):
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 33])
-@pytest.mark.parametrize("path", [B.MD_VERTEX, B.MD_EDGE])
+@pytest.mark.parametrize("path", [B.MD_VERTEX, B.MD_EDGE, B.MD_VERTEX_NEWTON, B.MD_EDGE_STORE])
 def test_tiny_systems(n, path):
     rng = np.random.default_rng(n)
     box = np.array([9.0, 9.5, 10.0])
@@ -264,7 +266,7 @@ def _min_image_err(a, b, box):
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("path", [B.MD_VERTEX, B.MD_EDGE])
 def test_fp64_trajectory_follows_oracle(path, use_graph):
-    """configs[0]-style LJ 4000: 100 FP64 steps stay on the oracle trajectory."""
+    """LJ N=4000 (the oracle-sized case): 100 FP64 steps stay on the oracle trajectory."""
     s = get_sys("lj4000")
     steps = 100
     p_ref, v_ref, _, _, tr = oracle.run_nve(s.pos, s.vel, model_of(s), s.dt, steps, use_cells=True)
