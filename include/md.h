@@ -176,7 +176,9 @@ typedef struct md_state {
 /* Byte offsets of the workspace sub-arrays (all 256-byte aligned). */
 typedef struct md_ws_layout {
   size_t total;          /* md_workspace_bytes()                                              */
-  int32_t ncell[3];      /* cells per axis (an axis with fewer than 3 cells of edge >= rv is 1) */
+  int32_t ncell[3];      /* cells per axis: edge >= rv/2 when there are at least 8 particles per
+                            rv^3 (and list_format = MD_FORMAT_GLOBAL), else edge >= rv; an axis with
+                            fewer than 5 (3) such cells is one cell                               */
   int32_t force_elem;    /* bytes per component of the force result (8: double)                */
   size_t status;         /* int32[MD_STATUS_WORDS]                                             */
   size_t energy;         /* double[MD_ENERGY_WORDS]                                            */
@@ -237,7 +239,8 @@ int md_init_workspace(const md_params* p, void* ws, void* stream);
  * md_build_cells -- cell binning with a counting sort (Sec. Methods: cell
  * filling one particle per thread; particles reordered for cache hits).
  * Wraps every position into [0, L), assigns each particle the cell of edge
- * L/ncell >= rv that holds it, and reorders pos, vel, quat, angmom and id into
+ * L/ncell >= rv/2 or rv (md_ws_layout.ncell) that holds it, and reorders pos, vel,
+ * quat, angmom and id into
  * cell order (within a cell: increasing previous slot), then writes
  * cell_start and the fixed-point coordinates fxp.  Deterministic.
  */
@@ -246,7 +249,8 @@ int md_build_cells(const md_params* p, md_state* s, void* ws, void* stream);
 /*
  * md_build_verlet -- Verlet lists L_i of every j with |x_j - x_i|^2 < rv^2,
  * rv = rc + skin (Sec. Methods), minimum image, from the cells of the last
- * md_build_cells.  which = MD_LIST_FULL (column-major list used by the vertex
+ * md_build_cells (the 5 x 5 x 5 cells around each particle's cell for cells of edge
+ * >= rv/2, 3 x 3 x 3 for cells of edge >= rv).  which = MD_LIST_FULL (column-major list used by the vertex
  * path), MD_LIST_HALF (pairs i < j used by the edge path), MD_LIST_BOTH, or
  * MD_LIST_NEWTON (the half rows of md_forces_vertex_newton, stored in place of
  * the full list).  MD_STATUS_LISTS records which lists are current.

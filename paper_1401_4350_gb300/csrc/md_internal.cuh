@@ -51,6 +51,7 @@ struct KArgs {
   int32_t trace_capacity;
   int32_t energy_every;
   int32_t ncell[3];
+  int32_t reach[3];  // neighbour cells searched on each side along each axis (0: a single cell)
   int32_t ncell_total;
   double box[3];
   double inv_box[3];

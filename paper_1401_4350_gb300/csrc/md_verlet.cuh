@@ -37,8 +37,8 @@ __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i, bool newto
     int lo[3], hi[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      lo[c] = a.ncell[c] >= 3 ? -1 : 0;
-      hi[c] = a.ncell[c] >= 3 ? 1 : 0;
+      lo[c] = -a.reach[c];
+      hi[c] = a.reach[c];
     }
     int half = 0;
     const size_t n = (size_t)a.n;
@@ -162,12 +162,12 @@ struct LocalBuildSmem {
 
 __device__ __forceinline__ int cell_rank_of(const KArgs& a, int c) { return a.cell_rank ? a.cell_rank[c] : c; }
 
-// Visits the (up to) 27 neighbour cells of the cell holding fixed-point position si, in the order of
-// verlet_full_one (an axis with fewer than three cells is a single cell, visited once).
+// Visits the neighbour cells of the cell holding fixed-point position si, in the order of
+// verlet_full_one (reach cells on each side along each axis; a single-cell axis is visited once).
 template <class F>
 __device__ __forceinline__ void for_neighbour_cells(const KArgs& a, const uint4& si, F f) {
   const int ci[3] = {fixed_cell(si.x, a.ncell[0]), fixed_cell(si.y, a.ncell[1]), fixed_cell(si.z, a.ncell[2])};
-  const int rz = a.ncell[2] >= 3 ? 1 : 0, ry = a.ncell[1] >= 3 ? 1 : 0, rx = a.ncell[0] >= 3 ? 1 : 0;
+  const int rz = a.reach[2], ry = a.reach[1], rx = a.reach[0];
   for (int dz = -rz; dz <= rz; dz++) {
     int z = ci[2] + dz;
     z += (z < 0) ? a.ncell[2] : 0;

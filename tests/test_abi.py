@@ -100,12 +100,23 @@ def test_workspace_layout(lib, precision, kind):
     n = s.n
     assert L.nbr_count - L.nbr >= 4 * n * p.max_neigh
     assert L.virial - L.force >= 32 * n
-    # cells of edge >= rv; an axis with fewer than three such cells is a single cell
+    # dense systems (>= 8 particles per rv^3): cells of edge >= rv/2, searched two cells deep, an axis with
+    # fewer than five of them is one cell; sparse ones: cells of edge >= rv, fewer than three -> one cell
+    dense = s.n / np.prod(s.box) * s.rv ** 3 >= 8.0
     for c in range(3):
         k = L.ncell[c]
-        assert k == 1 or (k >= 3 and s.box[c] / k >= s.rv)
+        if dense:
+            assert k == 1 or (k >= 5 and s.box[c] / k >= s.rv / 2)
+        else:
+            assert k == 1 or (k >= 3 and s.box[c] / k >= s.rv)
     if kind == "tiny":
-        assert tuple(L.ncell) == (1, 1, 1)
+        assert tuple(L.ncell) == (5, 5, 5)
+        p.box[0] = 6.5  # > 2 rv, but fewer than five cells of rv/2: one cell along x
+        assert B.md_workspace_layout(p).ncell[0] == 1
+        p.list_format = B.MD_FORMAT_LOCAL  # the block-local format keeps cells of edge >= rv
+        p.box[0] = s.box[0]
+        L2 = B.md_workspace_layout(p)
+        assert all(k == 1 or (k >= 3 and s.box[c] / k >= s.rv) for c, k in enumerate(L2.ncell))
 
 
 def test_struct_layouts_match_c(lib, tmp_path):
@@ -163,15 +174,15 @@ def test_newton_path_needs_copies(lib):
 
 def _grid_params(ncell):
     p = _lj_params(500)
-    p.n = 200000  # the grid is capped at 4 n + 27 cells; no memory is allocated here
+    p.n = 2000000  # the grid is capped at 4 n + 27 cells; no memory is allocated here
     rv = p.rc + p.skin
     for c in range(3):
-        p.box[c] = (ncell[c] + 0.5) * rv
+        p.box[c] = (ncell[c] + 0.5) * rv / 2  # cells of edge >= rv/2
     p.cell_order = B.MD_ORDER_HILBERT
     return p
 
 
-@pytest.mark.parametrize("k", [2, 3, 4, 5])
+@pytest.mark.parametrize("k", [3, 4, 5])
 def test_hilbert_cell_order_is_a_continuous_curve_on_power_of_two_grids(lib, k):
     """On a 2^k cube the Hilbert curve visits every cell once, starts in the corner cell, and steps to a
     face neighbour each time (the defining property of the curve)."""
@@ -188,7 +199,7 @@ def test_hilbert_cell_order_is_a_continuous_curve_on_power_of_two_grids(lib, k):
     assert (steps == 1).all()
 
 
-@pytest.mark.parametrize("ncell", [(3, 3, 3), (5, 7, 6), (38, 38, 38), (13, 3, 9)])
+@pytest.mark.parametrize("ncell", [(5, 5, 5), (5, 7, 6), (76, 76, 76), (13, 5, 9)])
 def test_hilbert_cell_order_is_a_local_permutation(lib, ncell):
     """Any grid: a permutation of the cells whose consecutive cells are close (the curve through the
     enclosing 2^b cube skips the missing cells); row-major order is the identity."""
