@@ -298,6 +298,8 @@ def run_ours(args, rank, world, dist):
         line["batch"] = run_batch()
     if not args.no_sweep and world == 1:
         line["density_sweep"] = run_density_sweep()
+    if not args.no_variants and world == 1:
+        line["accuracy"] = run_accuracy()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system)
     return line
@@ -326,6 +328,43 @@ def measured_traffic(kernel: str, n: int, entries: int):
     alg_now = 4.0 * entries + 52.0 * n
     alg_cap = 4.0 * rec["list_entries"] + 52.0 * rec["n"]
     return rec["dram_bytes_per_launch"] * alg_now / alg_cap
+
+
+def run_accuracy(n_drift: int = 65536, drift_steps: int = 2000):
+    """Force error of the mixed path against the FP64 path on the headline system's initial state, and
+    energy drift (least-squares slope of E_tot / N per 10^4 steps) of both precisions on LJ N = 65,536."""
+    import numpy as np
+    import torch
+    from paper_1401_4350_gb300 import binding as B
+    from paper_1401_4350_gb300 import systems
+    from paper_1401_4350_gb300.sim import Simulation
+    out = {}
+    s = make_system(0)
+    F = {}
+    for prec in (B.MD_MIXED, B.MD_FP64):
+        sim = Simulation(s, prec)
+        sim.prepare(B.MD_VERTEX)
+        F[prec] = sim.forces()[0]
+        del sim
+        torch.cuda.empty_cache()
+    frms = float(np.sqrt((F[B.MD_FP64] ** 2).sum(1).mean()))
+    out["max_force_error_mixed_vs_fp64_frms"] = float(np.abs(F[B.MD_MIXED] - F[B.MD_FP64]).max()) / frms
+    small = systems.make_lj(n_drift, 0.85, 1.0, seed=1001)
+    drift = {}
+    for name, prec in (("fp64", B.MD_FP64), ("mixed", B.MD_MIXED)):
+        sim = Simulation(small, prec, trace_capacity=drift_steps + 1)
+        sim.prepare(B.MD_VERTEX)
+        sim.step(drift_steps, B.MD_VERTEX, use_graph=True)
+        tr = sim.trace()
+        rows = tr[(tr[:, 0] > 0) & (tr[:, 0] <= drift_steps)]
+        rows = rows[np.argsort(rows[:, 0])]
+        e = (rows[:, 1] + rows[:, 2]) / n_drift
+        slope = float(np.polyfit(rows[:, 0], e, 1)[0]) * 1e4
+        drift[name] = {"per_1e4_steps": slope, "rms_fluctuation": float(np.std(e)), "steps": drift_steps}
+        del sim
+        torch.cuda.empty_cache()
+    out["energy_drift_lj65536"] = drift
+    return out
 
 
 def run_density_sweep(n: int = 131072, steps: int = 200):

@@ -196,13 +196,18 @@ def md_forces_edge_store(p, s, ws, stream=None):
     return _check(load().md_forces_edge_store(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _stream(stream)))
 
 
+MD_TUNE_CANDIDATES = 16
+TUNE_CANDIDATES = ([(MD_VERTEX, t, b) for t in (1, 2, 4, 8) for b in (64, 128, 256)] +
+                   [(MD_EDGE, 1, 128), (MD_EDGE, 1, 256), (MD_VERTEX_NEWTON, 1, 128), (MD_EDGE_STORE, 1, 256)])
+
+
 def md_autotune_system(p, s, ws, stream=None):
-    """(path, threads_per_particle, median ms of the seven candidates); p.threads_per_particle is updated."""
+    """(path, threads_per_particle, block_size, median ms per candidate of TUNE_CANDIDATES); p is updated."""
     path = ctypes.c_int32(0)
-    ms = (ctypes.c_float * 7)()
+    ms = (ctypes.c_float * MD_TUNE_CANDIDATES)()
     _check(load().md_autotune_system(ctypes.byref(p), ctypes.byref(s), _ptr(ws), ctypes.byref(path), ms,
                                      _stream(stream)))
-    return int(path.value), int(p.threads_per_particle), [float(x) for x in ms]
+    return int(path.value), int(p.threads_per_particle), int(p.block_size), [float(x) for x in ms]
 
 
 def md_forces_vertex_newton(p, s, ws, stream=None):

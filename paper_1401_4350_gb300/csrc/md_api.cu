@@ -588,6 +588,15 @@ static int get_graphs(const md_params* p, const md_state* s, const void* ws, int
 
 using namespace mdgb;
 
+// Candidates of md_autotune_system, in the order of its ms_out: vertex with 1/2/4/8 threads per particle
+// at block sizes 64/128/256, edge at 128/256, Newton-vertex at 128, per-edge store at 256.
+static const int md_tune_path[MD_TUNE_CANDIDATES] = {
+    MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX,
+    MD_VERTEX, MD_VERTEX, MD_EDGE, MD_EDGE, MD_VERTEX_NEWTON, MD_EDGE_STORE};
+static const int md_tune_tpp[MD_TUNE_CANDIDATES] = {1, 1, 1, 2, 2, 2, 4, 4, 4, 8, 8, 8, 1, 1, 1, 1};
+static const int md_tune_block[MD_TUNE_CANDIDATES] = {64, 128, 256, 64, 128, 256, 64, 128, 256, 64, 128, 256,
+                                                      128, 256, 128, 256};
+
 extern "C" {
 
 int md_abi_version(void) { return MD_ABI_VERSION; }
@@ -756,27 +765,28 @@ int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, f
   cudaEvent_t ev[2] = {nullptr, nullptr};
   if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-  // candidates: vertex with 1/2/4/8 threads per particle, edge, and the Newton and per-edge-store
-  // paths when the workspace has room for them
-  const int cand_path[7] = {MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_VERTEX, MD_EDGE, MD_VERTEX_NEWTON, MD_EDGE_STORE};
-  const int cand_tpp[7] = {1, 2, 4, 8, 1, 1, 1};
   float best = 3.0e38f;
   int best_k = 0;
-  for (int k = 0; k < 7 && e == cudaSuccess; k++) {
+  int built_for = -1;  // list kind currently built
+  for (int k = 0; k < MD_TUNE_CANDIDATES && e == cudaSuccess; k++) {
     float ms = -1.0f;
-    const bool usable = (cand_path[k] != MD_VERTEX_NEWTON || p->force_copies >= 1) &&
-                        (cand_path[k] != MD_EDGE_STORE || p->edge_store);
+    const int path = md_tune_path[k];
+    const bool usable = (path != MD_VERTEX_NEWTON || p->force_copies >= 1) && (path != MD_EDGE_STORE || p->edge_store);
     if (usable) {
       md_params q = *p;
-      q.threads_per_particle = cand_tpp[k];
+      q.threads_per_particle = md_tune_tpp[k];
+      q.block_size = md_tune_block[k];
       q.list_format = MD_FORMAT_GLOBAL;  // the workspace was laid out for p; timings use int32 lists
-      KArgs b = make_args(&q, s, ws, L);  // the layout does not depend on threads_per_particle
-      e = launch_build_verlet(b, list_kind(cand_path[k]), nullptr, st);
-      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_forces(b, cand_path[k], q.block_size, st);
+      KArgs b = make_args(&q, s, ws, L);  // the layout does not depend on tpp or the block size
+      if (built_for != list_kind(path)) {
+        e = launch_build_verlet(b, list_kind(path), nullptr, st);
+        built_for = list_kind(path);
+      }
+      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_forces(b, path, q.block_size, st);
       float reps[5];
       for (int r = 0; r < 5 && e == cudaSuccess; r++) {
         e = cudaEventRecord(ev[0], st);
-        if (e == cudaSuccess) e = launch_forces(b, cand_path[k], q.block_size, st);
+        if (e == cudaSuccess) e = launch_forces(b, path, q.block_size, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&reps[r], ev[0], ev[1]);
@@ -791,12 +801,13 @@ int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, f
   }
   if (e == cudaSuccess) {
     // leave the workspace prepared for the choice
-    p->threads_per_particle = cand_tpp[best_k];
+    p->threads_per_particle = md_tune_tpp[best_k];
+    p->block_size = md_tune_block[best_k];
     KArgs b = make_args(p, s, ws, L);
-    e = launch_build_verlet(b, list_kind(cand_path[best_k]), nullptr, st);
-    if (e == cudaSuccess) e = launch_forces(b, cand_path[best_k], p->block_size, st);
+    e = launch_build_verlet(b, list_kind(md_tune_path[best_k]), nullptr, st);
+    if (e == cudaSuccess) e = launch_forces(b, md_tune_path[best_k], p->block_size, st);
     if (e == cudaSuccess) e = launch_integrate(b, 3, 0, 0ULL, st);  // energies, as md_prepare
-    *path_out = cand_path[best_k];
+    *path_out = md_tune_path[best_k];
   }
   for (int k = 0; k < 2; k++)
     if (ev[k]) cudaEventDestroy(ev[k]);

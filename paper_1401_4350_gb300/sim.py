@@ -128,8 +128,9 @@ class Simulation:
         B.md_forces_edge_store(self.params, self.state(), self.ws, self._st())
 
     def autotune(self):
-        """Choose the fastest path (and threads per particle) by timing every available candidate;
-        returns (path, threads_per_particle, median ms per candidate).  Lists and forces stay prepared."""
+        """Choose the fastest path, threads per particle and block size by timing every available
+        candidate (binding.TUNE_CANDIDATES); returns (path, threads_per_particle, block_size, median ms per
+        candidate).  self.params is updated; lists and forces stay prepared for the choice."""
         return B.md_autotune_system(self.params, self.state(), self.ws, self._st())
 
     def prepare(self, path=B.MD_VERTEX):

@@ -136,11 +136,10 @@ def test_autotune_system_times_every_path_and_prepares_the_winner(name):
     s = get_sys(name)
     Fr, Tr, Er, _ = ref_forces(s, name)
     sim = Sim(s, B.MD_MIXED, force_copies=4, edge_store=1)
-    path, tpp, ms = sim.autotune()
+    path, tpp, block, ms = sim.autotune()
     assert all(t > 0 for t in ms), ms
-    cand = [(B.MD_VERTEX, 1), (B.MD_VERTEX, 2), (B.MD_VERTEX, 4), (B.MD_VERTEX, 8), (B.MD_EDGE, 1),
-            (B.MD_VERTEX_NEWTON, 1), (B.MD_EDGE_STORE, 1)]
-    assert (path, tpp) == cand[int(np.argmin(ms))]
+    assert (path, tpp, block) == B.TUNE_CANDIDATES[int(np.argmin(ms))]
+    assert (sim.params.threads_per_particle, sim.params.block_size) == (tpp, block)
     assert sim.status()[B.MD_STATUS_CODE] == 0
     F, E, T, W = sim.forces()
     check_mixed(F, Fr, "force after autotune")
@@ -148,5 +147,5 @@ def test_autotune_system_times_every_path_and_prepares_the_winner(name):
         check_mixed(T, Tr, "torque after autotune", over_nonzero=True)
     # without copies or store those two candidates are skipped
     sim2 = Sim(s, B.MD_MIXED)
-    _, _, ms2 = sim2.autotune()
-    assert ms2[5] == -1 and ms2[6] == -1 and all(t > 0 for t in ms2[:5])
+    _, _, _, ms2 = sim2.autotune()
+    assert ms2[14] == -1 and ms2[15] == -1 and all(t > 0 for t in ms2[:14])
