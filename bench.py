@@ -115,16 +115,25 @@ class ClockSampler:
 # our arm
 # ------------------------------------------------------------------------------------------------
 
+# Compulsory DRAM bytes per particle of one fused step launch (isotropic mixed vertex path): list count
+# 4, own fixed-point coordinates 16, velocity read + write 64, position read + write (other buffer) 64,
+# fixed-point coordinates at the last build 16, new fixed-point coordinates 16; plus 4 B per list entry.
+FUSED_BYTES_PER_PARTICLE = 180
+
+
 def algorithmic_bytes_force(path: int, precision: int, n: int, full_entries: int, pairs: int) -> float:
     """Compulsory DRAM bytes of one force launch (lists, per-particle arrays once, outputs once)."""
     from paper_1401_4350_gb300 import binding as B
-    if precision == B.MD_MIXED:
-        pos_b, out_b = 16, 32          # fixed-point coordinates; force + compensation (float4 x 2)
-    else:
-        pos_b, out_b = 32, 64          # double4 positions; force + virial words (double4 x 2)
     if path == B.MD_VERTEX:
-        return 4.0 * full_entries + n * (4 + pos_b + out_b)
+        # count 4 + own coordinates (fixed point 16, FP64 32) + force double4 32 + virial 8
+        return 4.0 * full_entries + n * (4 + (16 if precision == B.MD_MIXED else 32) + 40)
+    pos_b, out_b = (16, 32) if precision == B.MD_MIXED else (32, 64)
     return 8.0 * pairs + 8.0 * (n + 1) + n * (pos_b + 2 * out_b)  # outputs: zeroed once, accumulated once
+
+
+def algorithmic_bytes_fused(n: int, full_entries: int) -> float:
+    """Compulsory DRAM bytes of one fused force + integrate launch."""
+    return 4.0 * full_entries + FUSED_BYTES_PER_PARTICLE * n
 
 
 def run_ours(args, rank, world, dist):
@@ -197,19 +206,22 @@ def run_ours(args, rank, world, dist):
         uuid = None
 
     results = {}
-    # ---- headline: mixed precision, vertex path (the faster path on this workload) ----
+    # ---- headline: mixed precision, vertex path (the faster path on this workload), one fused
+    # force + integrate kernel per step ----
     headline_path = B.MD_VERTEX
-    sim = Simulation(system, B.MD_MIXED, trace_capacity=0, stream=stream)
+    sim = Simulation(system, B.MD_MIXED, trace_capacity=0, stream=stream, fuse_step=1)
     sim.prepare(headline_path)
     sim.step(max(args.warmup, 3), headline_path, use_graph=True)
     sampler = ClockSampler(uuid) if rank == 0 else None
     ms, rebuilds, clocks = time_steps(sim, headline_path, args.steps, sampler)
     ms = max_over_ranks(ms)
     full_entries, pairs = list_stats(sim)
+    kernel_ms = sim.time_step_kernel(headline_path, reps=min(args.steps, 200))
     force_ms = force_launch_ms(sim, headline_path, min(args.steps, 200))
     step_ms = ms / args.steps
     results["vertex_mixed"] = {"steps_per_s": 1e3 / step_ms, "ms_per_step": step_ms, "rebuilds": rebuilds,
-                               "pair_evals_per_s": pairs * 1e3 / step_ms, "force_kernel_ms": force_ms}
+                               "pair_evals_per_s": pairs * 1e3 / step_ms, "step_kernel_ms": kernel_ms,
+                               "force_kernel_ms": force_ms, "fuse_step": 1}
     # ---- end to end through the C ABI with host-resident state ----
     pos_h = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
     vel_h = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
@@ -240,6 +252,7 @@ def run_ours(args, rank, world, dist):
         NW, ES = B.MD_VERTEX_NEWTON, B.MD_EDGE_STORE
         HIL = {"cell_order": B.MD_ORDER_HILBERT}
         for name, path, precision, k, opts in (
+                ("vertex_mixed_separate_kernels", B.MD_VERTEX, B.MD_MIXED, min(args.steps, 1000), {"fuse_step": 0}),
                 ("vertex_mixed_hilbert", B.MD_VERTEX, B.MD_MIXED, min(args.steps, 1000), HIL),
                 ("edge_mixed", B.MD_EDGE, B.MD_MIXED, min(args.steps, 1000), {}),
                 ("edge_store_mixed", ES, B.MD_MIXED, min(args.steps, 300), {"edge_store": 1}),
@@ -266,13 +279,17 @@ def run_ours(args, rank, world, dist):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    alg = algorithmic_bytes_force(headline_path, B.MD_MIXED, n, full_entries, pairs)
-    achieved = alg / (force_ms * 1e-3) / 1e9
+    alg = algorithmic_bytes_fused(n, full_entries)
+    achieved = alg / (kernel_ms * 1e-3) / 1e9
+    force_alg = algorithmic_bytes_force(headline_path, B.MD_MIXED, n, full_entries, pairs)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": measured_traffic("k_vertex_iso_mixed<1,true>", n, full_entries),
-                "kernel": "k_vertex_iso_mixed<1,true>",
-                "algorithmic_bytes_per_launch": alg, "force_kernel_ms": force_ms,
-                "force_share_of_step": force_ms / step_ms,
+                "traffic": measured_traffic("k_vertex_step_mixed<1,true>", n, full_entries),
+                "kernel": "k_vertex_step_mixed<1,true>",
+                "algorithmic_bytes_per_launch": alg, "kernel_ms": kernel_ms,
+                "kernel_share_of_step": kernel_ms / step_ms,
+                "force_only": {"kernel": "k_vertex_iso_mixed<1,true>", "algorithmic_bytes_per_launch": force_alg,
+                               "ms": force_ms, "achieved": force_alg / (force_ms * 1e-3) / 1e9,
+                               "frac": force_alg / (force_ms * 1e-3) / 1e9 / hbm},
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
     value = job_throughput(world, args.steps, ms)
     line = {
@@ -288,9 +305,9 @@ def run_ours(args, rank, world, dist):
         "variants": results,
         "roofline": roofline,
         "e2e": e2e,
-        # per step: integrate (its last block decides) + forces; a rebuild adds 9 cell and 2 Verlet
-        # kernels; the last half kick of a call adds one integrate
-        "gpu_launches": 2 * args.steps + 1 + 11 * rebuilds,
+        # one call of K fused steps: the opening integrate, K - 1 fused step kernels (each one's last block
+        # decides), then the last forces and the closing integrate; a rebuild adds 9 cell and 2 Verlet kernels
+        "gpu_launches": args.steps + 2 + 11 * rebuilds,
         "clocks": clocks,
         "graph": not args.direct,
     }
@@ -306,10 +323,10 @@ def run_ours(args, rank, world, dist):
 
 
 def kernel_source_digest() -> str:
-    """sha256 of the force-kernel sources, to tell whether a stored ncu capture still describes them."""
+    """sha256 of the step-kernel sources, to tell whether a stored ncu capture still describes them."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("md_forces.cuh", "md_forces.cu", "md_internal.cuh"):
+    for f in ("md_forces.cuh", "md_forces.cu", "md_internal.cuh", "md_integrate.cuh", "md_step.cu"):
         with open(os.path.join(ROOT, "paper_1401_4350_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -325,8 +342,9 @@ def measured_traffic(kernel: str, n: int, entries: int):
     if rec.get("source_sha256") != kernel_source_digest():
         return None
     # traffic ~ 4 B per entry + per-particle bytes: scale the captured launch by its algorithmic bytes
-    alg_now = 4.0 * entries + 52.0 * n
-    alg_cap = 4.0 * rec["list_entries"] + 52.0 * rec["n"]
+    per = float(rec.get("bytes_per_particle", FUSED_BYTES_PER_PARTICLE))
+    alg_now = 4.0 * entries + per * n
+    alg_cap = 4.0 * rec["list_entries"] + per * rec["n"]
     return rec["dram_bytes_per_launch"] * alg_now / alg_cap
 
 

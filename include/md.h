@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 2
+#define MD_ABI_VERSION 3
 
 /* Return / status codes. */
 enum {
@@ -142,7 +142,11 @@ typedef struct md_params {
                                     MD_FORMAT_LOCAL (1): md_build_verlet(MD_LIST_FULL) writes 16-bit
                                     halo positions per block of MD_LOCAL_BLOCK slots when the system
                                     qualifies (see MD_LIST_FULL_LOCAL), else int32 slots            */
-  int32_t reserved;              /* must be 0                                                     */
+  int32_t fuse_step;             /* 1: md_step_verlet evaluates the forces and integrates in ONE kernel
+                                    per step where the step allows it (MD_VERTEX, mixed precision,
+                                    MD_LJ or MD_WCA, full list in MD_FORMAT_GLOBAL); the workspace
+                                    then holds a second copy of the positions and fixed-point
+                                    coordinates (pos_alt, fxp_alt).  0: separate kernels          */
   double box[3];                 /* periodic box edges; each must exceed 2 rv                    */
   double rc;                     /* centre-centre cut-off (LJ: 2.5 sigma; WCA: 2^(1/6) sigma)    */
   double skin;                   /* Verlet skin rs > 0; rv = rc + rs                             */
@@ -213,6 +217,9 @@ typedef struct md_ws_layout {
                             of a row is slot first + (v - offset) of the cell whose range holds v.
                             Empty unless the format can be chosen                                */
   size_t trace;          /* double[trace_capacity][4]: (step, K, U, W) rows of md_step_verlet */
+  size_t pos_alt;        /* fuse_step = 1: double[n][4] second position buffer (the fused kernel
+                            reads one buffer and writes the other); empty otherwise               */
+  size_t fxp_alt;        /* fuse_step = 1: uint32[n][4] second fixed-point buffer; empty otherwise */
   size_t scratch;        /* internal scratch                                                  */
 } md_ws_layout;
 
@@ -316,15 +323,36 @@ int md_forces_vertex_newton(const md_params* p, md_state* s, void* ws, void* str
  * exact rotation q <- exp(omega dt / 2) (x) q, omega = L / inertia.
  * Precondition: cells, lists and forces are current for the state (e.g. after
  * md_prepare).  The kinetic and potential energy and the virial of every
- * energy_every-th step (and of the last step of the call) are reduced in FP64
- * into the energy words and, when trace_capacity > 0, written to trace row
- * step % trace_capacity.  use_graph != 0 replays a CUDA graph per step whose rebuild is a
+ * energy_every-th step (and of the last step of the call) are reduced into the
+ * energy words (FP64 values of exact 64-bit fixed-point sums in 2^-32 units;
+ * mixed precision rounds each particle's FP32 terms to that grid once) and,
+ * when trace_capacity > 0, written to trace row step % trace_capacity.  use_graph != 0 replays a CUDA graph per step whose rebuild is a
  * conditional node (the graph is built on the first call for this
  * (p, s, ws, path) and cached); use_graph = 0 launches the kernels directly and
  * the rebuild kernels return early when no rebuild is due.
  */
 int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, int32_t path, int32_t use_graph,
                    void* stream);
+
+/*
+ * Fused steps (fuse_step = 1, path MD_VERTEX, mixed precision, MD_LJ or MD_WCA, global list format):
+ * md_step_verlet then runs the forces of step k and the integration that follows them (closing half
+ * kick of step k, opening half kick and drift of step k + 1, skin criterion, energies) in one kernel,
+ * which reads the positions of one buffer and writes the next positions to the other; the buffers
+ * swap every step, and the caller's pos (and the workspace fxp) hold the state again when the call
+ * returns.  The results are the same as with separate kernels: positions, velocities and the
+ * rebuild decisions bit for bit, and the energy totals too (exact sums of per-particle terms).
+ * The per-particle force, energy and virial words are written only by the last force evaluation of
+ * a call.
+ *
+ * md_time_step_kernel -- mean duration (ms, CUDA events on `stream`; synchronises) of `reps` launches
+ * of the kernel that md_step_verlet runs once per step for `path`: the fused kernel when fuse_step
+ * applies, else the force kernel.  Cells, lists and forces must be current (md_prepare).  The
+ * velocities, status, energy, trace and decision words are restored afterwards, so the system is left
+ * as it was.  Returns MD_OK, MD_ERR_INVALID or MD_ERR_CUDA.
+ */
+int md_time_step_kernel(const md_params* p, md_state* s, void* ws, int32_t path, int32_t reps, float* ms_out,
+                        void* stream);
 
 /*
  * md_autotune_system -- picks the fastest decomposition for this system on this GPU (generalising the

@@ -37,7 +37,7 @@ class md_params(ctypes.Structure):
                 ("threads_per_particle", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("trace_capacity", ctypes.c_int32), ("energy_every", ctypes.c_int32), ("force_copies", ctypes.c_int32),
                 ("cell_order", ctypes.c_int32), ("edge_store", ctypes.c_int32),
-                ("list_format", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("list_format", ctypes.c_int32), ("fuse_step", ctypes.c_int32),
                 ("box", ctypes.c_double * 3), ("rc", ctypes.c_double),
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double), ("mass", ctypes.c_double),
                 ("inertia", ctypes.c_double), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
@@ -57,7 +57,7 @@ class md_ws_layout(ctypes.Structure):
         (name, ctypes.c_size_t) for name in
         ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr", "nbr_count", "half_start",
          "pairs", "force", "virial", "torque", "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace",
-         "scratch")]
+         "pos_alt", "fxp_alt", "scratch")]
 
 
 class MDError(RuntimeError):
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
         "md_autotune_system": ([_P, _S, _V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _V],
                                ctypes.c_int),
         "md_step_verlet": ([_P, _S, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _V], ctypes.c_int),
+        "md_time_step_kernel": ([_P, _S, _V, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _V],
+                                ctypes.c_int),
         "md_prepare": ([_P, _S, _V, ctypes.c_int32, _V], ctypes.c_int),
         "md_get_forces": ([_P, _V, _V, _V, _V], ctypes.c_int),
         "md_read_status": ([_P, _V, ctypes.POINTER(ctypes.c_int32), _V], ctypes.c_int),
@@ -217,6 +219,14 @@ def md_forces_vertex_newton(p, s, ws, stream=None):
 def md_step_verlet(p, s, ws, nsteps, path=MD_VERTEX, use_graph=True, stream=None):
     return _check(load().md_step_verlet(ctypes.byref(p), ctypes.byref(s), _ptr(ws), int(nsteps), int(path),
                                         int(bool(use_graph)), _stream(stream)))
+
+
+def md_time_step_kernel(p, s, ws, path=MD_VERTEX, reps=20, stream=None) -> float:
+    """Mean ms of the kernel md_step_verlet runs once per step (fused step kernel or force kernel)."""
+    ms = ctypes.c_float(0.0)
+    _check(load().md_time_step_kernel(ctypes.byref(p), ctypes.byref(s), _ptr(ws), int(path), int(reps),
+                                      ctypes.byref(ms), _stream(stream)))
+    return float(ms.value)
 
 
 def md_prepare(p, s, ws, path=MD_VERTEX, stream=None):

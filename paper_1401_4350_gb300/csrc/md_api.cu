@@ -103,7 +103,7 @@ static int check(const md_params* p) {
     set_error("list_format must be MD_FORMAT_GLOBAL or MD_FORMAT_LOCAL");
     return MD_ERR_INVALID;
   }
-  if (p->reserved != 0) { set_error("reserved must be 0"); return MD_ERR_INVALID; }
+  if (p->fuse_step != 0 && p->fuse_step != 1) { set_error("fuse_step must be 0 or 1"); return MD_ERR_INVALID; }
   if (p->edge_store && p->max_pairs >= (int64_t)1 << 31) {
     set_error("edge_store needs max_pairs < 2^31 (32-bit positions in the by-partner index)");
     return MD_ERR_INVALID;
@@ -196,6 +196,8 @@ static void make_layout(const md_params* p, Layout* L) {
   P.jedge = take(p->edge_store ? sizeof(int32_t) * (size_t)p->max_pairs : 0);
   P.local_tab = take(local_list_eligible(p) ? sizeof(int32_t) * kLocalRec * ((n + MD_LOCAL_BLOCK - 1) / MD_LOCAL_BLOCK) : 0);
   P.trace = take(sizeof(double) * 4 * (size_t)p->trace_capacity);
+  P.pos_alt = take(p->fuse_step ? 32 * n : 0);
+  P.fxp_alt = take(p->fuse_step ? 16 * n : 0);
   P.scratch = off;
   L->scr_words = take(sizeof(uint32_t) * SCR_WORDS);
   const int nblk = (int)((n + 255) / 256);
@@ -358,6 +360,8 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.cell_start = (int32_t*)(w + L.pub.cell_start);
   a.fxp = (uint4*)(w + L.pub.fxp);
   a.fxp_build = (uint4*)(w + L.pub.fxp_build);
+  a.pos_alt = p->fuse_step ? (double4_32a*)(w + L.pub.pos_alt) : nullptr;
+  a.fxp_alt = p->fuse_step ? (uint4*)(w + L.pub.fxp_alt) : nullptr;
   a.patch_lab = (void*)(w + L.pub.patch_lab);
   a.nbr = (int32_t*)(w + L.pub.nbr);
   a.nbr_count = (int32_t*)(w + L.pub.nbr_count);
@@ -396,6 +400,7 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   make_layout(p, &L);
   KArgs a = make_args(p, s, nullptr, L);
   a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
+  a.pos_alt = nullptr; a.fxp_alt = nullptr;
   a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
   a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
   a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr; a.local_ok = 0; a.local_tab = nullptr;
@@ -441,15 +446,16 @@ struct GraphEntry {
   const void* ws;
   int path;
   int device;
-  cudaGraph_t g[2];
-  cudaGraphExec_t exec[2];  // 0: first step, 1: following steps
+  cudaGraph_t g[3];
+  cudaGraphExec_t exec[3];  // separate kernels: 0 first step, 1 following steps.  Fused steps: 0 first
+                            // step, 1 a step from the primary buffers, 2 a step from the alternate ones
 };
 
 static std::mutex g_graph_mu;
 static std::vector<GraphEntry> g_graphs;
 
 static void destroy_entry(GraphEntry& e) {
-  for (int k = 0; k < 2; k++) {
+  for (int k = 0; k < 3; k++) {
     if (e.exec[k]) cudaGraphExecDestroy(e.exec[k]);
     if (e.g[k]) cudaGraphDestroy(e.g[k]);
     e.exec[k] = nullptr;
@@ -488,7 +494,30 @@ static int check_path(const md_params* p, int path) {
   return MD_OK;
 }
 
-static int build_step_graph(const KArgs& a, int mode, int path, int block, cudaGraph_t* g_out, cudaGraphExec_t* exec_out) {
+// Whether md_step_verlet runs each step's forces and integration as one kernel: fuse_step = 1 and the
+// isotropic mixed-precision vertex path over the int32 full list.
+static bool fused_step(const md_params* p, int path) {
+  return p->fuse_step == 1 && path == MD_VERTEX && p->precision == MD_MIXED &&
+         (p->model == MD_LJ || p->model == MD_WCA) && !local_list_eligible(p);
+}
+
+// The kernel arguments with the primary and the alternate position / fixed-point buffers exchanged.
+static KArgs swapped(const KArgs& a) {
+  KArgs b = a;
+  b.pos = a.pos_alt;
+  b.pos_alt = a.pos;
+  b.fxp = a.fxp_alt;
+  b.fxp_alt = a.fxp;
+  return b;
+}
+
+enum { HEAD_FIRST = 0, HEAD_MIDDLE = 1, HEAD_FUSED = 2 };
+
+// One step as a graph: the head launch (integrate FIRST or MIDDLE with args ha, or the fused step
+// reading ha's buffers), whose last block sets the IF node's condition; the IF body rebuilds cells and
+// lists with args ba (the buffers that now hold the state); then, for separate kernels, the forces.
+static int build_step_graph(int head, const KArgs& ha, const KArgs& ba, bool forces_after, int path, int block,
+                            cudaGraph_t* g_out, cudaGraphExec_t* exec_out) {
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -505,7 +534,8 @@ static int build_step_graph(const KArgs& a, int mode, int path, int block, cudaG
       rc = cuda_fail(e, "cudaStreamBeginCaptureToGraph");
       break;
     }
-    cudaError_t le = launch_integrate(a, mode, 1, (unsigned long long)h, cs);
+    cudaError_t le = head == HEAD_FUSED ? launch_step_fused(ha, block, 1, (unsigned long long)h, cs)
+                                        : launch_integrate(ha, head, 1, (unsigned long long)h, cs);
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -518,7 +548,7 @@ static int build_step_graph(const KArgs& a, int mode, int path, int block, cudaG
     if (e == cudaSuccess && le == cudaSuccess) e = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp);
     if (e == cudaSuccess && le == cudaSuccess)
       e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-    if (e == cudaSuccess && le == cudaSuccess) le = launch_forces(a, path, block, cs);
+    if (e == cudaSuccess && le == cudaSuccess && forces_after) le = launch_forces(ha, path, block, cs);
     cudaGraph_t captured = nullptr;
     cudaError_t ee = cudaStreamEndCapture(cs, &captured);
     if (le != cudaSuccess) { rc = cuda_fail(le, "kernel launch during capture"); break; }
@@ -529,8 +559,8 @@ static int build_step_graph(const KArgs& a, int mode, int path, int block, cudaG
       rc = cuda_fail(e, "capture of the rebuild body");
       break;
     }
-    le = launch_build_cells(a, nullptr, cs);
-    if (le == cudaSuccess) le = launch_build_verlet(a, list_kind(path), nullptr, cs);
+    le = launch_build_cells(ba, nullptr, cs);
+    if (le == cudaSuccess) le = launch_build_verlet(ba, list_kind(path), nullptr, cs);
     ee = cudaStreamEndCapture(cs, &captured);
     if (le != cudaSuccess) { rc = cuda_fail(le, "rebuild launch during capture"); break; }
     if (ee != cudaSuccess) { rc = cuda_fail(ee, "cudaStreamEndCapture (rebuild body)"); break; }
@@ -544,15 +574,14 @@ static int build_step_graph(const KArgs& a, int mode, int path, int block, cudaG
 }
 
 static int get_graphs(const md_params* p, const md_state* s, const void* ws, int path, const KArgs& a,
-                      cudaGraphExec_t* first, cudaGraphExec_t* mid) {
+                      cudaGraphExec_t exec[3]) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_graph_mu);
   for (auto& e : g_graphs) {
     if (e.ws == ws && e.path == path && e.device == dev && memcmp(&e.params, p, sizeof(*p)) == 0 &&
         memcmp(&e.state, s, sizeof(*s)) == 0) {
-      *first = e.exec[0];
-      *mid = e.exec[1];
+      for (int k = 0; k < 3; k++) exec[k] = e.exec[k];
       return MD_OK;
     }
   }
@@ -571,16 +600,21 @@ static int get_graphs(const md_params* p, const md_state* s, const void* ws, int
   e.ws = ws;
   e.path = path;
   e.device = dev;
-  for (int m = 0; m < 2; m++) {
-    int rc = build_step_graph(a, m, path, p->block_size, &e.g[m], &e.exec[m]);
+  const bool fused = fused_step(p, path);
+  const KArgs b = fused ? swapped(a) : a;
+  for (int m = 0; m < (fused ? 3 : 2); m++) {
+    int rc;
+    if (!fused) rc = build_step_graph(m == 0 ? HEAD_FIRST : HEAD_MIDDLE, a, a, true, path, p->block_size, &e.g[m], &e.exec[m]);
+    else if (m == 0) rc = build_step_graph(HEAD_FIRST, a, a, false, path, p->block_size, &e.g[m], &e.exec[m]);
+    else if (m == 1) rc = build_step_graph(HEAD_FUSED, a, b, false, path, p->block_size, &e.g[m], &e.exec[m]);
+    else rc = build_step_graph(HEAD_FUSED, b, a, false, path, p->block_size, &e.g[m], &e.exec[m]);
     if (rc != MD_OK) {
       destroy_entry(e);
       return rc;
     }
   }
   g_graphs.push_back(e);
-  *first = e.exec[0];
-  *mid = e.exec[1];
+  for (int k = 0; k < 3; k++) exec[k] = e.exec[k];
   return MD_OK;
 }
 
@@ -727,6 +761,10 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
   KArgs a = make_args(p, s, ws, L);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
+  // fused steps alternate between the primary buffers (a) and the alternate ones (b)
+  const bool fused = fused_step(p, path);
+  const KArgs b = fused ? swapped(a) : a;
+  bool alt = false;  // the state is in the alternate buffers
   if (use_graph) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
@@ -734,22 +772,100 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
       set_error("use_graph = 1 while the stream is being captured: call with use_graph = 0 inside a capture");
       return MD_ERR_INVALID;
     }
-    cudaGraphExec_t first = nullptr, mid = nullptr;
-    rc = get_graphs(p, s, ws, path, a, &first, &mid);
+    cudaGraphExec_t ex[3] = {nullptr, nullptr, nullptr};
+    rc = get_graphs(p, s, ws, path, a, ex);
     if (rc != MD_OK) return rc;
-    e = cudaGraphLaunch(first, st);
-    for (int k = 1; k < nsteps && e == cudaSuccess; k++) e = cudaGraphLaunch(mid, st);
+    e = cudaGraphLaunch(ex[0], st);
+    for (int k = 1; k < nsteps && e == cudaSuccess; k++) {
+      e = cudaGraphLaunch(fused && alt ? ex[2] : ex[1], st);
+      if (fused) alt = !alt;
+    }
   } else {
     const uint32_t* gate = a.scr_words + SCR_GATE;
     for (int k = 0; k < nsteps && e == cudaSuccess; k++) {
-      e = launch_integrate(a, k == 0 ? 0 : 1, 0, 0ULL, st);
-      if (e == cudaSuccess) e = launch_build_cells(a, gate, st);
-      if (e == cudaSuccess) e = launch_build_verlet(a, list_kind(path), gate, st);
-      if (e == cudaSuccess) e = launch_forces(a, path, p->block_size, st);
+      const KArgs& c = alt ? b : a;
+      if (fused && k > 0) {  // forces of step k, its closing half kick, then half kick + drift into the other buffers
+        const KArgs& nx = alt ? a : b;
+        e = launch_step_fused(c, p->block_size, 0, 0ULL, st);
+        if (e == cudaSuccess) e = launch_build_cells(nx, gate, st);
+        if (e == cudaSuccess) e = launch_build_verlet(nx, list_kind(path), gate, st);
+        alt = !alt;
+        continue;
+      }
+      e = launch_integrate(c, k == 0 ? 0 : 1, 0, 0ULL, st);
+      if (e == cudaSuccess) e = launch_build_cells(c, gate, st);
+      if (e == cudaSuccess) e = launch_build_verlet(c, list_kind(path), gate, st);
+      if (e == cudaSuccess && !fused) e = launch_forces(c, path, p->block_size, st);
     }
   }
-  if (e == cudaSuccess) e = launch_integrate(a, 2, 0, 0ULL, st);
+  const KArgs& c = alt ? b : a;
+  if (e == cudaSuccess && fused) e = launch_forces(c, path, p->block_size, st);  // forces of the last step
+  if (e == cudaSuccess) e = launch_integrate(c, 2, 0, 0ULL, st);
+  if (e == cudaSuccess && alt) {  // the caller's positions and the primary coordinates hold the state again
+    e = cudaMemcpyAsync(a.pos, b.pos, 32 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a.fxp, b.fxp, 16 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
+  }
   return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_step_verlet");
+}
+
+int md_time_step_kernel(const md_params* p, md_state* s, void* ws, int32_t path, int32_t reps, float* ms_out,
+                        void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc == MD_OK) rc = check_path(p, path);
+  if (rc != MD_OK) return rc;
+  if (reps < 1 || !ms_out) { set_error("reps must be >= 1 and ms_out non-NULL"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  KArgs a = make_args(p, s, ws, L);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fused = fused_step(p, path);
+  char* w = (char*)ws;
+  // what a launch changes besides the force arrays: status, energy, trace and decision words and the
+  // energy accumulators (kept on the host), and, fused, the velocities (kept in the cell-sort scratch)
+  const size_t off[5] = {L.pub.status, L.pub.energy, L.pub.trace, L.scr_words, L.block_partials};
+  const size_t len[5] = {sizeof(int32_t) * MD_STATUS_WORDS, sizeof(double) * MD_ENERGY_WORDS,
+                         sizeof(double) * 4 * (size_t)p->trace_capacity, sizeof(uint32_t) * SCR_WORDS, 32};
+  size_t total = 0;
+  for (int k = 0; k < 5; k++) total += len[k];
+  std::vector<char> keep(total);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0, o = 0; k < 5 && e == cudaSuccess; o += (int)len[k], k++)
+    if (len[k]) e = cudaMemcpyAsync(keep.data() + o, w + off[k], len[k], cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && fused) e = cudaMemcpyAsync(a.tmp_d4, a.vel, 32 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "md_time_step_kernel (save)");
+  auto launch = [&]() {
+    return fused ? launch_step_fused(a, p->block_size, 0, 0ULL, st) : launch_forces(a, path, p->block_size, st);
+  };
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  if (e == cudaSuccess) e = launch();  // warm-up
+  for (int r = 0; r < reps && e == cudaSuccess; r++) {
+    e = cudaEventRecord(ev[2 * r], st);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  double sum = 0.0;
+  for (int r = 0; r < reps && e == cudaSuccess; r++) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+    sum += ms;
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  // restore, whatever happened above
+  cudaError_t er = cudaSuccess;
+  for (int k = 0, o = 0; k < 5 && er == cudaSuccess; o += (int)len[k], k++)
+    if (len[k]) er = cudaMemcpyAsync(w + off[k], keep.data() + o, len[k], cudaMemcpyHostToDevice, st);
+  if (er == cudaSuccess && fused) er = cudaMemcpyAsync(a.vel, a.tmp_d4, 32 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
+  if (er == cudaSuccess) er = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "md_time_step_kernel");
+  if (er != cudaSuccess) return cuda_fail(er, "md_time_step_kernel (restore)");
+  *ms_out = (float)(sum / reps);
+  return MD_OK;
 }
 
 int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, float* ms_out, void* stream) {

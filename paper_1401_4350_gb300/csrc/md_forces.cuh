@@ -647,8 +647,24 @@ __device__ __forceinline__ double scale_ff(float s, float lo, float sh, float sl
   return (double)p + (double)__fmaf_rn(s, sl, __fmaf_rn(lo, sh, err));
 }
 
+// One particle's result of the isotropic mixed vertex evaluation: the FP64 force and the FP64 values of
+// the FP32 halves E_i and W_i.  Filled by the thread that owns the particle (l == 0, i < n); the plain
+// kernels store it, the fused step kernel integrates with it.
+struct IsoResult {
+  double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0, w = 0.0;
+  bool set = false;  // false: not the owner, or the full list is not current (nothing to store)
+};
+
+__device__ __forceinline__ void store_iso(const KArgs& a, int gt, int tpp, const IsoResult& r) {
+  if (r.set) {
+    const int i = gt / tpp;
+    a.force[i] = make_double4_32a(r.fx, r.fy, r.fz, r.e);
+    a.virial[i] = r.w;
+  }
+}
+
 template <int TPP, class Rows>
-__device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R) {
+__device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R, IsoResult& res) {
   const int i = gt / TPP, l = gt % TPP;
   const bool valid = i < a.n;
   const size_t n = (size_t)a.n;
@@ -733,20 +749,22 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
   if (valid && l == 0) {
     const float e = 0.5f * (a.lj_c4_f * (s12 - s6) - a.lj_shift_f * (float)nin);
     const float w = 0.5f * a.lj_c24_f * (2.f * s12 - s6);
-    a.force[i] = make_double4_32a(scale_ff(S[0], lo[0], a.fscale_hi, a.fscale_lo),
-                                  scale_ff(S[1], lo[1], a.fscale_hi, a.fscale_lo),
-                                  scale_ff(S[2], lo[2], a.fscale_hi, a.fscale_lo), (double)e);
-    a.virial[i] = (double)w;
+    res.fx = scale_ff(S[0], lo[0], a.fscale_hi, a.fscale_lo);
+    res.fy = scale_ff(S[1], lo[1], a.fscale_hi, a.fscale_lo);
+    res.fz = scale_ff(S[2], lo[2], a.fscale_hi, a.fscale_lo);
+    res.e = (double)e;
+    res.w = (double)w;
+    res.set = true;
   }
 }
 
 template <int TPP>
-__device__ __forceinline__ void vertex_iso_cubic_body(const KArgs& a, int gt) {
+__device__ __forceinline__ void vertex_iso_cubic_eval(const KArgs& a, int gt, IsoResult& res) {
   if (!full_list_current(a)) return;
   GlobalRows R;
   R.nb4 = (const int4*)a.nbr + min(gt / TPP, a.n - 1);
   R.jmax = (unsigned)a.n - 1u;
-  vertex_iso_cubic_rows<TPP>(a, gt, R);
+  vertex_iso_cubic_rows<TPP>(a, gt, R, res);
 }
 
 // The block-local list: the block (MD_LOCAL_BLOCK threads, one per slot) first stages its halo's
@@ -773,13 +791,16 @@ __device__ __forceinline__ void vertex_iso_local_body(const KArgs& a, uint4* hal
     }
   }
   __syncthreads();
-  vertex_iso_cubic_rows<1>(a, i, R);
+  IsoResult res;
+  vertex_iso_cubic_rows<1>(a, i, R, res);
+  store_iso(a, i, 1, res);
 }
 
+// The isotropic mixed vertex evaluation over the int32 full list (cubic boxes: the integer-r^2 path)
 template <int TPP, bool CUBIC>
-__device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
+__device__ __forceinline__ void vertex_iso_mixed_eval(const KArgs& a, int gt, IsoResult& res) {
   if (CUBIC) {
-    vertex_iso_cubic_body<TPP>(a, gt);
+    vertex_iso_cubic_eval<TPP>(a, gt, res);
     return;
   }
   if (!full_list_current(a)) return;
@@ -867,10 +888,20 @@ __device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
   if (valid && l == 0) {
     // sum + compensation once per particle in FP64, then back from fixed-point units (exact scale 2^32/L)
     const double s = CUBIC ? a.fxp_scale[0] : 1.0;
-    a.force[i] = make_double4_32a(((double)fx + (double)lx) * s, ((double)fy + (double)ly) * s,
-                                  ((double)fz + (double)lz) * s, 0.5 * (double)e);
-    a.virial[i] = 0.5 * (double)w;
+    res.fx = ((double)fx + (double)lx) * s;
+    res.fy = ((double)fy + (double)ly) * s;
+    res.fz = ((double)fz + (double)lz) * s;
+    res.e = 0.5 * (double)e;
+    res.w = 0.5 * (double)w;
+    res.set = true;
   }
+}
+
+template <int TPP, bool CUBIC>
+__device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
+  IsoResult res;
+  vertex_iso_mixed_eval<TPP, CUBIC>(a, gt, res);
+  store_iso(a, gt, TPP, res);
 }
 
 template <int TPP, bool CUBIC>

@@ -18,15 +18,7 @@ namespace mdgb {
 // The integrate phase and, in the last block to finish, the step decision (one launch per phase).
 __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a, int mode, int use_cond, unsigned long long cond_handle) {
   integrate_body(a, mode, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
-  __shared__ bool last;
-  __threadfence();  // this block's accumulator and displacement atomics before its ticket
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(a.scr_words + SCR_TICKET, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  if (threadIdx.x == 0) a.scr_words[SCR_TICKET] = 0u;
-  if (threadIdx.x < 32) step_decide_body(a, mode, gridDim.x, use_cond, cond_handle);
+  integrate_epilogue(a, mode, use_cond, cond_handle);
 }
 
 int integrate_blocks(const KArgs& a) { return (a.n + kIntBlock - 1) / kIntBlock; }

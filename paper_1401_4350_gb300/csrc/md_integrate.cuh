@@ -14,19 +14,58 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Warp total of the unevaluated sums s + c of all lanes, with the rounding of every addition kept
-// (TwoSum), left in every lane's (s, c): FP32 operations only, since FP64 ones are scarce on this GPU
-// (about 1.7 per clock per SM) and this runs for every particle.
-__device__ __forceinline__ void warp_sum_ff(float& s, float& c) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    const float o = __shfl_xor_sync(0xffffffffu, s, d), oc = __shfl_xor_sync(0xffffffffu, c, d);
-    const float t = __fadd_rn(s, o);
-    const float bb = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(o, bb));
-    c = __fadd_rn(__fadd_rn(c, oc), err);
-    s = t;
+// x * 2^32 rounded to the nearest integer (halves away from zero), from the binary64 fields with integer
+// operations only.  Valid for |x| < 2^31; zero and subnormal inputs give 0.
+__device__ __forceinline__ long long fixed32_of(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const long long m = (long long)((b & 0xfffffffffffffull) | (1ull << 52));
+  const int sh = e - 1043;  // x * 2^32 = m * 2^(e - 1075 + 32)
+  long long v = 0;
+  if (e != 0) {
+    if (sh >= 0) v = m << min(sh, 10);
+    else if (sh > -64) v = (m + (1ll << (-sh - 1))) >> (-sh);
   }
+  return (b >> 63) ? -v : v;
+}
+
+// The same for an FP32 value (equal to fixed32_of((double)x) for every x).
+__device__ __forceinline__ long long fixed32_of(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xffu);
+  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 118;  // x * 2^32 = m * 2^(e - 150 + 32)
+  long long v = 0;
+  if (e != 0) {
+    if (sh >= 0) v = m << min(sh, 39);
+    else if (sh > -64) v = (m + (1ll << (-sh - 1))) >> (-sh);
+  }
+  return (b >> 31) ? -v : v;
+}
+
+// FP64 -> FP32, rounded to nearest (halves away from zero), from the binary64 fields with integer
+// operations; magnitudes below 2^-126 give signed zero, above the FP32 range infinity.  For the
+// per-particle kinetic terms of the mixed path, where FP32 suffices and the FP64 pipe (which also
+// carries the hardware conversion) is the scarce unit.
+__device__ __forceinline__ float f32_of(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int ef = (int)((hi >> 20) & 0x7ffu) - 896;  // biased FP32 exponent
+  uint32_t mag = ((uint32_t)max(ef, 0) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  mag += (lo >> 28) & 1u;  // a carry out of the significand moves into the exponent, as it should
+  mag = ef <= 0 ? 0u : min(mag, 0x7f800000u);
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+// Warp total of 64-bit integers, in every lane: 32-bit reductions of four 16-bit pieces (exact while
+// the total fits in 64 bits).
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+  const unsigned long long u = (unsigned long long)v;
+  const unsigned p0 = __reduce_add_sync(0xffffffffu, (unsigned)(u & 0xffffu));
+  const unsigned p1 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> 16) & 0xffffu));
+  const unsigned p2 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> 32) & 0xffffu));
+  const int p3 = __reduce_add_sync(0xffffffffu, (int)(v >> 48));
+  return (long long)((unsigned long long)(long long)p3 << 48) + ((long long)p2 << 32) + ((long long)p1 << 16) +
+         (long long)p0;
 }
 
 // Quaternion product a (x) b, (w, x, y, z) stored as double4_32a (x=w, y=x, z=y, w=z).
@@ -151,12 +190,15 @@ __device__ __forceinline__ bool energy_step(const KArgs& a, int mode) {
 }
 
 // One particle's share of a velocity-Verlet phase (every thread of the block calls it: it ends with
-// block reductions); block_index selects the block's slot in block_partials.
-__device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, int block_index) {
+// block reductions).  FUSED: the fused force + integrate kernel hands over the particle's force
+// (Fin: F, E_i; Win: W_i) in registers, and the drift writes pos_alt / fxp_alt instead of updating
+// pos / fxp in place (other threads of that launch still read pos and fxp); isotropic models only.
+template <bool FUSED>
+__device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, const double4_32a& Fin, double Win) {
   const bool valid = i < a.n;
   const bool drift = (mode == 0 || mode == 1);
   const bool energies = energy_step(a, mode);
-  const bool patchy = is_patchy(a.model);
+  const bool patchy = !FUSED && is_patchy(a.model);
   const bool mixed = a.precision == MD_MIXED;
   double kt = 0.0, kr = 0.0, u = 0.0, w = 0.0;  // per-particle energy terms (FP64 values)
   float ktf = 0.f, krf = 0.f;                    // mixed: kinetic terms in FP32
@@ -165,19 +207,19 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
   const bool thermo = thermostat_step(a, mode, tstep);
   if (valid) {
     double4_32a v = a.vel[i];
-    const double4_32a F = a.force[i];
+    const double4_32a F = FUSED ? Fin : a.force[i];
     double vn[3], ln[3];
     const bool refresh = thermo && thermostat_draw(a, tstep, (uint32_t)a.id[i], vn, ln);
     if (energies) {
       u = F.w;
-      w = a.virial[i];
+      w = FUSED ? Win : a.virial[i];
     }
     if (mode == 1) {
       // closing half kick of the finished step (energies from v_n) and opening half kick of the next
       if (mixed) {
         if (energies) {
-          const float vx = (float)v.x + (float)F.x * a.half_dt_over_m_f, vy = (float)v.y + (float)F.y * a.half_dt_over_m_f,
-                      vz = (float)v.z + (float)F.z * a.half_dt_over_m_f;
+          const float vx = f32_of(v.x) + f32_of(F.x) * a.half_dt_over_m_f, vy = f32_of(v.y) + f32_of(F.y) * a.half_dt_over_m_f,
+                      vz = f32_of(v.z) + f32_of(F.z) * a.half_dt_over_m_f;
           ktf = a.half_mass_f * (vx * vx + vy * vy + vz * vz);
         }
         if (refresh) {  // the refreshed velocity replaces v_n; then the opening half kick
@@ -214,7 +256,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
     }
     if (mode == 2 || mode == 3) {
       if (mixed) {
-        const float vx = (float)v.x, vy = (float)v.y, vz = (float)v.z;
+        const float vx = f32_of(v.x), vy = f32_of(v.y), vz = f32_of(v.z);
         ktf = a.half_mass_f * (vx * vx + vy * vy + vz * vz);
       } else {
         kt = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
@@ -228,7 +270,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
       if (mode == 1) {
         L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
         if (mixed) {
-          const float lx = (float)L.x, ly = (float)L.y, lz = (float)L.z;
+          const float lx = f32_of(L.x), ly = f32_of(L.y), lz = f32_of(L.z);
           krf = 0.5f * a.inv_inertia_f * (lx * lx + ly * ly + lz * lz);
         } else {
           kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
@@ -241,7 +283,7 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
       }
       if (mode == 2 || mode == 3) {
         if (mixed) {
-          const float lx = (float)L.x, ly = (float)L.y, lz = (float)L.z;
+          const float lx = f32_of(L.x), ly = f32_of(L.y), lz = f32_of(L.z);
           krf = 0.5f * a.inv_inertia_f * (lx * lx + ly * ly + lz * lz);
         } else {
           kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
@@ -259,10 +301,10 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
       x.x = fma(v.x, a.dt, x.x);
       x.y = fma(v.y, a.dt, x.y);
       x.z = fma(v.z, a.dt, x.z);
-      a.pos[i] = x;
+      (FUSED ? a.pos_alt : a.pos)[i] = x;
       if (!finite3(x)) record_error(a.status, MD_ERR_NONFINITE);
       const uint4 f = fixed3(x, a);
-      a.fxp[i] = f;
+      (FUSED ? a.fxp_alt : a.fxp)[i] = f;
       const uint4 b = a.fxp_build[i];
       const float dx = (float)(int)(f.x - b.x) * a.fxp_unit[0];
       const float dy = (float)(int)(f.y - b.y) * a.fxp_unit[1];
@@ -278,30 +320,40 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
     if (lane == 0 && m) atomicMax(a.scr_words + SCR_DISPMAX, m);
   }
   if (energies) {
-    __shared__ double sred[kIntBlock / 32][4];
-    __shared__ float sredf[kIntBlock / 32][4][2];
+    // totals in 64-bit fixed point (2^-32 units) in integer atomics: exact, and independent of the
+    // order in which blocks finish
+    __shared__ long long sred[kIntBlock / 32][4];
     if (mixed) {
-      // compensated FP32 sums within the warp, (sum, error) per warp into shared memory; U_i and W_i
-      // of the mixed paths are FP32 values stored in FP64 words, so they enter as FP32
-      float s[4] = {ktf, patchy ? krf : 0.f, (float)u, (float)w}, c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < 4; k++) warp_sum_ff(s[k], c[k]);
-      if (lane == 0)
-        for (int k = 0; k < 4; k++) { sredf[wid][k][0] = s[k]; sredf[wid][k][1] = c[k]; }
+      // every particle's FP32 terms (U_i and W_i are FP32 values in FP64 words) rounded to fixed point
+      // once, then exact integer sums: the totals do not depend on how particles fall into warps and
+      // blocks, and no FP64 instruction is spent
+      const long long q0 = warp_sum_i64(fixed32_of(ktf));
+      const long long q1 = patchy ? warp_sum_i64(fixed32_of(krf)) : 0ll;
+      const long long q2 = warp_sum_i64(fixed32_of(u)), q3 = warp_sum_i64(fixed32_of(w));
+      if (lane == 0) { sred[wid][0] = q0; sred[wid][1] = q1; sred[wid][2] = q2; sred[wid][3] = q3; }
     } else {
       const double s0 = warp_sum(kt), s1 = warp_sum(kr), s2 = warp_sum(u), s3 = warp_sum(w);
-      if (lane == 0) { sred[wid][0] = s0; sred[wid][1] = s1; sred[wid][2] = s2; sred[wid][3] = s3; }
+      if (lane == 0) {
+        sred[wid][0] = llrint(s0 * 4294967296.0);
+        sred[wid][1] = llrint(s1 * 4294967296.0);
+        sred[wid][2] = llrint(s2 * 4294967296.0);
+        sred[wid][3] = llrint(s3 * 4294967296.0);
+      }
     }
     __syncthreads();
     if (threadIdx.x < 4) {
-      double t = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++)
-        t += mixed ? (double)sredf[k][threadIdx.x][0] + (double)sredf[k][threadIdx.x][1] : sred[k][threadIdx.x];
-      // block sum -> 64-bit fixed point (2^-32 units): integer atomics make the total exact and
-      // independent of the order in which blocks finish
-      atomicAdd(energy_accumulators(a) + threadIdx.x, (unsigned long long)llrint(t * 4294967296.0));
+      long long t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sred[k][threadIdx.x];
+      if (t) atomicAdd(energy_accumulators(a) + threadIdx.x, (unsigned long long)t);
     }
   }
+}
+
+// One particle's share of a phase with the force read from the force arrays (the separate integrate
+// kernels); block_index is kept for the batched callers.
+__device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, int block_index) {
+  (void)block_index;
+  integrate_core<false>(a, mode, i, make_double4_32a(0.0, 0.0, 0.0, 0.0), 0.0);
 }
 
 // Run by the last block of an integrate launch (or the batch's per-replica decide): the FP64 energy
@@ -341,6 +393,21 @@ __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int n
       if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, g);
     }
   }
+}
+
+// End of every launch that integrates a step (every thread calls it after integrate_core): the block
+// takes a ticket once its accumulator and displacement atomics are visible, and the last block to
+// finish makes the step decision.
+__device__ __forceinline__ void integrate_epilogue(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle) {
+  __shared__ bool last;
+  __threadfence();  // this block's accumulator and displacement atomics before its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.scr_words + SCR_TICKET, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) a.scr_words[SCR_TICKET] = 0u;
+  if (threadIdx.x < 32) step_decide_body(a, mode, gridDim.x, use_cond, cond_handle);
 }
 
 }  // namespace mdgb

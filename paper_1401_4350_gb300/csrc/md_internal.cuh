@@ -4,6 +4,9 @@
 //   pos/vel/quat/angmom  double4_32a [n]      FP64 state (caller-owned)
 //   fxp                  uint4   [n]      x/L * 2^32 per axis (periodic by integer wrap-around)
 //   fxp_build            uint4   [n]      fxp at the last Verlet build (skin criterion)
+//   pos_alt/fxp_alt      the second position / fixed-point buffers of fused steps (fuse_step = 1):
+//                        a fused launch reads pos/fxp and writes pos_alt/fxp_alt, and the next
+//                        launch runs with the two swapped
 //   patch_lab            float4 or double4_32a [n][MD_MAX_PATCH]  lab-frame patch sites
 //   nbr                  int32   [ceil(max_neigh/4)][n][4] full list: entry k of slot i at
 //                        ((k/4) n + i) 4 + k%4 (int4 groups, coalesced per warp)
@@ -117,6 +120,8 @@ struct KArgs {
   const int32_t* cell_rank;  // Hilbert order: position of each row-major cell id along the curve (else null)
   uint4* fxp;
   uint4* fxp_build;
+  double4_32a* pos_alt;  // fused steps: where the drift of this launch writes (else null)
+  uint4* fxp_alt;
   void* patch_lab;
   int32_t* nbr;
   int32_t* nbr_count;
@@ -165,6 +170,9 @@ cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st);
 // energies), 3 = energies only, 4 = derived arrays only (fxp, patch_lab).
 cudaError_t launch_integrate(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle,
                              cudaStream_t st);
+// The fused force + integrate step (MIDDLE phase) of the isotropic mixed vertex path: reads pos/fxp,
+// writes the drifted state to pos_alt/fxp_alt; the last block makes the step decision.
+cudaError_t launch_step_fused(const KArgs& a, int block, int use_cond, unsigned long long cond_handle, cudaStream_t st);
 cudaError_t launch_get_forces(const KArgs& a, double* fout, double* tout, cudaStream_t st);
 cudaError_t launch_init_ws(const KArgs& a, cudaStream_t st);
 int integrate_blocks(const KArgs& a);

@@ -1,0 +1,54 @@
+// md_step.cu -- one kernel per velocity-Verlet step for the isotropic mixed-precision vertex path.
+//
+// A step of Sec. Methods is a force evaluation followed by the integration that uses it.  With the
+// vertex decomposition each particle's force is complete once its own thread (or group of tpp
+// threads) has walked its list, and the integration of that particle needs nothing else, so the
+// owner thread goes on to integrate the particle in the same launch: the closing half kick of the
+// step whose forces these are, the opening half kick and the drift of the next step, the squared
+// displacement since the last build, and the energy contributions.  The force never goes to memory
+// and there is one launch per step instead of two.
+//
+// Other threads of the launch still gather the coordinates (fxp) and, near rc, the FP64 positions
+// (pos) of this particle, so the drift writes the new ones to the second buffers (pos_alt, fxp_alt);
+// the caller swaps the two buffer sets between launches.  The last block to finish makes the step
+// decision exactly as the separate integrate kernel does.
+#include "md_forces.cuh"
+#include "md_integrate.cuh"
+
+namespace mdgb {
+
+template <int TPP, bool CUBIC>
+__global__ void __launch_bounds__(256, 4) k_vertex_step_mixed(KArgs a, int use_cond, unsigned long long cond_handle) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  IsoResult res;
+  vertex_iso_mixed_eval<TPP, CUBIC>(a, gt, res);
+  // the owner of each particle integrates it (its force is zero if the list was not current, which
+  // has been recorded as an error); the other threads of its group only join the block reductions
+  const int i = (gt % TPP == 0) ? gt / TPP : a.n;
+  integrate_core<true>(a, 1, i, make_double4_32a(res.fx, res.fy, res.fz, res.e), res.w);
+  integrate_epilogue(a, 1, use_cond, cond_handle);
+}
+
+cudaError_t launch_step_fused(const KArgs& a, int block, int use_cond, unsigned long long cond_handle, cudaStream_t st) {
+  if (block <= 0) block = 128;
+  const int64_t threads = (int64_t)a.n * a.tpp;
+  const int grid = (int)((threads + block - 1) / block);
+  if (a.cubic) {
+    switch (a.tpp) {
+      case 1: k_vertex_step_mixed<1, true><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+      case 2: k_vertex_step_mixed<2, true><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+      case 4: k_vertex_step_mixed<4, true><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+      default: k_vertex_step_mixed<8, true><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+    }
+  } else {
+    switch (a.tpp) {
+      case 1: k_vertex_step_mixed<1, false><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+      case 2: k_vertex_step_mixed<2, false><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+      case 4: k_vertex_step_mixed<4, false><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+      default: k_vertex_step_mixed<8, false><<<grid, block, 0, st>>>(a, use_cond, cond_handle); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mdgb

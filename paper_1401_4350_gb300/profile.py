@@ -4,7 +4,9 @@
 
 Builds the seeded workload, prepares cells, lists and forces once, then launches the chosen phase
 `reps` times (forces: md_forces_vertex / md_forces_edge; build: md_build_cells + md_build_verlet;
-step: md_step_verlet of one step).  Prints the median CUDA-event time per launch.
+step: md_step_verlet of one step; steps3: of three steps; stepkernel: md_time_step_kernel, the kernel
+one step runs, i.e. the fused force + integrate kernel when fuse_step applies).  Prints the median
+CUDA-event time per call.
 """
 from __future__ import annotations
 
@@ -32,7 +34,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="lj524288", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--path", default="vertex", choices=["vertex", "edge"])
-    ap.add_argument("--what", default="forces", choices=["forces", "build", "step", "steps3"])
+    ap.add_argument("--what", default="forces", choices=["forces", "build", "step", "steps3", "stepkernel"])
+    ap.add_argument("--fuse", type=int, default=1, choices=[0, 1], help="fuse_step of the system")
     ap.add_argument("--tpp", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--order", default="rows", choices=["rows", "hilbert"])
@@ -44,7 +47,8 @@ def main(argv=None):
     s = WORKLOADS[a.workload]()
     prec = B.MD_MIXED if a.precision == "mixed" else B.MD_FP64
     path = B.MD_VERTEX if a.path == "vertex" else B.MD_EDGE
-    sim = Simulation(s, prec, tpp=a.tpp, cell_order=B.MD_ORDER_HILBERT if a.order == "hilbert" else B.MD_ORDER_ROWS)
+    sim = Simulation(s, prec, tpp=a.tpp, cell_order=B.MD_ORDER_HILBERT if a.order == "hilbert" else B.MD_ORDER_ROWS,
+                     fuse_step=a.fuse)
     sim.prepare(path)
     if a.equilibrate > 0:  # time the liquid rather than the initial lattice
         sim.step(a.equilibrate, path, use_graph=True)
@@ -58,9 +62,12 @@ def main(argv=None):
     elif a.what == "step":
         def fn():
             sim.step(1, path, use_graph=False)
-    else:  # three steps: the integrate launches are FIRST, MIDDLE, MIDDLE, LAST
+    elif a.what == "steps3":  # three steps: FIRST, then MIDDLE or fused launches, LAST
         def fn():
             sim.step(3, path, use_graph=False)
+    else:  # the kernel one step runs (fused step kernel or force kernel): a warm-up and one timed launch
+        def fn():
+            sim.time_step_kernel(path, reps=1)
     st = torch.cuda.current_stream()
     fn()  # warm-up launch
     torch.cuda.synchronize()
@@ -80,11 +87,11 @@ def main(argv=None):
 
 
 def source_digest() -> str:
-    """sha256 of the force-kernel sources (the same digest bench.py checks before it quotes a capture)."""
+    """sha256 of the step-kernel sources (the same digest bench.py checks before it quotes a capture)."""
     import hashlib
     import os
     h = hashlib.sha256()
-    for f in ("md_forces.cuh", "md_forces.cu", "md_internal.cuh"):
+    for f in ("md_forces.cuh", "md_forces.cu", "md_internal.cuh", "md_integrate.cuh", "md_step.cu"):
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

@@ -26,7 +26,7 @@ def default_capacities(system: System, slack: float = 1.6):
 
 def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, tpp: int = 1, block: int = 0,
                 trace_capacity: int = 0, energy_every: int = 1, force_copies: int = 0,
-                cell_order: int = 0, edge_store: int = 0, list_format: int = 0) -> B.md_params:
+                cell_order: int = 0, edge_store: int = 0, list_format: int = 0, fuse_step: int = 0) -> B.md_params:
     mn, mp = default_capacities(system)
     p = B.md_params()
     p.n = system.n
@@ -43,6 +43,7 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
     p.cell_order = cell_order
     p.edge_store = edge_store
     p.list_format = list_format
+    p.fuse_step = fuse_step
     for c in range(3):
         p.box[c] = float(system.box[c])
     p.rc, p.skin, p.dt, p.mass, p.inertia = system.rc, system.skin, system.dt, system.mass, system.inertia
@@ -61,10 +62,11 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
 class Simulation:
     def __init__(self, system: System, precision: int = B.MD_MIXED, max_neigh=None, max_pairs=None, tpp: int = 1,
                  block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None, energy_every: int = 1,
-                 force_copies: int = 0, cell_order: int = 0, edge_store: int = 0, list_format: int = 0):
+                 force_copies: int = 0, cell_order: int = 0, edge_store: int = 0, list_format: int = 0,
+                 fuse_step: int = 1):
         self.system = system
         self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity, energy_every,
-                                  force_copies, cell_order, edge_store, list_format)
+                                  force_copies, cell_order, edge_store, list_format, fuse_step)
         rc = B.md_check_params(self.params)
         if rc != B.MD_OK:
             raise B.MDError(rc, B.last_error())
@@ -132,6 +134,11 @@ class Simulation:
         candidate (binding.TUNE_CANDIDATES); returns (path, threads_per_particle, block_size, median ms per
         candidate).  self.params is updated; lists and forces stay prepared for the choice."""
         return B.md_autotune_system(self.params, self.state(), self.ws, self._st())
+
+    def time_step_kernel(self, path=B.MD_VERTEX, reps: int = 20) -> float:
+        """Mean ms of the kernel one step of `path` runs (the fused step kernel where fuse_step applies,
+        else the force kernel); the system is left as it was."""
+        return B.md_time_step_kernel(self.params, self.state(), self.ws, path, reps, self._st())
 
     def prepare(self, path=B.MD_VERTEX):
         B.md_prepare(self.params, self.state(), self.ws, path, self._st())

@@ -29,7 +29,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_abi_version(lib):
-    assert B.md_abi_version() == 2
+    assert B.md_abi_version() == 3
 
 
 def _lj_params(n=4000, precision=B.MD_MIXED):
@@ -51,7 +51,7 @@ def _lj_params(n=4000, precision=B.MD_MIXED):
     ("force_copies", -1, "force_copies"),
     ("force_copies", 65, "force_copies"),
     ("list_format", 2, "list_format"),
-    ("reserved", 1, "reserved"),
+    ("fuse_step", 2, "fuse_step"),
     ("cell_order", 2, "cell_order"),
     ("thermostat_every", -1, "thermostat_every"),
 ])
@@ -93,7 +93,8 @@ def test_workspace_layout(lib, precision, kind):
     assert L.total == B.md_workspace_bytes(p) > 0
     offs = [getattr(L, f) for f in ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr",
                                     "nbr_count", "half_start", "pairs", "force", "virial", "torque",
-                                    "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace", "scratch")]
+                                    "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace", "pos_alt",
+                                    "fxp_alt", "scratch")]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and len(set(offs)) == len(offs)
     assert L.force_elem == 8
@@ -140,6 +141,22 @@ def test_struct_layouts_match_c(lib, tmp_path):
         assert int(out[st]) == ctypes.sizeof(cls), st
         for nm in fields[st]:
             assert int(out[f"{st}.{nm}"]) == getattr(cls, nm).offset, (st, nm)
+
+
+@pytest.mark.parametrize("precision", [B.MD_FP64, B.MD_MIXED])
+def test_fused_step_buffers(lib, precision):
+    """fuse_step = 1 reserves the second position (double[n][4]) and fixed-point (uint32[n][4]) buffers;
+    fuse_step = 0 leaves them empty; nothing else moves."""
+    s = systems.make_lj(3000, 0.85, seed=5)
+    p = make_params(s, precision)
+    L0 = B.md_workspace_layout(p)
+    assert L0.fxp_alt - L0.pos_alt <= 256 and L0.scratch - L0.fxp_alt <= 256
+    p.fuse_step = 1
+    L1 = B.md_workspace_layout(p)
+    assert L1.fxp_alt - L1.pos_alt >= 32 * s.n and L1.scratch - L1.fxp_alt >= 16 * s.n
+    assert L1.total - L0.total >= 48 * s.n - 512  # the empty regions held 256 bytes each
+    for f in ("status", "fxp", "nbr", "force", "trace", "pos_alt"):
+        assert getattr(L1, f) == getattr(L0, f)
 
 
 @pytest.mark.parametrize("precision", [B.MD_FP64, B.MD_MIXED])
