@@ -305,9 +305,10 @@ def run_ours(args, rank, world, dist):
         "variants": results,
         "roofline": roofline,
         "e2e": e2e,
-        # one call of K fused steps: the opening integrate, K - 1 fused step kernels (each one's last block
-        # decides), then the last forces and the closing integrate; a rebuild adds 9 cell and 2 Verlet kernels
-        "gpu_launches": args.steps + 2 + 11 * rebuilds,
+        # one call of K fused steps: the opening integrate (its last block decides), K - 1 fused step
+        # kernels each followed by a one-warp decision kernel, then the last forces and the closing
+        # integrate; a rebuild adds 9 cell and 2 Verlet kernels
+        "gpu_launches": 2 * args.steps + 1 + 11 * rebuilds,
         "clocks": clocks,
         "graph": not args.direct,
     }

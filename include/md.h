@@ -128,7 +128,9 @@ typedef struct md_params {
   int64_t max_pairs;             /* half-list capacity in pairs, >= 1                            */
   int32_t n_patch;               /* patchy: patch sites per particle, 1..MD_MAX_PATCH            */
   int32_t threads_per_particle;  /* vertex path: 1, 2, 4 or 8 threads cooperate on a particle   */
-  int32_t block_size;            /* force-kernel CTA size: 0 (default) or 32..1024, multiple of 32 */
+  int32_t block_size;            /* force-kernel CTA size: 0 (default: 128 for the vertex kernels,
+                                    256 for the edge kernels, 64 for the fused step kernel) or a
+                                    multiple of 32 in [32, 256]                                   */
   int32_t trace_capacity;        /* energy-trace rows kept by md_step_verlet (0 = none)         */
   int32_t energy_every;          /* md_step_verlet reduces energies on steps that are multiples of this
                                     (0 or 1: every step); the last step of a call always            */
@@ -235,7 +237,10 @@ int md_check_params(const md_params* p);
 /* Workspace size in bytes for p (0 if p is invalid). */
 size_t md_workspace_bytes(const md_params* p);
 
-/* Fills *out with the workspace layout for p.  Returns MD_OK or MD_ERR_INVALID. */
+/* Fills *out with the workspace layout for p.  Returns MD_OK or MD_ERR_INVALID.  The layout depends on
+ * the fields of p (sizes, capacities, model, precision and the options that reserve regions), so a
+ * workspace serves only calls with the md_params it was laid out and initialised for; changing such a
+ * field (e.g. fuse_step) needs a new workspace. */
 int md_workspace_layout(const md_params* p, md_ws_layout* out);
 
 /* Clears the workspace status, energy and trace words and the displacement
@@ -346,8 +351,8 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
  * a call.
  *
  * md_time_step_kernel -- mean duration (ms, CUDA events on `stream`; synchronises) of `reps` launches
- * of the kernel that md_step_verlet runs once per step for `path`: the fused kernel when fuse_step
- * applies, else the force kernel.  Cells, lists and forces must be current (md_prepare).  The
+ * of what md_step_verlet runs once per step for `path` besides the rebuild: the fused kernel and the
+ * one-warp step-decision kernel after it when fuse_step applies, else the force kernel.  Cells, lists and forces must be current (md_prepare).  The
  * velocities, status, energy, trace and decision words are restored afterwards, so the system is left
  * as it was.  Returns MD_OK, MD_ERR_INVALID or MD_ERR_CUDA.
  */

@@ -155,8 +155,7 @@ static size_t copies_bytes(const md_params* p) {
 
 struct Layout {
   md_ws_layout pub;
-  size_t scr_words, block_partials, cell_of, rank, perm, count_tmp, block_sums, tmp_d4, tmp_i, cell_rank;
-  int partial_capacity;
+  size_t scr_words, acc_slots, cell_of, rank, perm, count_tmp, block_sums, tmp_d4, tmp_i, cell_rank;
 };
 
 static void make_layout(const md_params* p, Layout* L) {
@@ -200,9 +199,7 @@ static void make_layout(const md_params* p, Layout* L) {
   P.fxp_alt = take(p->fuse_step ? 16 * n : 0);
   P.scratch = off;
   L->scr_words = take(sizeof(uint32_t) * SCR_WORDS);
-  const int nblk = (int)((n + 255) / 256);
-  L->partial_capacity = nblk;
-  L->block_partials = take(sizeof(double) * 4 * (size_t)nblk);
+  L->acc_slots = take(sizeof(unsigned long long) * 4 * kAccSlots + sizeof(uint32_t) * kAccSlots);
   L->cell_of = take(sizeof(int32_t) * n);
   L->rank = take(sizeof(int32_t) * n);
   L->perm = take(sizeof(int32_t) * n);
@@ -380,7 +377,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.jedge = p->edge_store ? (int32_t*)(w + L.pub.jedge) : nullptr;
   a.trace = (double*)(w + L.pub.trace);
   a.scr_words = (uint32_t*)(w + L.scr_words);
-  a.block_partials = (double*)(w + L.block_partials);
+  a.acc_slots = (unsigned long long*)(w + L.acc_slots);
   a.cell_of = (int32_t*)(w + L.cell_of);
   a.rank = (int32_t*)(w + L.rank);
   a.perm = (int32_t*)(w + L.perm);
@@ -389,7 +386,6 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.tmp_d4 = (double4_32a*)(w + L.tmp_d4);
   a.tmp_i = (int32_t*)(w + L.tmp_i);
   a.cell_rank = p->cell_order == MD_ORDER_HILBERT ? (const int32_t*)(w + L.cell_rank) : nullptr;
-  a.partial_capacity = L.partial_capacity;
   return a;
 }
 
@@ -404,7 +400,7 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
   a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
   a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr; a.local_ok = 0; a.local_tab = nullptr;
-  a.scr_words = nullptr; a.block_partials = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;
+  a.scr_words = nullptr; a.acc_slots = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;
   a.count_tmp = nullptr; a.block_sums = nullptr; a.tmp_d4 = nullptr; a.tmp_i = nullptr; a.cell_rank = nullptr;
   return a;
 }
@@ -823,9 +819,10 @@ int md_time_step_kernel(const md_params* p, md_state* s, void* ws, int32_t path,
   char* w = (char*)ws;
   // what a launch changes besides the force arrays: status, energy, trace and decision words and the
   // energy accumulators (kept on the host), and, fused, the velocities (kept in the cell-sort scratch)
-  const size_t off[5] = {L.pub.status, L.pub.energy, L.pub.trace, L.scr_words, L.block_partials};
+  const size_t off[5] = {L.pub.status, L.pub.energy, L.pub.trace, L.scr_words, L.acc_slots};
   const size_t len[5] = {sizeof(int32_t) * MD_STATUS_WORDS, sizeof(double) * MD_ENERGY_WORDS,
-                         sizeof(double) * 4 * (size_t)p->trace_capacity, sizeof(uint32_t) * SCR_WORDS, 32};
+                         sizeof(double) * 4 * (size_t)p->trace_capacity, sizeof(uint32_t) * SCR_WORDS,
+                         sizeof(unsigned long long) * 4 * kAccSlots + sizeof(uint32_t) * kAccSlots};
   size_t total = 0;
   for (int k = 0; k < 5; k++) total += len[k];
   std::vector<char> keep(total);

@@ -99,7 +99,7 @@ __global__ void k_b_init(BatchDev b) {
   if (t < MD_STATUS_WORDS) ka.status[t] = 0;
   if (t < MD_ENERGY_WORDS) ka.energy[t] = 0.0;
   if (t < SCR_WORDS) ka.scr_words[t] = 0u;
-  if (t < 4) ((unsigned long long*)ka.block_partials)[t] = 0ULL;  // energy accumulators
+  for (int k = t; k < 9 * kAccSlots; k += blockDim.x) ((uint32_t*)ka.acc_slots)[k] = 0u;  // step accumulators
   for (int k = t; k < ka.trace_capacity * 4; k += blockDim.x) ka.trace[k] = 0.0;
   for (int k = t; k < ka.n; k += blockDim.x) ka.nbr_count[k] = 0;
   for (int k = t; k <= ka.n; k += blockDim.x) ka.half_start[k] = 0;

@@ -10,7 +10,8 @@
 //   3 ENERGY: energies of the current state only
 // After a drift each thread refreshes the fixed-point coordinates (and patch sites) used by the
 // pair kernels and its squared displacement since the last Verlet build; the last block to finish
-// turns the largest one into the rebuild decision (max > (skin/2)^2) and forms the FP64 energy totals.
+// turns the largest one into the rebuild decision (max > (skin/2)^2) and forms the FP64 energy totals
+// (after a fused force + integrate launch, a one-warp kernel does that instead).
 #include "md_integrate.cuh"
 
 namespace mdgb {
@@ -19,6 +20,16 @@ namespace mdgb {
 __global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a, int mode, int use_cond, unsigned long long cond_handle) {
   integrate_body(a, mode, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
   integrate_epilogue(a, mode, use_cond, cond_handle);
+}
+
+// The step decision alone (one warp), after a launch that integrated without a ticket.
+__global__ void __launch_bounds__(32) k_step_decide(KArgs a, int mode, int use_cond, unsigned long long cond_handle) {
+  step_decide_body(a, mode, 0, use_cond, cond_handle);
+}
+
+cudaError_t launch_decide(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle, cudaStream_t st) {
+  k_step_decide<<<1, 32, 0, st>>>(a, mode, use_cond, cond_handle);
+  return cudaGetLastError();
 }
 
 int integrate_blocks(const KArgs& a) { return (a.n + kIntBlock - 1) / kIntBlock; }
@@ -52,7 +63,7 @@ __global__ void k_init_ws(KArgs a) {
   if (t < MD_STATUS_WORDS) a.status[t] = 0;
   if (t < MD_ENERGY_WORDS) a.energy[t] = 0.0;
   if (t < SCR_WORDS) a.scr_words[t] = 0u;
-  if (t < 4) ((unsigned long long*)a.block_partials)[t] = 0ULL;  // energy accumulators
+  if (t < 9 * kAccSlots) ((uint32_t*)a.acc_slots)[t] = 0u;  // step accumulators ([4][kAccSlots] u64, [kAccSlots] u32)
   for (int k = t; k < a.trace_capacity * 4; k += gridDim.x * blockDim.x) a.trace[k] = 0.0;
   // empty lists until the first build: force kernels called early see no pairs
   for (int k = t; k < a.n; k += gridDim.x * blockDim.x) a.nbr_count[k] = 0;

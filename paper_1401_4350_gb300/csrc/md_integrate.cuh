@@ -122,10 +122,14 @@ __device__ __forceinline__ bool finite3(const double4_32a& p) {
   return ((__double2hiint(p.x) & e) != e) & ((__double2hiint(p.y) & e) != e) & ((__double2hiint(p.z) & e) != e);
 }
 
-// The four energy accumulators (K_trans, K_rot, U, W) as 64-bit fixed-point words in 2^-32 units,
-// kept in the first 32 bytes of the block-partials scratch.
-__device__ __forceinline__ unsigned long long* energy_accumulators(const KArgs& a) {
-  return (unsigned long long*)a.block_partials;
+// Step accumulators: slot k of energy quantity q (K_trans, K_rot, U, W; 64-bit fixed point, 2^-32
+// units) and slot k of the largest squared displacement (float bits).  Warps add into slot
+// (global warp index mod kAccSlots), so no address takes more than a 1/kAccSlots share of the atomics.
+__device__ __forceinline__ unsigned long long* energy_slot(const KArgs& a, int q, int k) {
+  return a.acc_slots + q * kAccSlots + k;
+}
+__device__ __forceinline__ unsigned* disp_slot(const KArgs& a, int k) {
+  return (unsigned*)(a.acc_slots + 4 * kAccSlots) + k;
 }
 
 // ---- thermostat: momentum refresh with counter-based random numbers ------------------------------
@@ -190,7 +194,7 @@ __device__ __forceinline__ bool energy_step(const KArgs& a, int mode) {
 }
 
 // One particle's share of a velocity-Verlet phase (every thread of the block calls it: it ends with
-// block reductions).  FUSED: the fused force + integrate kernel hands over the particle's force
+// warp reductions).  FUSED: the fused force + integrate kernel hands over the particle's force
 // (Fin: F, E_i; Win: W_i) in registers, and the drift writes pos_alt / fxp_alt instead of updating
 // pos / fxp in place (other threads of that launch still read pos and fxp); isotropic models only.
 template <bool FUSED>
@@ -313,38 +317,49 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
       if (!(disp2 == disp2)) disp2 = 3.0e38f;  // NaN: force a rebuild (and the error is recorded)
     }
   }
-  // ---- per-block reductions; the totals are formed by the step decision ----
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // ---- reductions into the step accumulators; the totals are formed by the step decision ----
+  // FUSED: per warp, without a block barrier (a warp that is done leaves at once, which matters inside
+  // the long force walk); else per block, which keeps the atomics, and the fence before the ticket that
+  // waits for them, to one set per block.
+  const int lane = threadIdx.x & 31;
+  const int slot = (int)((FUSED ? blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) : blockIdx.x) % kAccSlots);
   if (drift) {
     const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
-    if (lane == 0 && m) atomicMax(a.scr_words + SCR_DISPMAX, m);
+    if (lane == 0 && m) atomicMax(disp_slot(a, slot), m);
   }
   if (energies) {
     // totals in 64-bit fixed point (2^-32 units) in integer atomics: exact, and independent of the
-    // order in which blocks finish
-    __shared__ long long sred[kIntBlock / 32][4];
+    // order in which warps finish
+    long long q[4];
     if (mixed) {
       // every particle's FP32 terms (U_i and W_i are FP32 values in FP64 words) rounded to fixed point
       // once, then exact integer sums: the totals do not depend on how particles fall into warps and
       // blocks, and no FP64 instruction is spent
-      const long long q0 = warp_sum_i64(fixed32_of(ktf));
-      const long long q1 = patchy ? warp_sum_i64(fixed32_of(krf)) : 0ll;
-      const long long q2 = warp_sum_i64(fixed32_of(u)), q3 = warp_sum_i64(fixed32_of(w));
-      if (lane == 0) { sred[wid][0] = q0; sred[wid][1] = q1; sred[wid][2] = q2; sred[wid][3] = q3; }
+      q[0] = warp_sum_i64(fixed32_of(ktf));
+      q[1] = patchy ? warp_sum_i64(fixed32_of(krf)) : 0ll;
+      q[2] = warp_sum_i64(fixed32_of(u));
+      q[3] = warp_sum_i64(fixed32_of(w));
     } else {
-      const double s0 = warp_sum(kt), s1 = warp_sum(kr), s2 = warp_sum(u), s3 = warp_sum(w);
-      if (lane == 0) {
-        sred[wid][0] = llrint(s0 * 4294967296.0);
-        sred[wid][1] = llrint(s1 * 4294967296.0);
-        sred[wid][2] = llrint(s2 * 4294967296.0);
-        sred[wid][3] = llrint(s3 * 4294967296.0);
-      }
+      q[0] = llrint(warp_sum(kt) * 4294967296.0);
+      q[1] = llrint(warp_sum(kr) * 4294967296.0);
+      q[2] = llrint(warp_sum(u) * 4294967296.0);
+      q[3] = llrint(warp_sum(w) * 4294967296.0);
     }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-      long long t = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sred[k][threadIdx.x];
-      if (t) atomicAdd(energy_accumulators(a) + threadIdx.x, (unsigned long long)t);
+    if (FUSED) {
+      if (lane < 4) {
+        const long long t = lane == 0 ? q[0] : lane == 1 ? q[1] : lane == 2 ? q[2] : q[3];
+        if (t) atomicAdd(energy_slot(a, lane, slot), (unsigned long long)t);
+      }
+    } else {
+      __shared__ long long sred[kIntBlock / 32][4];
+      if (lane == 0)
+        for (int c = 0; c < 4; c++) sred[threadIdx.x >> 5][c] = q[c];
+      __syncthreads();
+      if (threadIdx.x < 4) {
+        long long t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sred[k][threadIdx.x];
+        if (t) atomicAdd(energy_slot(a, threadIdx.x, slot), (unsigned long long)t);
+      }
     }
   }
 }
@@ -356,20 +371,27 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
   integrate_core<false>(a, mode, i, make_double4_32a(0.0, 0.0, 0.0, 0.0), 0.0);
 }
 
-// Run by the last block of an integrate launch (or the batch's per-replica decide): the FP64 energy
-// totals from the fixed-point accumulators, the trace row, the step counter, and the rebuild decision (largest displacement since the build against (skin/2)^2), which
-// sets the gate word for the gated rebuild kernels and, inside a graph, the IF node's condition.
+// Run by the first warp of the step decision (the last block of an integrate launch, the decision
+// kernel after a fused step, or the batch's per-replica decide): the FP64 energy totals from the
+// fixed-point accumulators, the trace row, the step counter, and the rebuild decision (largest
+// displacement since the build against (skin/2)^2), which sets the gate word for the gated rebuild
+// kernels and, inside a graph, the IF node's condition.  The accumulators are cleared for the next step.
 __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int nblocks, int use_cond,
                                                  unsigned long long cond_handle) {
+  if (threadIdx.x >= 32) return;
   const bool drift = (mode == 0 || mode == 1);
   const bool energies = energy_step(a, mode);
+  const int lane = threadIdx.x;
   (void)nblocks;
+  // read and clear at L2, where the warps' atomics landed: one slot per lane
+  unsigned m = 0u;
+  if (drift) m = __reduce_max_sync(0xffffffffu, atomicExch(disp_slot(a, lane), 0u));
   if (energies) {
-    if (threadIdx.x == 0) {
-      unsigned long long* acc = energy_accumulators(a);
+    long long tot[4];
+    for (int c = 0; c < 4; c++) tot[c] = warp_sum_i64((long long)atomicExch(energy_slot(a, c, lane), 0ULL));
+    if (lane == 0) {
       double v[4];
-      for (int c = 0; c < 4; c++)  // read and clear at L2: the blocks' atomics landed there
-        v[c] = (double)(long long)atomicExch(acc + c, 0ULL) * (1.0 / 4294967296.0);
+      for (int c = 0; c < 4; c++) v[c] = (double)tot[c] * (1.0 / 4294967296.0);
       const double K = v[0], KR = v[1], U = v[2], W = v[3];
       a.energy[MD_ENERGY_U] = U;
       a.energy[MD_ENERGY_KT] = K;
@@ -383,10 +405,9 @@ __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int n
       }
     }
   }
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
     if (mode == 1 || mode == 2) a.status[MD_STATUS_STEPS] += 1;
     if (drift) {
-      const unsigned m = atomicExch(a.scr_words + SCR_DISPMAX, 0u);
       const unsigned g = __uint_as_float(m) > a.disp_thr2 ? 1u : 0u;
       a.scr_words[SCR_GATE] = g;
       a.status[MD_STATUS_REBUILDS] += (int)g;

@@ -25,11 +25,12 @@ namespace mdgb {
 constexpr int kScanItems = 4;      // elements per thread in the block scan
 constexpr int kScanThreads = 512;  // threads per scan block
 constexpr int kScanTile = kScanItems * kScanThreads;
+constexpr int kAccSlots = 32;      // slots of the step accumulators (one warp reads them all)
 
 // Scratch words at the start of the scratch region (uint32 each).
 enum {
   SCR_TICKET = 0,     // last-block ticket of the integrate kernels
-  SCR_DISPMAX = 1,    // max squared displacement since the build (float bits)
+  SCR_SPARE1 = 1,     // spare
   SCR_GATE = 2,       // 1 when a rebuild is due (read by the gated rebuild kernels)
   SCR_TICKET2 = 3,    // spare ticket
   SCR_WORDS = 64
@@ -140,7 +141,9 @@ struct KArgs {
   int32_t* jedge;        // by-partner index entries [max_pairs]
   double* trace;
   uint32_t* scr_words;   // SCR_WORDS control words
-  double* block_partials;  // [max_blocks][8] FP64 partial sums of the integrate kernels
+  unsigned long long* acc_slots;  // step accumulators, spread over kAccSlots slots against contention:
+                                  // [4][kAccSlots] energy sums (K_trans, K_rot, U, W; 64-bit fixed point,
+                                  // 2^-32 units), then uint32 [kAccSlots] largest squared displacement
   int32_t* cell_of;      // [n] cell id per slot (build)
   int32_t* rank;         // [n] rank within cell (build)
   int32_t* perm;         // [n] new slot -> old slot
@@ -148,7 +151,6 @@ struct KArgs {
   int64_t* block_sums;   // scan block totals
   double4_32a* tmp_d4;       // [4][n] gather buffers
   int32_t* tmp_i;        // [n]
-  int32_t partial_capacity;
 };
 
 // Host-side helpers implemented in md_api.cu
@@ -171,8 +173,10 @@ cudaError_t launch_forces(const KArgs& a, int path, int block, cudaStream_t st);
 cudaError_t launch_integrate(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle,
                              cudaStream_t st);
 // The fused force + integrate step (MIDDLE phase) of the isotropic mixed vertex path: reads pos/fxp,
-// writes the drifted state to pos_alt/fxp_alt; the last block makes the step decision.
+// writes the drifted state to pos_alt/fxp_alt; then the one-warp step decision.
 cudaError_t launch_step_fused(const KArgs& a, int block, int use_cond, unsigned long long cond_handle, cudaStream_t st);
+// The step decision as a one-warp kernel (after the fused step kernel).
+cudaError_t launch_decide(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle, cudaStream_t st);
 cudaError_t launch_get_forces(const KArgs& a, double* fout, double* tout, cudaStream_t st);
 cudaError_t launch_init_ws(const KArgs& a, cudaStream_t st);
 int integrate_blocks(const KArgs& a);
