@@ -42,6 +42,7 @@ __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i, bool newto
     }
     int half = 0;
     const size_t n = (size_t)a.n;
+    const int nx = a.ncell[0];
     for (int dz = lo[2]; dz <= hi[2]; dz++) {
       int z = ci[2] + dz;
       z += (z < 0) ? a.ncell[2] : 0;
@@ -50,13 +51,35 @@ __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i, bool newto
         int y = ci[1] + dy;
         y += (y < 0) ? a.ncell[1] : 0;
         y -= (y >= a.ncell[1]) ? a.ncell[1] : 0;
-        for (int dx = lo[0]; dx <= hi[0]; dx++) {
-          int x = ci[0] + dx;
-          x += (x < 0) ? a.ncell[0] : 0;
-          x -= (x >= a.ncell[0]) ? a.ncell[0] : 0;
-          int c = (z * a.ncell[1] + y) * a.ncell[0] + x;
-          if (a.cell_rank) c = a.cell_rank[c];
-          const int b = a.cell_start[c], e = a.cell_start[c + 1];
+        const int row = (z * a.ncell[1] + y) * nx;
+        // Row-major order: the cells x - reach .. x + reach of this row are consecutive cells (up to one
+        // periodic wrap) holding consecutive slots, so the walk is one or two slot ranges, taken in the
+        // order of dx: the same candidates in the same order as cell by cell, with less loop overhead
+        // and less divergence between the lanes of a warp.  Hilbert order: cell by cell.
+        const int xl = ci[0] + lo[0], xh = ci[0] + hi[0];
+        const int nseg = a.cell_rank ? hi[0] - lo[0] + 1 : (xl < 0 || xh >= nx ? 2 : 1);
+        for (int g = 0; g < nseg; g++) {
+          int b, e;
+          if (a.cell_rank) {
+            int x = xl + g;
+            x += (x < 0) ? nx : 0;
+            x -= (x >= nx) ? nx : 0;
+            const int c = a.cell_rank[row + x];
+            b = a.cell_start[c];
+            e = a.cell_start[c + 1];
+          } else {
+            const int* cs = a.cell_start + row;
+            if (xl < 0) {
+              b = g == 0 ? cs[xl + nx] : cs[0];
+              e = g == 0 ? cs[nx] : cs[xh + 1];
+            } else if (xh >= nx) {
+              b = g == 0 ? cs[xl] : cs[0];
+              e = g == 0 ? cs[nx] : cs[xh - nx + 1];
+            } else {
+              b = cs[xl];
+              e = cs[xh + 1];
+            }
+          }
           for (int j = b; j < e; j++) {
             if (j == i) continue;
             bool in = verlet_candidate_in(a, si, a.fxp[j], i, j);
