@@ -362,13 +362,16 @@ int md_time_step_kernel(const md_params* p, md_state* s, void* ws, int32_t path,
 /*
  * md_autotune_system -- picks the fastest decomposition for this system on this GPU (generalising the
  * paper's conclusion that the better path depends on the model and the density into a measurement):
- * bins the particles, then for each candidate builds its lists and times five force evaluations
- * (median, CUDA events on `stream`; the call synchronises).  The MD_TUNE_CANDIDATES candidates, in
+ * bins the particles, then for each candidate builds its lists and times what md_step_verlet runs per
+ * step for it, rebuilds aside (median of five, CUDA events on `stream`; the call synchronises): the
+ * fused force + integrate kernel and its decision kernel where fuse_step applies to the candidate,
+ * else its force kernel plus the integrate kernel.  Velocities, positions (and orientations) and the
+ * step words changed by the timed launches are put back.  The MD_TUNE_CANDIDATES candidates, in
  * order: vertex with 1, 2, 4 and 8 threads per particle, each at block sizes 64, 128 and 256; edge at
  * 128 and 256; MD_VERTEX_NEWTON at 128 (when force_copies >= 1); MD_EDGE_STORE at 256 (when
  * edge_store = 1).  Writes the winner to *path_out, p->threads_per_particle and p->block_size, leaves
- * lists and forces prepared for it, and, if ms_out is not NULL, the median times in milliseconds
- * (-1: candidate not available).
+ * lists and forces prepared for it, and, if ms_out is not NULL, the median per-step times in
+ * milliseconds (-1: candidate not available).
  */
 #define MD_TUNE_CANDIDATES 16
 int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, float* ms_out, void* stream);

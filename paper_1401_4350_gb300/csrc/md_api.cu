@@ -614,6 +614,96 @@ static int get_graphs(const md_params* p, const md_state* s, const void* ws, int
   return MD_OK;
 }
 
+// What a timed launch changes and a measurement must put back: the status, energy, trace and decision
+// words and the step accumulators (kept on the host), the velocities (kept in the cell-sort scratch)
+// and, when positions = true, the positions and, patchy, the orientations and angular momenta too
+// (scratch as well; the fixed-point coordinates and patch sites are then derived from them again).
+struct StateKeeper {
+  const md_params* p;
+  const KArgs* a;
+  char* w;
+  cudaStream_t st;
+  bool positions;
+  size_t off[5], len[5];
+  std::vector<char> keep;
+
+  StateKeeper(const md_params* p_, const KArgs* a_, void* ws, const Layout& L, cudaStream_t st_, bool pos_)
+      : p(p_), a(a_), w((char*)ws), st(st_), positions(pos_) {
+    const size_t o[5] = {L.pub.status, L.pub.energy, L.pub.trace, L.scr_words, L.acc_slots};
+    const size_t n[5] = {sizeof(int32_t) * MD_STATUS_WORDS, sizeof(double) * MD_ENERGY_WORDS,
+                         sizeof(double) * 4 * (size_t)p->trace_capacity, sizeof(uint32_t) * SCR_WORDS,
+                         sizeof(unsigned long long) * 4 * kAccSlots + sizeof(uint32_t) * kAccSlots};
+    size_t total = 0;
+    for (int k = 0; k < 5; k++) {
+      off[k] = o[k];
+      len[k] = n[k];
+      total += n[k];
+    }
+    keep.resize(total);
+  }
+  // the scratch holds 2n double4 (4n for patchy): velocities, positions, orientations, angular momenta
+  cudaError_t copies(bool back) {
+    const size_t n = (size_t)p->n, nb = 32 * n;
+    double4_32a* arr[4] = {a->vel, a->pos, a->quat, a->angmom};
+    const int m = positions ? (is_patchy(p->model) ? 4 : 2) : 1;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < m && e == cudaSuccess; k++)
+      e = back ? cudaMemcpyAsync(arr[k], a->tmp_d4 + k * n, nb, cudaMemcpyDeviceToDevice, st)
+               : cudaMemcpyAsync(a->tmp_d4 + k * n, arr[k], nb, cudaMemcpyDeviceToDevice, st);
+    return e;
+  }
+  cudaError_t save() {
+    cudaError_t e = cudaSuccess;
+    size_t o = 0;
+    for (int k = 0; k < 5 && e == cudaSuccess; o += len[k], k++)
+      if (len[k]) e = cudaMemcpyAsync(keep.data() + o, w + off[k], len[k], cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = copies(false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  }
+  cudaError_t restore() {
+    cudaError_t e = cudaSuccess;
+    size_t o = 0;
+    for (int k = 0; k < 5 && e == cudaSuccess; o += len[k], k++)
+      if (len[k]) e = cudaMemcpyAsync(w + off[k], keep.data() + o, len[k], cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = copies(true);
+    if (e == cudaSuccess && positions) e = launch_integrate(*a, 4, 0, 0ULL, st);  // derived coordinates again
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  }
+};
+
+// Median (or mean) CUDA-event time of `reps` calls of `launch` after `warm` untimed ones.
+template <class F>
+static cudaError_t time_launches(F launch, int warm, int reps, bool median, cudaStream_t st, float* ms_out) {
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  for (int r = 0; r < warm && e == cudaSuccess; r++) e = launch();
+  for (int r = 0; r < reps && e == cudaSuccess; r++) {
+    e = cudaEventRecord(ev[2 * r], st);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  std::vector<float> t((size_t)reps, 0.f);
+  for (int r = 0; r < reps && e == cudaSuccess; r++) e = cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]);
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e == cudaSuccess) {
+    if (median) {
+      std::sort(t.begin(), t.end());
+      *ms_out = t[(size_t)reps / 2];
+    } else {
+      double sum = 0.0;
+      for (float x : t) sum += x;
+      *ms_out = (float)(sum / reps);
+    }
+  }
+  return e;
+}
+
 }  // namespace mdgb
 
 using namespace mdgb;
@@ -816,52 +906,17 @@ int md_time_step_kernel(const md_params* p, md_state* s, void* ws, int32_t path,
   KArgs a = make_args(p, s, ws, L);
   cudaStream_t st = (cudaStream_t)stream;
   const bool fused = fused_step(p, path);
-  char* w = (char*)ws;
-  // what a launch changes besides the force arrays: status, energy, trace and decision words and the
-  // energy accumulators (kept on the host), and, fused, the velocities (kept in the cell-sort scratch)
-  const size_t off[5] = {L.pub.status, L.pub.energy, L.pub.trace, L.scr_words, L.acc_slots};
-  const size_t len[5] = {sizeof(int32_t) * MD_STATUS_WORDS, sizeof(double) * MD_ENERGY_WORDS,
-                         sizeof(double) * 4 * (size_t)p->trace_capacity, sizeof(uint32_t) * SCR_WORDS,
-                         sizeof(unsigned long long) * 4 * kAccSlots + sizeof(uint32_t) * kAccSlots};
-  size_t total = 0;
-  for (int k = 0; k < 5; k++) total += len[k];
-  std::vector<char> keep(total);
-  cudaError_t e = cudaSuccess;
-  for (int k = 0, o = 0; k < 5 && e == cudaSuccess; o += (int)len[k], k++)
-    if (len[k]) e = cudaMemcpyAsync(keep.data() + o, w + off[k], len[k], cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && fused) e = cudaMemcpyAsync(a.tmp_d4, a.vel, 32 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  StateKeeper keeper(p, &a, ws, L, st, false);
+  cudaError_t e = keeper.save();
   if (e != cudaSuccess) return cuda_fail(e, "md_time_step_kernel (save)");
-  auto launch = [&]() {
-    return fused ? launch_step_fused(a, p->block_size, 0, 0ULL, st) : launch_forces(a, path, p->block_size, st);
-  };
-  std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
-  for (auto& x : ev)
-    if (e == cudaSuccess) e = cudaEventCreate(&x);
-  if (e == cudaSuccess) e = launch();  // warm-up
-  for (int r = 0; r < reps && e == cudaSuccess; r++) {
-    e = cudaEventRecord(ev[2 * r], st);
-    if (e == cudaSuccess) e = launch();
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], st);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  double sum = 0.0;
-  for (int r = 0; r < reps && e == cudaSuccess; r++) {
-    float ms = 0.f;
-    e = cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
-    sum += ms;
-  }
-  for (auto& x : ev)
-    if (x) cudaEventDestroy(x);
-  // restore, whatever happened above
-  cudaError_t er = cudaSuccess;
-  for (int k = 0, o = 0; k < 5 && er == cudaSuccess; o += (int)len[k], k++)
-    if (len[k]) er = cudaMemcpyAsync(w + off[k], keep.data() + o, len[k], cudaMemcpyHostToDevice, st);
-  if (er == cudaSuccess && fused) er = cudaMemcpyAsync(a.vel, a.tmp_d4, 32 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
-  if (er == cudaSuccess) er = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  e = time_launches([&]() { return fused ? launch_step_fused(a, p->block_size, 0, 0ULL, st)
+                                         : launch_forces(a, path, p->block_size, st); },
+                    1, reps, false, st, &ms);
+  const cudaError_t er = keeper.restore();  // whatever happened above
   if (e != cudaSuccess) return cuda_fail(e, "md_time_step_kernel");
   if (er != cudaSuccess) return cuda_fail(er, "md_time_step_kernel (restore)");
-  *ms_out = (float)(sum / reps);
+  *ms_out = ms;
   return MD_OK;
 }
 
@@ -875,10 +930,14 @@ int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, f
   make_layout(p, &L);
   KArgs a = make_args(p, s, ws, L);
   cudaError_t e = launch_build_cells(a, nullptr, st);
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
-  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-  float best = 3.0e38f;
+  // Each candidate is scored by what md_step_verlet runs per step for it (rebuilds aside): the fused
+  // force + integrate kernel and its decision kernel where fuse_step applies to the candidate, else its
+  // force kernel plus the separate integrate kernel (timed once, on the first such candidate's lists).
+  // The timed launches change velocities (and, for the integrate kernel, positions) and the step words:
+  // those are put back after each timing.
+  StateKeeper keeper(p, &a, ws, L, st, true);
+  if (e == cudaSuccess) e = keeper.save();
+  float best = 3.0e38f, integ_ms = -1.0f;
   int best_k = 0;
   int built_for = -1;  // list kind currently built
   for (int k = 0; k < MD_TUNE_CANDIDATES && e == cudaSuccess; k++) {
@@ -895,18 +954,19 @@ int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, f
         e = launch_build_verlet(b, list_kind(path), nullptr, st);
         built_for = list_kind(path);
       }
-      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_forces(b, path, q.block_size, st);
-      float reps[5];
-      for (int r = 0; r < 5 && e == cudaSuccess; r++) {
-        e = cudaEventRecord(ev[0], st);
-        if (e == cudaSuccess) e = launch_forces(b, path, q.block_size, st);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&reps[r], ev[0], ev[1]);
+      const bool fused = fused_step(&q, path);
+      float t = 0.f;
+      if (e == cudaSuccess)
+        e = time_launches([&]() { return fused ? launch_step_fused(b, q.block_size, 0, 0ULL, st)
+                                               : launch_forces(b, path, q.block_size, st); },
+                          2, 5, true, st, &t);
+      if (e == cudaSuccess && fused) e = keeper.restore();
+      if (e == cudaSuccess && !fused && integ_ms < 0.0f) {
+        e = time_launches([&]() { return launch_integrate(b, 1, 0, 0ULL, st); }, 2, 5, true, st, &integ_ms);
+        if (e == cudaSuccess) e = keeper.restore();
       }
       if (e == cudaSuccess) {
-        std::sort(reps, reps + 5);
-        ms = reps[2];
+        ms = fused ? t : t + integ_ms;
         if (ms < best) { best = ms; best_k = k; }
       }
     }
@@ -922,8 +982,6 @@ int md_autotune_system(md_params* p, md_state* s, void* ws, int32_t* path_out, f
     if (e == cudaSuccess) e = launch_integrate(b, 3, 0, 0ULL, st);  // energies, as md_prepare
     *path_out = md_tune_path[best_k];
   }
-  for (int k = 0; k < 2; k++)
-    if (ev[k]) cudaEventDestroy(ev[k]);
   return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_autotune_system");
 }
 

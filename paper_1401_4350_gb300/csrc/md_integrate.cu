@@ -17,7 +17,7 @@
 namespace mdgb {
 
 // The integrate phase and, in the last block to finish, the step decision (one launch per phase).
-__global__ void __launch_bounds__(kIntBlock) k_integrate(KArgs a, int mode, int use_cond, unsigned long long cond_handle) {
+__global__ void __launch_bounds__(kIntBlock, 4) k_integrate(KArgs a, int mode, int use_cond, unsigned long long cond_handle) {
   integrate_body(a, mode, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
   integrate_epilogue(a, mode, use_cond, cond_handle);
 }

@@ -209,7 +209,11 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
   float disp2 = 0.f;
   uint32_t tstep = 0;
   const bool thermo = thermostat_step(a, mode, tstep);
-  if (valid) {
+  if (!FUSED && mode == 4 && valid) {  // derived arrays only: fixed-point coordinates (and patch sites)
+    a.fxp[i] = fixed3(a.pos[i], a);
+    if (patchy) write_patch_lab(a, i, a.quat[i]);
+  }
+  if (valid && mode != 4) {
     double4_32a v = a.vel[i];
     const double4_32a F = FUSED ? Fin : a.force[i];
     double vn[3], ln[3];

@@ -136,7 +136,15 @@ def test_autotune_system_times_every_path_and_prepares_the_winner(name):
     s = get_sys(name)
     Fr, Tr, Er, _ = ref_forces(s, name)
     sim = Sim(s, B.MD_MIXED, force_copies=4, edge_store=1)
+    x0, v0 = sim.positions()
+    q0 = sim.orientations() if s.quat is not None else None
     path, tpp, block, ms = sim.autotune()
+    # the timed launches moved nothing: every candidate's changes were put back
+    x1, v1 = sim.positions()
+    assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
+    if q0 is not None:
+        q1 = sim.orientations()
+        assert np.array_equal(q0[0], q1[0]) and np.array_equal(q0[1], q1[1])
     assert all(t > 0 for t in ms), ms
     assert (path, tpp, block) == B.TUNE_CANDIDATES[int(np.argmin(ms))]
     assert (sim.params.threads_per_particle, sim.params.block_size) == (tpp, block)
