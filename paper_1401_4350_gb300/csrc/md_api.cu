@@ -237,12 +237,14 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     a.fxp_unit[c] = f32(a.fxp_unit_d[c]);
   }
   a.ncell_total = L.pub.ncell[0] * L.pub.ncell[1] * L.pub.ncell[2];
+  for (int c = 0; c < 3; c++) a.cell_edge_f[c] = f32(p->box[c] / L.pub.ncell[c]);
   const double rv = p->rc + p->skin;
   a.rc2_d = p->rc * p->rc;
   a.rc2_f = f32(a.rc2_d);
   a.rv2_d = rv * rv;
   a.rv2_lo = f32(a.rv2_d * (1.0 - 1e-5));
   a.rv2_hi = f32(a.rv2_d * (1.0 + 1e-5));
+  a.rv2_pad_f = f32(a.rv2_d * (1.0 + 2e-4));
   {
     // integer separations differ from the FP64 ones by at most one unit per axis (two roundings of
     // half a unit), so |r_u^2 - (r/u)^2| <= 2 sqrt(3) r/u + 3: a relative band of 4 / (rv/u) (+1e-9)

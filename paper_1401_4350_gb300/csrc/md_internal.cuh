@@ -65,6 +65,8 @@ struct KArgs {
   double rc2_d, rv2_d;
   float rc2_f;
   float rv2_lo, rv2_hi;  // FP32 filter band of the Verlet build
+  float cell_edge_f[3];  // cell edge per axis (box / ncell)
+  float rv2_pad_f;       // (rv (1 + 1e-4))^2: rows and cells farther than rv from a particle are skipped
   // cubic boxes: the same decision on the exact integer r^2 of the fixed-point separation, with the
   // band around rv^2 only as wide as the fixed-point rounding of the positions can move r^2
   unsigned long long rv2_lo_u, rv2_hi_u;

@@ -43,21 +43,48 @@ __device__ __forceinline__ int verlet_full_one(const KArgs& a, int i, bool newto
     int half = 0;
     const size_t n = (size_t)a.n;
     const int nx = a.ncell[0];
+    // The particle's offset inside its cell along each axis (the low bits of s * ncell / 2^32), and the
+    // distance from it to a neighbouring row of cells: rows and, along x, cells beyond rv (padded by
+    // 1e-4 against FP32 rounding) hold no neighbour and are skipped.  The remaining candidates are
+    // those of the full stencil in the same order, so the lists do not change; at half-size cells this
+    // visits about 10.5 rv^3 of cells per particle instead of 15.6 rv^3.
+    float u[3];
+    {
+      const uint32_t sc[3] = {si.x, si.y, si.z};
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+        u[c] = (float)(uint32_t)((unsigned long long)sc[c] * (unsigned long long)a.ncell[c]) * 2.3283064365386963e-10f *
+               a.cell_edge_f[c];
+    }
+    auto row_gap = [&](int c, int d) {  // distance along axis c from the particle to cell offset d
+      return d > 0 ? (float)d * a.cell_edge_f[c] - u[c] : d < 0 ? u[c] - (float)(d + 1) * a.cell_edge_f[c] : 0.f;
+    };
     for (int dz = lo[2]; dz <= hi[2]; dz++) {
       int z = ci[2] + dz;
       z += (z < 0) ? a.ncell[2] : 0;
       z -= (z >= a.ncell[2]) ? a.ncell[2] : 0;
+      const float gz = a.ncell[2] > 1 ? row_gap(2, dz) : 0.f;
       for (int dy = lo[1]; dy <= hi[1]; dy++) {
         int y = ci[1] + dy;
         y += (y < 0) ? a.ncell[1] : 0;
         y -= (y >= a.ncell[1]) ? a.ncell[1] : 0;
         const int row = (z * a.ncell[1] + y) * nx;
-        // Row-major order: the cells x - reach .. x + reach of this row are consecutive cells (up to one
+        const float gy = a.ncell[1] > 1 ? row_gap(1, dy) : 0.f;
+        const float h2 = a.rv2_pad_f - gy * gy - gz * gz;
+        if (h2 < 0.f) continue;  // the whole row is beyond rv
+        // cells along x within rv of the particle (a one-cell axis keeps its single cell)
+        int dxl = lo[0], dxh = hi[0];
+        if (nx > 1) {
+          const float h = sqrtf(h2), inv = 1.0f / a.cell_edge_f[0];
+          dxl = max(dxl, (int)floorf((u[0] - h) * inv));
+          dxh = min(dxh, (int)floorf((u[0] + h) * inv));
+        }
+        // Row-major order: the cells x + dxl .. x + dxh of this row are consecutive cells (up to one
         // periodic wrap) holding consecutive slots, so the walk is one or two slot ranges, taken in the
         // order of dx: the same candidates in the same order as cell by cell, with less loop overhead
         // and less divergence between the lanes of a warp.  Hilbert order: cell by cell.
-        const int xl = ci[0] + lo[0], xh = ci[0] + hi[0];
-        const int nseg = a.cell_rank ? hi[0] - lo[0] + 1 : (xl < 0 || xh >= nx ? 2 : 1);
+        const int xl = ci[0] + dxl, xh = ci[0] + dxh;
+        const int nseg = a.cell_rank ? dxh - dxl + 1 : (xl < 0 || xh >= nx ? 2 : 1);
         for (int g = 0; g < nseg; g++) {
           int b, e;
           if (a.cell_rank) {
