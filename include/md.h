@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 3
+#define MD_ABI_VERSION 4
 
 /* Return / status codes. */
 enum {
@@ -107,6 +107,7 @@ enum {
   MD_STATUS_REBUILDS = 4,      /* number of cell + Verlet rebuilds done by md_step_verlet  */
   MD_STATUS_STEPS = 5,         /* number of steps done by md_step_verlet                   */
   MD_STATUS_LISTS = 6,         /* MD_LIST_* bits of the lists built by the last md_build_verlet */
+  MD_STATUS_PRUNES = 7,        /* number of inner-list prunes done by fused steps (prune_skin > 0) */
   MD_STATUS_WORDS = 16
 };
 
@@ -168,6 +169,13 @@ typedef struct md_params {
                                     dynamics, NVT).  Random numbers: Philox4x32-10 with counter
                                     (s, original id, stream 0/1, 0) and key (seed, 0), Box-Muller.  */
   uint32_t seed;                 /* key of the thermostat's random numbers                       */
+  double prune_skin;             /* 0: off.  0 < prune_skin < skin, with fused steps (fuse_step = 1,
+                                    one thread per particle, cubic box): the fused kernel walks an
+                                    inner list of the Verlet-list pairs closer than rc + prune_skin,
+                                    pruned from the Verlet list by the fused kernel itself after every
+                                    rebuild and whenever a particle has moved more than prune_skin / 2
+                                    since the last prune; the results are those of the full list up
+                                    to the order of the FP32 sums                                   */
 } md_params;
 
 /* Primary state: FP64 device arrays owned by the caller, [n][4] each. */
@@ -222,6 +230,9 @@ typedef struct md_ws_layout {
   size_t pos_alt;        /* fuse_step = 1: double[n][4] second position buffer (the fused kernel
                             reads one buffer and writes the other); empty otherwise               */
   size_t fxp_alt;        /* fuse_step = 1: uint32[n][4] second fixed-point buffer; empty otherwise */
+  size_t nbr_in;         /* prune_skin > 0 with fused steps: the inner list, laid out as nbr      */
+  size_t nbr_in_count;   /* int32[n]: inner-list length per slot                                */
+  size_t fxp_prune;      /* uint32[n][4]: fixed-point coordinates at the last prune              */
   size_t scratch;        /* internal scratch                                                  */
 } md_ws_layout;
 

@@ -27,7 +27,7 @@ MD_LIST_FULL_LOCAL, MD_LOCAL_BLOCK, MD_LOCAL_MAX_CELLS = 8, 256, 512
 MD_FORMAT_GLOBAL, MD_FORMAT_LOCAL = 0, 1
 MD_MAX_PATCH = 4
 MD_STATUS_CODE, MD_STATUS_NEED_NEIGH, MD_STATUS_NEED_PAIRS_LO, MD_STATUS_NEED_PAIRS_HI = 0, 1, 2, 3
-MD_STATUS_REBUILDS, MD_STATUS_STEPS, MD_STATUS_LISTS, MD_STATUS_WORDS = 4, 5, 6, 16
+MD_STATUS_REBUILDS, MD_STATUS_STEPS, MD_STATUS_LISTS, MD_STATUS_PRUNES, MD_STATUS_WORDS = 4, 5, 6, 7, 16
 MD_ENERGY_U, MD_ENERGY_KT, MD_ENERGY_KR, MD_ENERGY_W, MD_ENERGY_WORDS = 0, 1, 2, 3, 8
 
 
@@ -44,7 +44,7 @@ class md_params(ctypes.Structure):
                 ("eps_p", ctypes.c_double), ("delta", ctypes.c_double),
                 ("patch", (ctypes.c_double * 3) * MD_MAX_PATCH), ("patch_rc", ctypes.c_double),
                 ("kT", ctypes.c_double), ("thermostat_prob", ctypes.c_double),
-                ("thermostat_every", ctypes.c_int32), ("seed", ctypes.c_uint32)]
+                ("thermostat_every", ctypes.c_int32), ("seed", ctypes.c_uint32), ("prune_skin", ctypes.c_double)]
 
 
 class md_state(ctypes.Structure):
@@ -57,7 +57,7 @@ class md_ws_layout(ctypes.Structure):
         (name, ctypes.c_size_t) for name in
         ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr", "nbr_count", "half_start",
          "pairs", "force", "virial", "torque", "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace",
-         "pos_alt", "fxp_alt", "scratch")]
+         "pos_alt", "fxp_alt", "nbr_in", "nbr_in_count", "fxp_prune", "scratch")]
 
 
 class MDError(RuntimeError):

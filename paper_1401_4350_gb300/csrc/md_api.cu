@@ -104,6 +104,10 @@ static int check(const md_params* p) {
     return MD_ERR_INVALID;
   }
   if (p->fuse_step != 0 && p->fuse_step != 1) { set_error("fuse_step must be 0 or 1"); return MD_ERR_INVALID; }
+  if (!(p->prune_skin >= 0.0) || (p->prune_skin > 0.0 && !(p->prune_skin < p->skin))) {
+    set_error("prune_skin must be 0 (off) or in (0, skin)");
+    return MD_ERR_INVALID;
+  }
   if (p->edge_store && p->max_pairs >= (int64_t)1 << 31) {
     set_error("edge_store needs max_pairs < 2^31 (32-bit positions in the by-partner index)");
     return MD_ERR_INVALID;
@@ -137,6 +141,14 @@ static bool local_list_eligible(const md_params* p) {
   const double rv = p->rc + p->skin;
   const double nbar = 4.18879020478639 * rv * rv * rv * (double)p->n / (p->box[0] * p->box[1] * p->box[2]);
   return nbar >= 16.0;
+}
+
+// Whether the workspace holds an inner list: prune_skin > 0 on the fused LJ/WCA mixed path in a cubic box
+// (the fused kernel uses it with one thread per particle; the layout does not depend on that choice).
+static bool inner_layout(const md_params* p) {
+  return p->prune_skin > 0.0 && p->fuse_step == 1 && p->precision == MD_MIXED &&
+         (p->model == MD_LJ || p->model == MD_WCA) && !local_list_eligible(p) && p->box[0] == p->box[1] &&
+         p->box[1] == p->box[2];
 }
 
 // Bytes of the per-edge store (0 unless edge_store): blocks A, B and, patchy, C of max_pairs entries.
@@ -197,9 +209,13 @@ static void make_layout(const md_params* p, Layout* L) {
   P.trace = take(sizeof(double) * 4 * (size_t)p->trace_capacity);
   P.pos_alt = take(p->fuse_step ? 32 * n : 0);
   P.fxp_alt = take(p->fuse_step ? 16 * n : 0);
+  const bool inner = inner_layout(p);
+  P.nbr_in = take(inner ? sizeof(int32_t) * 4 * n * (size_t)((p->max_neigh + 3) / 4) : 0);
+  P.nbr_in_count = take(inner ? sizeof(int32_t) * n : 0);
+  P.fxp_prune = take(inner ? 16 * n : 0);
   P.scratch = off;
   L->scr_words = take(sizeof(uint32_t) * SCR_WORDS);
-  L->acc_slots = take(sizeof(unsigned long long) * 4 * kAccSlots + sizeof(uint32_t) * kAccSlots);
+  L->acc_slots = take(sizeof(unsigned long long) * 4 * kAccSlots + 2 * sizeof(uint32_t) * kAccSlots);
   L->cell_of = take(sizeof(int32_t) * n);
   L->rank = take(sizeof(int32_t) * n);
   L->perm = take(sizeof(int32_t) * n);
@@ -287,6 +303,9 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     const double fscale = -24.0 * p->eps / (u * ldexp(1.0, S));
     a.fscale_hi = f32(fscale);
     a.fscale_lo = f32(fscale - (double)a.fscale_hi);
+    const double rin = p->rc + p->prune_skin;
+    a.rin2_s = f32(rin * rin * (1.0 + 1e-5) / unit2);
+    a.prune_thr2 = f32(0.25 * p->prune_skin * p->prune_skin * (1.0 - 1e-4));
   }
   const double sr2 = p->sigma * p->sigma / a.rwca2_d, sr6 = sr2 * sr2 * sr2;
   a.sig2_d = p->sigma * p->sigma;
@@ -361,6 +380,12 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.fxp_build = (uint4*)(w + L.pub.fxp_build);
   a.pos_alt = p->fuse_step ? (double4_32a*)(w + L.pub.pos_alt) : nullptr;
   a.fxp_alt = p->fuse_step ? (uint4*)(w + L.pub.fxp_alt) : nullptr;
+  if (inner_layout(p)) {
+    a.inner = p->threads_per_particle == 1 ? 1 : 0;
+    a.nbr_in = (int32_t*)(w + L.pub.nbr_in);
+    a.nbr_in_count = (int32_t*)(w + L.pub.nbr_in_count);
+    a.fxp_prune = (uint4*)(w + L.pub.fxp_prune);
+  }
   a.patch_lab = (void*)(w + L.pub.patch_lab);
   a.nbr = (int32_t*)(w + L.pub.nbr);
   a.nbr_count = (int32_t*)(w + L.pub.nbr_count);
@@ -398,7 +423,8 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   make_layout(p, &L);
   KArgs a = make_args(p, s, nullptr, L);
   a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
-  a.pos_alt = nullptr; a.fxp_alt = nullptr;
+  a.pos_alt = nullptr; a.fxp_alt = nullptr; a.inner = 0; a.nbr_in = nullptr; a.nbr_in_count = nullptr;
+  a.fxp_prune = nullptr;
   a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
   a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
   a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr; a.local_ok = 0; a.local_tab = nullptr;
@@ -634,7 +660,7 @@ struct StateKeeper {
     const size_t o[5] = {L.pub.status, L.pub.energy, L.pub.trace, L.scr_words, L.acc_slots};
     const size_t n[5] = {sizeof(int32_t) * MD_STATUS_WORDS, sizeof(double) * MD_ENERGY_WORDS,
                          sizeof(double) * 4 * (size_t)p->trace_capacity, sizeof(uint32_t) * SCR_WORDS,
-                         sizeof(unsigned long long) * 4 * kAccSlots + sizeof(uint32_t) * kAccSlots};
+                         sizeof(unsigned long long) * 4 * kAccSlots + 2 * sizeof(uint32_t) * kAccSlots};
     size_t total = 0;
     for (int k = 0; k < 5; k++) {
       off[k] = o[k];

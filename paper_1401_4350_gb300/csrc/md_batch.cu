@@ -99,7 +99,7 @@ __global__ void k_b_init(BatchDev b) {
   if (t < MD_STATUS_WORDS) ka.status[t] = 0;
   if (t < MD_ENERGY_WORDS) ka.energy[t] = 0.0;
   if (t < SCR_WORDS) ka.scr_words[t] = 0u;
-  for (int k = t; k < 9 * kAccSlots; k += blockDim.x) ((uint32_t*)ka.acc_slots)[k] = 0u;  // step accumulators
+  for (int k = t; k < 10 * kAccSlots; k += blockDim.x) ((uint32_t*)ka.acc_slots)[k] = 0u;  // step accumulators
   for (int k = t; k < ka.trace_capacity * 4; k += blockDim.x) ka.trace[k] = 0.0;
   for (int k = t; k < ka.n; k += blockDim.x) ka.nbr_count[k] = 0;
   for (int k = t; k <= ka.n; k += blockDim.x) ka.half_start[k] = 0;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_b_decide(BatchDev b, int mode, int use_
   const int r = blockIdx.x;
   load_kargs(ka, b.table + r);
   __syncthreads();
-  step_decide_body(ka, mode, (ka.n + kBChunk - 1) / kBChunk, 0, 0ULL);
+  step_decide_body(ka, mode, false, 0, 0ULL);
   const bool drift = (mode == 0 || mode == 1);
   if (threadIdx.x == 0) {
     b.flags[r] = drift ? (int)ka.scr_words[SCR_GATE] : 0;

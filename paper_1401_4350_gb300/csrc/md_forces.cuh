@@ -542,15 +542,67 @@ struct IsoAcc {
 // Where the entries of a row and the coordinates they name come from.
 // Global format: int32 slots, groups of four per int4; coordinates gathered from fxp.
 struct GlobalRows {
-  const int4* nb4;
+  const int4* nb4;      // this slot's first group
+  const int32_t* list;  // the row storage (the Verlet list nbr, or the inner list nbr_in)
+  const int32_t* cnt;   // its lengths
   unsigned jmax;
+  __device__ __forceinline__ int count(const KArgs& a, int i) const { return min(__ldg(cnt + i), a.max_neigh); }
   __device__ __forceinline__ int4 group(int g, int ng, size_t n) const { return load_group(nb4, g, ng, n); }
   __device__ __forceinline__ void prefetch(int g, size_t n) const { prefetch_l2(nb4 + (size_t)g * n); }
   // an index can only be out of range in a list that was never built: clamp, never fault
   __device__ __forceinline__ uint4 coords(const KArgs& a, unsigned v) const { return __ldg(a.fxp + min(v, jmax)); }
   __device__ __forceinline__ unsigned slot(const KArgs&, unsigned v) const { return min(v, jmax); }
-  __device__ __forceinline__ unsigned entry(const KArgs& a, int k, int i, size_t n) const {
-    return (unsigned)__ldg((const int*)a.nbr + nbr_index(k, i, n));
+  __device__ __forceinline__ unsigned entry(const KArgs&, int k, int i, size_t n) const {
+    return (unsigned)__ldg(list + nbr_index(k, i, n));
+  }
+};
+
+// The rows of the Verlet list (or, inner = true, of the inner list) of slot min(i, n - 1).
+__device__ __forceinline__ GlobalRows global_rows(const KArgs& a, int i, bool inner) {
+  GlobalRows R;
+  R.list = inner ? a.nbr_in : a.nbr;
+  R.cnt = inner ? a.nbr_in_count : a.nbr_count;
+  R.nb4 = (const int4*)R.list + min(i, a.n - 1);
+  R.jmax = (unsigned)a.n - 1u;
+  return R;
+}
+
+// Where the kept entries of a walk go: nowhere (NoPrune), or, when the fused step prunes, into the
+// slot's inner-list row (the entries closer than rc + prune_skin, in walk order, four per int4 group).
+struct NoPrune {
+  static constexpr bool kPrune = false;
+  __device__ __forceinline__ void take(const int4&, unsigned) {}
+  __device__ __forceinline__ void finish(const KArgs&, int, const uint4&) {}
+};
+
+struct InnerPrune {
+  static constexpr bool kPrune = true;
+  int4* out;  // the slot's first group in nbr_in (group g at out[g * n])
+  size_t n;
+  int written, nb;
+  int b0, b1, b2, b3;
+  __device__ __forceinline__ void push(int j) {
+    b0 = nb == 0 ? j : b0;
+    b1 = nb == 1 ? j : b1;
+    b2 = nb == 2 ? j : b2;
+    b3 = nb == 3 ? j : b3;
+    if (++nb == 4) {
+      out[(size_t)(written >> 2) * n] = make_int4(b0, b1, b2, b3);
+      written += 4;
+      nb = 0;
+    }
+  }
+  __device__ __forceinline__ void take(const int4& cur, unsigned keep) {
+    if (keep & 1u) push(cur.x);
+    if (keep & 2u) push(cur.y);
+    if (keep & 4u) push(cur.z);
+    if (keep & 8u) push(cur.w);
+  }
+  // the row is never longer than the Verlet-list row it comes from, so it fits the same capacity
+  __device__ __forceinline__ void finish(const KArgs& a, int i, const uint4& si) {
+    if (nb) out[(size_t)(written >> 2) * n] = make_int4(b0, b1, b2, b3);
+    a.nbr_in_count[i] = written + nb;
+    a.fxp_prune[i] = si;
   }
 };
 
@@ -568,6 +620,7 @@ struct LocalRows {
     return make_int4((int)(w.x & 0xffffu), (int)(w.x >> 16), (int)(w.y & 0xffffu), (int)(w.y >> 16));
   }
   __device__ __forceinline__ void prefetch(int g, size_t n) const { prefetch_l2(nb2 + (size_t)g * n); }
+  __device__ __forceinline__ int count(const KArgs& a, int i) const { return min(__ldg(a.nbr_count + i), a.max_neigh); }
   __device__ __forceinline__ unsigned slot(const KArgs&, unsigned v) const {
     v = min(v, (unsigned)max(H - 1, 0));
     int lo = 0, hi = U - 1;  // last cell whose offset is <= v
@@ -586,9 +639,10 @@ struct LocalRows {
   }
 };
 
-template <bool LIVE, class Rows>
+// keep (PRUNE): the entries of the group closer than rc + prune_skin, as bits 0..3.
+template <bool LIVE, class Rows, bool PRUNE = false>
 __device__ __forceinline__ void iso_group(const KArgs& a, const uint4& si, const int4& cur, int lim, const Rows& R,
-                                          IsoAcc& A) {
+                                          IsoAcc& A, unsigned* keep = nullptr) {
   uint4 sj[4];
   sj[0] = R.coords(a, (unsigned)cur.x);
   sj[1] = R.coords(a, (unsigned)cur.y);
@@ -602,6 +656,12 @@ __device__ __forceinline__ void iso_group(const KArgs& a, const uint4& si, const
     dx[u] = (float)ix;
     dy[u] = (float)iy;
     dz[u] = (float)iz;
+  }
+  if (PRUNE) {
+    unsigned k = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; u++) k |= ((!LIVE || u < lim) && r2[u] < a.rin2_s) ? (1u << u) : 0u;
+    *keep = k;
   }
   const float2 thr2 = make_float2(-a.rwca2_s, -a.rwca2_s);
   float2 gx, gy, gz;
@@ -663,8 +723,9 @@ __device__ __forceinline__ void store_iso(const KArgs& a, int gt, int tpp, const
   }
 }
 
-template <int TPP, class Rows>
-__device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R, IsoResult& res) {
+template <int TPP, class Rows, class Sink = NoPrune>
+__device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R, IsoResult& res,
+                                                      Sink* sink = nullptr) {
   const int i = gt / TPP, l = gt % TPP;
   const bool valid = i < a.n;
   const size_t n = (size_t)a.n;
@@ -676,7 +737,7 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
   uint4 si = make_uint4(0u, 0u, 0u, 0u);
   if (valid) {
     si = __ldg(a.fxp + i);
-    cnt = min(__ldg(a.nbr_count + i), a.max_neigh);
+    cnt = R.count(a, i);
     const int ng = (cnt + 3) >> 2, nfull = cnt >> 2;
     int4 cur = R.group(l, ng, n);
     // the list streams from DRAM: groups further ahead are requested into L2 so that their loads
@@ -688,10 +749,17 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
     for (; g < nfull; g += TPP) {  // groups of four entries that are all in the list
       const int4 nxt = R.group(g + TPP, ng, n);
       if (g + kListPrefetch * TPP < ng) R.prefetch(g + kListPrefetch * TPP, n);
-      iso_group<false>(a, si, cur, 4, R, A);
+      unsigned keep = 0u;
+      iso_group<false, Rows, Sink::kPrune>(a, si, cur, 4, R, A, &keep);
+      if (Sink::kPrune) sink->take(cur, keep);
       cur = nxt;
     }
-    if (g < ng) iso_group<true>(a, si, cur, cnt - 4 * g, R, A);  // the partial last group
+    if (g < ng) {  // the partial last group
+      unsigned keep = 0u;
+      iso_group<true, Rows, Sink::kPrune>(a, si, cur, cnt - 4 * g, R, A, &keep);
+      if (Sink::kPrune) sink->take(cur, keep);
+    }
+    if (Sink::kPrune) sink->finish(a, i, si);
   }
   if (A.bmin <= a.rwca2_band_s) {
     // pairs near rc: take the side of the exact FP64 definition, re-walking this lane's entries
@@ -761,10 +829,26 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
 template <int TPP>
 __device__ __forceinline__ void vertex_iso_cubic_eval(const KArgs& a, int gt, IsoResult& res) {
   if (!full_list_current(a)) return;
-  GlobalRows R;
-  R.nb4 = (const int4*)a.nbr + min(gt / TPP, a.n - 1);
-  R.jmax = (unsigned)a.n - 1u;
+  const GlobalRows R = global_rows(a, gt / TPP, false);
   vertex_iso_cubic_rows<TPP>(a, gt, R, res);
+}
+
+// The fused step's walk with an inner list (one thread per particle, cubic box): the inner list, or,
+// when a prune is due, the Verlet list, writing the new inner list on the way.
+__device__ __forceinline__ void vertex_iso_inner_eval(const KArgs& a, int i, bool prune, IsoResult& res) {
+  if (!full_list_current(a)) return;
+  if (prune) {
+    const GlobalRows R = global_rows(a, i, false);
+    InnerPrune S;
+    S.out = (int4*)a.nbr_in + min(i, a.n - 1);
+    S.n = (size_t)a.n;
+    S.written = S.nb = 0;
+    S.b0 = S.b1 = S.b2 = S.b3 = 0;
+    vertex_iso_cubic_rows<1>(a, i, R, res, &S);
+  } else {
+    const GlobalRows R = global_rows(a, i, true);
+    vertex_iso_cubic_rows<1>(a, i, R, res);
+  }
 }
 
 // The block-local list: the block (MD_LOCAL_BLOCK threads, one per slot) first stages its halo's

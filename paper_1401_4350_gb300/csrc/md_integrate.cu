@@ -22,9 +22,9 @@ __global__ void __launch_bounds__(kIntBlock, 4) k_integrate(KArgs a, int mode, i
   integrate_epilogue(a, mode, use_cond, cond_handle);
 }
 
-// The step decision alone (one warp), after a launch that integrated without a ticket.
+// The step decision alone (one warp), after a fused step launch (which integrated without a ticket).
 __global__ void __launch_bounds__(32) k_step_decide(KArgs a, int mode, int use_cond, unsigned long long cond_handle) {
-  step_decide_body(a, mode, 0, use_cond, cond_handle);
+  step_decide_body(a, mode, true, use_cond, cond_handle);
 }
 
 cudaError_t launch_decide(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle, cudaStream_t st) {
@@ -63,7 +63,8 @@ __global__ void k_init_ws(KArgs a) {
   if (t < MD_STATUS_WORDS) a.status[t] = 0;
   if (t < MD_ENERGY_WORDS) a.energy[t] = 0.0;
   if (t < SCR_WORDS) a.scr_words[t] = 0u;
-  if (t < 9 * kAccSlots) ((uint32_t*)a.acc_slots)[t] = 0u;  // step accumulators ([4][kAccSlots] u64, [kAccSlots] u32)
+  if (t < 10 * kAccSlots) ((uint32_t*)a.acc_slots)[t] = 0u;  // step accumulators ([4][kAccSlots] u64, [2][kAccSlots] u32)
+  if (t == 0) a.scr_words[SCR_PRUNE] = 1u;  // no inner list yet
   for (int k = t; k < a.trace_capacity * 4; k += gridDim.x * blockDim.x) a.trace[k] = 0.0;
   // empty lists until the first build: force kernels called early see no pairs
   for (int k = t; k < a.n; k += gridDim.x * blockDim.x) a.nbr_count[k] = 0;

@@ -206,7 +206,7 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
   const bool mixed = a.precision == MD_MIXED;
   double kt = 0.0, kr = 0.0, u = 0.0, w = 0.0;  // per-particle energy terms (FP64 values)
   float ktf = 0.f, krf = 0.f;                    // mixed: kinetic terms in FP32
-  float disp2 = 0.f;
+  float disp2 = 0.f, disp2p = 0.f;  // squared displacement since the last build / the last prune
   uint32_t tstep = 0;
   const bool thermo = thermostat_step(a, mode, tstep);
   if (!FUSED && mode == 4 && valid) {  // derived arrays only: fixed-point coordinates (and patch sites)
@@ -319,6 +319,14 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
       const float dz = (float)(int)(f.z - b.z) * a.fxp_unit[2];
       disp2 = dx * dx + dy * dy + dz * dz;
       if (!(disp2 == disp2)) disp2 = 3.0e38f;  // NaN: force a rebuild (and the error is recorded)
+      if (a.inner) {
+        const uint4 q = a.fxp_prune[i];
+        const float px = (float)(int)(f.x - q.x) * a.fxp_unit[0];
+        const float py = (float)(int)(f.y - q.y) * a.fxp_unit[1];
+        const float pz = (float)(int)(f.z - q.z) * a.fxp_unit[2];
+        disp2p = px * px + py * py + pz * pz;
+        if (!(disp2p == disp2p)) disp2p = 3.0e38f;
+      }
     }
   }
   // ---- reductions into the step accumulators; the totals are formed by the step decision ----
@@ -330,6 +338,10 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
   if (drift) {
     const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
     if (lane == 0 && m) atomicMax(disp_slot(a, slot), m);
+    if (a.inner) {
+      const unsigned mp = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2p));
+      if (lane == 0 && mp) atomicMax(disp_slot(a, kAccSlots + slot), mp);
+    }
   }
   if (energies) {
     // totals in 64-bit fixed point (2^-32 units) in integer atomics: exact, and independent of the
@@ -379,17 +391,20 @@ __device__ __forceinline__ void integrate_body(const KArgs& a, int mode, int i, 
 // kernel after a fused step, or the batch's per-replica decide): the FP64 energy totals from the
 // fixed-point accumulators, the trace row, the step counter, and the rebuild decision (largest
 // displacement since the build against (skin/2)^2), which sets the gate word for the gated rebuild
-// kernels and, inside a graph, the IF node's condition.  The accumulators are cleared for the next step.
-__device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int nblocks, int use_cond,
+// kernels and, inside a graph, the IF node's condition.  With an inner list it also decides whether
+// the next fused step prunes it again: after a rebuild, while a prune is pending, or when a particle
+// has moved more than prune_skin/2 since the last prune (after_fused: the launch before this decision
+// was a fused step, which pruned if a prune was pending).  The accumulators are cleared for the next step.
+__device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, bool after_fused, int use_cond,
                                                  unsigned long long cond_handle) {
   if (threadIdx.x >= 32) return;
   const bool drift = (mode == 0 || mode == 1);
   const bool energies = energy_step(a, mode);
   const int lane = threadIdx.x;
-  (void)nblocks;
   // read and clear at L2, where the warps' atomics landed: one slot per lane
-  unsigned m = 0u;
+  unsigned m = 0u, mp = 0u;
   if (drift) m = __reduce_max_sync(0xffffffffu, atomicExch(disp_slot(a, lane), 0u));
+  if (drift && a.inner) mp = __reduce_max_sync(0xffffffffu, atomicExch(disp_slot(a, kAccSlots + lane), 0u));
   if (energies) {
     long long tot[4];
     for (int c = 0; c < 4; c++) tot[c] = warp_sum_i64((long long)atomicExch(energy_slot(a, c, lane), 0ULL));
@@ -415,6 +430,12 @@ __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, int n
       const unsigned g = __uint_as_float(m) > a.disp_thr2 ? 1u : 0u;
       a.scr_words[SCR_GATE] = g;
       a.status[MD_STATUS_REBUILDS] += (int)g;
+      if (a.inner) {
+        const bool pending = a.scr_words[SCR_PRUNE] != 0u;
+        const bool pruned = after_fused && pending;
+        if (pruned) a.status[MD_STATUS_PRUNES] += 1;
+        a.scr_words[SCR_PRUNE] = (g || (pending && !pruned) || __uint_as_float(mp) > a.prune_thr2) ? 1u : 0u;
+      }
       if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, g);
     }
   }
@@ -432,7 +453,7 @@ __device__ __forceinline__ void integrate_epilogue(const KArgs& a, int mode, int
   if (!last) return;
   __threadfence();
   if (threadIdx.x == 0) a.scr_words[SCR_TICKET] = 0u;
-  if (threadIdx.x < 32) step_decide_body(a, mode, gridDim.x, use_cond, cond_handle);
+  if (threadIdx.x < 32) step_decide_body(a, mode, false, use_cond, cond_handle);
 }
 
 }  // namespace mdgb

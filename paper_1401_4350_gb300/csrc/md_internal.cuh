@@ -30,7 +30,7 @@ constexpr int kAccSlots = 32;      // slots of the step accumulators (one warp r
 // Scratch words at the start of the scratch region (uint32 each).
 enum {
   SCR_TICKET = 0,     // last-block ticket of the integrate kernels
-  SCR_SPARE1 = 1,     // spare
+  SCR_PRUNE = 1,      // 1 when the inner list must be pruned again by the next fused step
   SCR_GATE = 2,       // 1 when a rebuild is due (read by the gated rebuild kernels)
   SCR_TICKET2 = 3,    // spare ticket
   SCR_WORDS = 64
@@ -66,6 +66,13 @@ struct KArgs {
   float rc2_f;
   float rv2_lo, rv2_hi;  // FP32 filter band of the Verlet build
   float cell_edge_f[3];  // cell edge per axis (box / ncell)
+  // inner list (prune_skin > 0 with fused steps, one thread per particle, cubic box)
+  int32_t inner;          // 1: the fused step walks nbr_in and prunes it from nbr when SCR_PRUNE is set
+  int32_t* nbr_in;        // the inner list, laid out as nbr
+  int32_t* nbr_in_count;
+  uint4* fxp_prune;       // fixed-point coordinates at the last prune
+  float rin2_s;           // (rc + prune_skin)^2 (1 + 1e-5) in the scaled r^2 units of the cubic path
+  float prune_thr2;       // (prune_skin / 2)^2 (1 - 1e-4): displacement that calls for a new prune
   float rv2_pad_f;       // (rv (1 + 1e-4))^2: rows and cells farther than rv from a particle are skipped
   // cubic boxes: the same decision on the exact integer r^2 of the fixed-point separation, with the
   // band around rv^2 only as wide as the fixed-point rounding of the positions can move r^2

@@ -32,7 +32,10 @@ __global__ void __launch_bounds__(256, 4) k_vertex_step_mixed(KArgs a) {
     prefetch_l2(a.fxp_build + i);
   }
   IsoResult res;
-  vertex_iso_mixed_eval<TPP, CUBIC>(a, gt, res);
+  if (TPP == 1 && CUBIC && a.inner)  // the inner list; pruned again from the Verlet list when due
+    vertex_iso_inner_eval(a, gt, a.scr_words[SCR_PRUNE] != 0u, res);
+  else
+    vertex_iso_mixed_eval<TPP, CUBIC>(a, gt, res);
   integrate_core<true>(a, 1, i, make_double4_32a(res.fx, res.fy, res.fz, res.e), res.w);
 }
 

@@ -22,10 +22,11 @@ __global__ void k_verlet_half(KArgs a, const uint32_t* gate) {
   if (i < a.n) verlet_half_one(a, i);
 }
 
-__global__ void k_reset_need(int32_t* status, const uint32_t* gate, int which) {
+__global__ void k_reset_need(int32_t* status, uint32_t* scr, const uint32_t* gate, int which) {
   if (gate_closed(gate)) return;
   status[MD_STATUS_NEED_NEIGH] = 0;
   status[MD_STATUS_LISTS] = which;
+  scr[SCR_PRUNE] = 1u;  // a new Verlet list: the inner list is pruned from it again
 }
 
 // Block-local full list of one block of MD_LOCAL_BLOCK slots (see md_verlet.cuh).
@@ -153,11 +154,11 @@ cudaError_t launch_build_verlet(const KArgs& a, int which, const uint32_t* gate,
   const int B = 128;
   const int gn = (a.n + B - 1) / B;
   if (which == MD_LIST_FULL && a.local_ok) {  // the vertex path's list in the block-local format
-    k_reset_need<<<1, 1, 0, st>>>(a.status, gate, MD_LIST_FULL | MD_LIST_FULL_LOCAL);
+    k_reset_need<<<1, 1, 0, st>>>(a.status, a.scr_words, gate, MD_LIST_FULL | MD_LIST_FULL_LOCAL);
     k_verlet_local<<<(a.n + MD_LOCAL_BLOCK - 1) / MD_LOCAL_BLOCK, MD_LOCAL_BLOCK, 0, st>>>(a, gate);
     return cudaGetLastError();
   }
-  k_reset_need<<<1, 1, 0, st>>>(a.status, gate, which);
+  k_reset_need<<<1, 1, 0, st>>>(a.status, a.scr_words, gate, which);
   k_verlet_full<<<gn, B, 0, st>>>(a, gate, (which & MD_LIST_NEWTON) ? 1 : 0);
   if (which & MD_LIST_HALF) {
     cudaError_t e = launch_scan<int64_t>(a.count_tmp, a.half_start, a.block_sums, a.n, gate, st);

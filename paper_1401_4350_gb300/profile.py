@@ -36,6 +36,7 @@ def main(argv=None):
     ap.add_argument("--path", default="vertex", choices=["vertex", "edge"])
     ap.add_argument("--what", default="forces", choices=["forces", "build", "step", "steps3", "stepkernel"])
     ap.add_argument("--fuse", type=int, default=1, choices=[0, 1], help="fuse_step of the system")
+    ap.add_argument("--prune", type=float, default=0.0, help="prune_skin of the system (inner list)")
     ap.add_argument("--tpp", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--order", default="rows", choices=["rows", "hilbert"])
@@ -48,7 +49,7 @@ def main(argv=None):
     prec = B.MD_MIXED if a.precision == "mixed" else B.MD_FP64
     path = B.MD_VERTEX if a.path == "vertex" else B.MD_EDGE
     sim = Simulation(s, prec, tpp=a.tpp, cell_order=B.MD_ORDER_HILBERT if a.order == "hilbert" else B.MD_ORDER_ROWS,
-                     fuse_step=a.fuse)
+                     fuse_step=a.fuse, prune_skin=a.prune)
     sim.prepare(path)
     if a.equilibrate > 0:  # time the liquid rather than the initial lattice
         sim.step(a.equilibrate, path, use_graph=True)
@@ -82,8 +83,9 @@ def main(argv=None):
     status = sim.status()
     assert status[B.MD_STATUS_CODE] == 0, status
     entries = int(sim.view("nbr_count", torch.int32, s.n).sum().item())
+    inner = int(sim.view("nbr_in_count", torch.int32, s.n).sum().item()) if a.prune > 0 else 0
     print(f"{a.workload} {a.precision} {a.path} {a.what}: median {statistics.median(times):.4f} ms over {a.reps}; "
-          f"n={s.n} list_entries={entries} kernel_sources_sha256={source_digest()}")
+          f"n={s.n} list_entries={entries} inner_entries={inner} kernel_sources_sha256={source_digest()}")
 
 
 def source_digest() -> str:

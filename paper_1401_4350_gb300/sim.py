@@ -26,7 +26,8 @@ def default_capacities(system: System, slack: float = 1.6):
 
 def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, tpp: int = 1, block: int = 0,
                 trace_capacity: int = 0, energy_every: int = 1, force_copies: int = 0,
-                cell_order: int = 0, edge_store: int = 0, list_format: int = 0, fuse_step: int = 0) -> B.md_params:
+                cell_order: int = 0, edge_store: int = 0, list_format: int = 0, fuse_step: int = 0,
+                prune_skin: float = 0.0) -> B.md_params:
     mn, mp = default_capacities(system)
     p = B.md_params()
     p.n = system.n
@@ -44,6 +45,7 @@ def make_params(system: System, precision: int, max_neigh=None, max_pairs=None, 
     p.edge_store = edge_store
     p.list_format = list_format
     p.fuse_step = fuse_step
+    p.prune_skin = float(prune_skin)
     for c in range(3):
         p.box[c] = float(system.box[c])
     p.rc, p.skin, p.dt, p.mass, p.inertia = system.rc, system.skin, system.dt, system.mass, system.inertia
@@ -63,10 +65,10 @@ class Simulation:
     def __init__(self, system: System, precision: int = B.MD_MIXED, max_neigh=None, max_pairs=None, tpp: int = 1,
                  block: int = 0, trace_capacity: int = 0, device: str = "cuda", stream=None, energy_every: int = 1,
                  force_copies: int = 0, cell_order: int = 0, edge_store: int = 0, list_format: int = 0,
-                 fuse_step: int = 1):
+                 fuse_step: int = 1, prune_skin: float = 0.0):
         self.system = system
         self.params = make_params(system, precision, max_neigh, max_pairs, tpp, block, trace_capacity, energy_every,
-                                  force_copies, cell_order, edge_store, list_format, fuse_step)
+                                  force_copies, cell_order, edge_store, list_format, fuse_step, prune_skin)
         rc = B.md_check_params(self.params)
         if rc != B.MD_OK:
             raise B.MDError(rc, B.last_error())
@@ -205,6 +207,16 @@ class Simulation:
         key = a * n + b
         key, counts = torch.unique(key, return_counts=True)
         return (torch.stack([key // n, key % n], 1).cpu().numpy(), counts.cpu().numpy(), int(mask.sum()))
+
+    def list_rows(self, name: str = "nbr", count: str = "nbr_count"):
+        """Rows of a grouped list (the Verlet list nbr, or the inner list nbr_in) as slot indices, in slot order."""
+        n = self.system.n
+        cnt = self.view(count, torch.int32, n).cpu().numpy()
+        cap = self.params.max_neigh
+        ng = (cap + 3) // 4
+        tab = self.view(name, torch.int32, ng * n * 4).view(ng, n, 4).permute(1, 0, 2).reshape(n, ng * 4)
+        tab = tab.cpu().numpy()
+        return [tab[i, :min(int(cnt[i]), cap)] for i in range(n)]
 
     def local_list_pairs(self):
         """Like full_list_pairs, for a full list held in the block-local format: each uint16 entry is a halo

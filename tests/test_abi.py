@@ -29,7 +29,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_abi_version(lib):
-    assert B.md_abi_version() == 3
+    assert B.md_abi_version() == 4
 
 
 def _lj_params(n=4000, precision=B.MD_MIXED):
@@ -52,6 +52,8 @@ def _lj_params(n=4000, precision=B.MD_MIXED):
     ("force_copies", 65, "force_copies"),
     ("list_format", 2, "list_format"),
     ("fuse_step", 2, "fuse_step"),
+    ("prune_skin", -0.1, "prune_skin"),
+    ("prune_skin", 0.3, "prune_skin"),
     ("cell_order", 2, "cell_order"),
     ("thermostat_every", -1, "thermostat_every"),
 ])
@@ -94,7 +96,7 @@ def test_workspace_layout(lib, precision, kind):
     offs = [getattr(L, f) for f in ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr",
                                     "nbr_count", "half_start", "pairs", "force", "virial", "torque",
                                     "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace", "pos_alt",
-                                    "fxp_alt", "scratch")]
+                                    "fxp_alt", "nbr_in", "nbr_in_count", "fxp_prune", "scratch")]
     assert all(o % 256 == 0 for o in offs)
     assert offs == sorted(offs) and len(set(offs)) == len(offs)
     assert L.force_elem == 8
@@ -150,13 +152,32 @@ def test_fused_step_buffers(lib, precision):
     s = systems.make_lj(3000, 0.85, seed=5)
     p = make_params(s, precision)
     L0 = B.md_workspace_layout(p)
-    assert L0.fxp_alt - L0.pos_alt <= 256 and L0.scratch - L0.fxp_alt <= 256
+    assert L0.fxp_alt - L0.pos_alt <= 256 and L0.nbr_in - L0.fxp_alt <= 256
     p.fuse_step = 1
     L1 = B.md_workspace_layout(p)
-    assert L1.fxp_alt - L1.pos_alt >= 32 * s.n and L1.scratch - L1.fxp_alt >= 16 * s.n
+    assert L1.fxp_alt - L1.pos_alt >= 32 * s.n and L1.nbr_in - L1.fxp_alt >= 16 * s.n
     assert L1.total - L0.total >= 48 * s.n - 512  # the empty regions held 256 bytes each
     for f in ("status", "fxp", "nbr", "force", "trace", "pos_alt"):
         assert getattr(L1, f) == getattr(L0, f)
+
+
+def test_inner_list_regions(lib):
+    """prune_skin > 0 with fused steps on the LJ/WCA mixed path in a cubic box reserves the inner list (as large
+    as the Verlet list), its lengths and the prune coordinates; any other case leaves them empty."""
+    s = systems.make_lj(3000, 0.85, seed=5)
+    p = make_params(s, B.MD_MIXED, fuse_step=1, prune_skin=0.1)
+    L = B.md_workspace_layout(p)
+    n = s.n
+    assert L.nbr_in_count - L.nbr_in >= 4 * n * p.max_neigh
+    assert L.fxp_prune - L.nbr_in_count >= 4 * n and L.scratch - L.fxp_prune >= 16 * n
+    for change in (dict(fuse_step=0), dict(prune_skin=0.0), dict(precision=B.MD_FP64)):
+        q = make_params(s, change.get("precision", B.MD_MIXED), fuse_step=change.get("fuse_step", 1),
+                        prune_skin=change.get("prune_skin", 0.1))
+        M = B.md_workspace_layout(q)
+        assert M.nbr_in_count - M.nbr_in <= 256 and M.scratch - M.fxp_prune <= 256, change
+    p.box[2] = p.box[2] * 1.1  # a non-cubic box has no inner list
+    M = B.md_workspace_layout(p)
+    assert M.nbr_in_count - M.nbr_in <= 256
 
 
 @pytest.mark.parametrize("precision", [B.MD_FP64, B.MD_MIXED])

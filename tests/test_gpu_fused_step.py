@@ -9,9 +9,10 @@ was."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1401_4350_gb300 import binding as B
 from paper_1401_4350_gb300 import systems
-from tests.test_gpu_parity import Sim, get_sys
+from tests.test_gpu_parity import Sim, get_sys, model_of
 
 pytestmark = pytest.mark.gpu
 
@@ -154,12 +155,12 @@ def test_flag_leaves_other_paths_unchanged(name, precision, path):
         assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
-@pytest.mark.parametrize("fuse", [1, 0])
-def test_kernel_timer_leaves_the_system_unchanged(fuse):
+@pytest.mark.parametrize("fuse,prune", [(1, 0.0), (0, 0.0), (1, 0.1)])
+def test_kernel_timer_leaves_the_system_unchanged(fuse, prune):
     import torch
     s = get_sys("lj4000")
-    a = Sim(s, B.MD_MIXED, fuse_step=fuse, trace_capacity=8)
-    b = Sim(s, B.MD_MIXED, fuse_step=fuse, trace_capacity=8)
+    a = Sim(s, B.MD_MIXED, fuse_step=fuse, trace_capacity=8, prune_skin=prune)
+    b = Sim(s, B.MD_MIXED, fuse_step=fuse, trace_capacity=8, prune_skin=prune)
     for sim in (a, b):
         sim.prepare(B.MD_VERTEX)
         sim.step(5, B.MD_VERTEX)
@@ -175,3 +176,62 @@ def test_kernel_timer_leaves_the_system_unchanged(fuse):
     for sim in (a, b):
         sim.step(40, B.MD_VERTEX)
     _same_state(a, b)
+
+
+# ---- the inner list (prune_skin > 0) ------------------------------------------------------------
+
+def _is_subsequence(small, big):
+    it = iter(big.tolist())
+    return all(any(x == y for y in it) for x in small.tolist())
+
+
+def test_inner_list_holds_every_pair_within_rc_in_verlet_list_order():
+    """After the first fused step (which prunes), every row of the inner list is a subsequence of the
+    slot's Verlet-list row, and it holds every pair closer than rc at the current positions."""
+    s = get_sys("lj4000")
+    sim = Sim(s, B.MD_MIXED, fuse_step=1, prune_skin=0.1)
+    sim.prepare(B.MD_VERTEX)
+    sim.step(2, B.MD_VERTEX)
+    st = sim.status()
+    assert st[B.MD_STATUS_CODE] == 0 and st[B.MD_STATUS_PRUNES] == 1, st
+    outer = sim.list_rows("nbr", "nbr_count")
+    inner = sim.list_rows("nbr_in", "nbr_in_count")
+    assert all(_is_subsequence(r_in, r_out) for r_in, r_out in zip(inner, outer))
+    assert sum(len(r) for r in inner) < 0.95 * sum(len(r) for r in outer)
+    x = sim.pos[:, :3].cpu().numpy()  # slot order
+    close = oracle.pairs(x, s.box, s.rc, use_cells=True)
+    sets = [set(r.tolist()) for r in inner]
+    assert all(j in sets[i] and i in sets[j] for i, j in close)
+
+
+@pytest.mark.parametrize("tpp", [1, 2])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_pruned_steps_follow_the_oracle(use_graph, tpp):
+    """150 steps with an inner list (rc + 0.1), rebuilds and prunes included, stay on the oracle's FP64
+    trajectory to the mixed precision's level (as without the inner list); with two threads per
+    particle the inner list is not used and nothing is pruned."""
+    s = get_sys("lj4000")
+    steps = 150
+    p_ref, v_ref, _, _, tr = oracle.run_nve(s.pos, s.vel, model_of(s), s.dt, steps, use_cells=True)
+    sim = Sim(s, B.MD_MIXED, fuse_step=1, prune_skin=0.1, tpp=tpp, trace_capacity=steps + 1)
+    sim.prepare(B.MD_VERTEX)
+    sim.step(steps, B.MD_VERTEX, use_graph=use_graph)
+    st = sim.status()
+    assert st[B.MD_STATUS_CODE] == 0 and st[B.MD_STATUS_REBUILDS] >= 1, st
+    if tpp == 1:
+        assert st[B.MD_STATUS_PRUNES] > st[B.MD_STATUS_REBUILDS] + 1, st
+    else:
+        assert st[B.MD_STATUS_PRUNES] == 0, st
+    pos, _ = sim.positions()
+    d = pos - p_ref
+    d -= s.box * np.rint(d / s.box)
+    assert np.abs(d).max() < 1e-6
+    t = sim.trace()
+    e_gpu = t[:, 1] + t[:, 2]
+    e_ref = tr[:, 0] + tr[:, 1] + tr[:, 2]
+    assert np.abs(e_gpu - e_ref).max() / s.n < 1e-5
+    # the same run without the inner list: the same trajectory up to the order of the FP32 sums
+    plain, _ = _run(s, 1, steps, use_graph, tpp=tpp)
+    dp = pos - plain.positions()[0]
+    dp -= s.box * np.rint(dp / s.box)
+    assert np.abs(dp).max() < 1e-8
