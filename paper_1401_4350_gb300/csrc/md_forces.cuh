@@ -21,7 +21,7 @@ __device__ __forceinline__ void lj_terms(const KArgs& a, float r2, float& fs, fl
 }
 
 __device__ __forceinline__ void lj_terms(const KArgs& a, double r2, double& fs, double& pe) {
-  const double r2i = __drcp_rn(r2);
+  const double r2i = drcp_refined(r2);
   const double sr2 = a.sig2_d * r2i;
   const double sr6 = sr2 * sr2 * sr2;
   fs = -a.lj_c24_d * sr6 * (2.0 * sr6 - 1.0) * r2i;
@@ -1036,7 +1036,7 @@ __device__ __forceinline__ void vertex_fp64_body(const KArgs& a, int gt) {
         if (PATCHY) o = patchy_pair<(PATCHY ? NP : 1), false>(a, d, r2, Pi, i, jj[u]);
         else o = iso_pair<double>(a, d, r2, i, jj[u]);
         acc[0] += o.F.x; acc[1] += o.F.y; acc[2] += o.F.z;
-        acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z;
+        if (PATCHY) { acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z; }
         acc[6] += o.e; acc[7] += o.w;
       }
       cur = nxt;
@@ -1420,7 +1420,7 @@ __device__ __forceinline__ void vertex_newton_fp64_body(const KArgs& a, int i) {
         atomicAdd(tj + 0, o.tj.x); atomicAdd(tj + 1, o.tj.y); atomicAdd(tj + 2, o.tj.z);
       }
       acc[0] += o.F.x; acc[1] += o.F.y; acc[2] += o.F.z;
-      acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z;
+      if (PATCHY) { acc[3] += o.ti.x; acc[4] += o.ti.y; acc[5] += o.ti.z; }
       acc[6] += eh; acc[7] += wh;
     }
     cur = nxt;

@@ -232,6 +232,16 @@ __device__ __forceinline__ float frcp_refined(float x) {
   return __fmaf_rn(y, __fmaf_rn(-x, y, 1.f), y);
 }
 
+// 1/x in FP64 for x a normal positive number: the hardware approximation refined by two Newton-Raphson
+// steps y <- y + y (1 - x y), each of which squares the relative error, so a start within 2^-14 ends
+// below the FP64 rounding (not always correctly rounded; the FP64 path's parity bound is 1e-12).
+__device__ __forceinline__ double drcp_refined(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
 __device__ __forceinline__ float fexp2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
