@@ -361,9 +361,10 @@ def measured_traffic(kernel: str, n: int, entries: int):
     return rec["dram_bytes_per_launch"] * alg_now / alg_cap
 
 
-def run_accuracy(n_drift: int = 65536, drift_steps: int = 2000):
-    """Force error of the mixed path against the FP64 path on the headline system's initial state, and
-    energy drift (least-squares slope of E_tot / N per 10^4 steps) of both precisions on LJ N = 65,536."""
+def run_accuracy(n_drift: int = 65536, drift_steps: int = 2000, snapshot_steps: int = 1000):
+    """Force error of the mixed path against the FP64 path on the headline system's initial state and after
+    `snapshot_steps` headline steps, and energy drift (least-squares slope of E_tot / N per 10^4 steps) of
+    both precisions on LJ N = 65,536 (mixed: the headline's fused steps over the inner list)."""
     import numpy as np
     import torch
     from paper_1401_4350_gb300 import binding as B
@@ -380,10 +381,28 @@ def run_accuracy(n_drift: int = 65536, drift_steps: int = 2000):
         torch.cuda.empty_cache()
     frms = float(np.sqrt((F[B.MD_FP64] ** 2).sum(1).mean()))
     out["max_force_error_mixed_vs_fp64_frms"] = float(np.abs(F[B.MD_MIXED] - F[B.MD_FP64]).max()) / frms
+    # the same after the headline's steps: the liquid the timed run sees
+    run = Simulation(s, B.MD_MIXED, fuse_step=1, prune_skin=PRUNE_SKIN)
+    run.prepare(B.MD_VERTEX)
+    run.step(snapshot_steps, B.MD_VERTEX, use_graph=True)
+    x, v = run.positions()
+    del run
+    torch.cuda.empty_cache()
+    for prec in (B.MD_MIXED, B.MD_FP64):
+        sim = Simulation(s, prec)
+        sim.load_state(x, v)
+        sim.prepare(B.MD_VERTEX)
+        F[prec] = sim.forces()[0]
+        del sim
+        torch.cuda.empty_cache()
+    frms = float(np.sqrt((F[B.MD_FP64] ** 2).sum(1).mean()))
+    out[f"max_force_error_mixed_vs_fp64_frms_step{snapshot_steps}"] = \
+        float(np.abs(F[B.MD_MIXED] - F[B.MD_FP64]).max()) / frms
     small = systems.make_lj(n_drift, 0.85, 1.0, seed=1001)
     drift = {}
     for name, prec in (("fp64", B.MD_FP64), ("mixed", B.MD_MIXED)):
-        sim = Simulation(small, prec, trace_capacity=drift_steps + 1)
+        sim = Simulation(small, prec, trace_capacity=drift_steps + 1,
+                         prune_skin=PRUNE_SKIN if prec == B.MD_MIXED else 0.0)
         sim.prepare(B.MD_VERTEX)
         sim.step(drift_steps, B.MD_VERTEX, use_graph=True)
         tr = sim.trace()

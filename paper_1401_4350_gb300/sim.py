@@ -151,6 +151,39 @@ class Simulation:
     def status(self):
         return B.md_read_status(self.params, self.ws, self._st())
 
+    # -- checkpoint / resume -------------------------------------------------------------------------
+    def checkpoint(self, path):
+        """Writes the dynamic state to an .npz file: FP64 positions and velocities (and, patchy, orientations and
+        angular momenta) in slot order with each slot's original particle id, the step counter (which also
+        keys the thermostat's random numbers), the box and the particle count.  Slot order is kept so that a
+        resumed run sorts its cells, and so sums its forces, exactly as the original would."""
+        extra = {}
+        if self.quat is not None:
+            extra = {"quat": self.quat.cpu().numpy(), "angmom": self.angmom[:, :3].cpu().numpy()}
+        st = self.status()
+        np.savez(path, pos=self.pos[:, :3].cpu().numpy(), vel=self.vel[:, :3].cpu().numpy(),
+                 id=self.id.cpu().numpy(), step=np.int64(st[B.MD_STATUS_STEPS]),
+                 box=np.asarray(self.system.box, float), n=np.int64(self.system.n), **extra)
+
+    def resume(self, path, path_kind=B.MD_VERTEX):
+        """Loads a checkpoint written by checkpoint() for the same system, restores the step counter and
+        prepares cells, lists and forces for `path_kind`."""
+        d = np.load(path)
+        if int(d["n"]) != self.system.n or not np.array_equal(d["box"], np.asarray(self.system.box, float)):
+            raise ValueError("the checkpoint is of another system (particle count or box differ)")
+        ids = np.asarray(d["id"])
+        if not np.array_equal(np.sort(ids), np.arange(self.system.n)):
+            raise ValueError("the checkpoint's particle ids are not a permutation")
+        self.pos[:, :3] = torch.as_tensor(d["pos"], dtype=torch.float64, device=self.device)
+        self.vel[:, :3] = torch.as_tensor(d["vel"], dtype=torch.float64, device=self.device)
+        if self.quat is not None:
+            self.quat[:] = torch.as_tensor(d["quat"], dtype=torch.float64, device=self.device)
+            self.angmom[:, :3] = torch.as_tensor(d["angmom"], dtype=torch.float64, device=self.device)
+        self.id.copy_(torch.as_tensor(ids, dtype=torch.int32, device=self.device))
+        B.md_init_workspace(self.params, self.ws, self._st())
+        self.view("status", torch.int32, B.MD_STATUS_WORDS)[B.MD_STATUS_STEPS] = int(d["step"])
+        self.prepare(path_kind)
+
     # -- results in the caller's original order -------------------------------------------------
     def _order(self):
         return self.id.long()
