@@ -538,7 +538,6 @@ struct IsoAcc {
   float bmin;         // smallest |r^2 - rc^2| seen (band test)
 };
 
-// One group of four list entries (cur) of particle si.  LIVE: some entries may lie past the count.
 // Where the entries of a row and the coordinates they name come from.
 // Global format: int32 slots, groups of four per int4; coordinates gathered from fxp.
 struct GlobalRows {
@@ -571,37 +570,34 @@ __device__ __forceinline__ GlobalRows global_rows(const KArgs& a, int i, bool in
 // slot's inner-list row (the entries closer than rc + prune_skin, in walk order, four per int4 group).
 struct NoPrune {
   static constexpr bool kPrune = false;
-  __device__ __forceinline__ void take(const int4&, unsigned) {}
-  __device__ __forceinline__ void finish(const KArgs&, int, const uint4&) {}
+  __device__ __forceinline__ void take(const KArgs&, const int4&, unsigned) {}
+  __device__ __forceinline__ void finish(const KArgs&, const uint4&) {}
 };
 
 struct InnerPrune {
   static constexpr bool kPrune = true;
-  int4* out;  // the slot's first group in nbr_in (group g at out[g * n])
-  size_t n;
-  int written, nb;
-  int b0, b1, b2, b3;
-  __device__ __forceinline__ void push(int j) {
-    b0 = nb == 0 ? j : b0;
-    b1 = nb == 1 ? j : b1;
-    b2 = nb == 2 ? j : b2;
-    b3 = nb == 3 ? j : b3;
-    if (++nb == 4) {
-      out[(size_t)(written >> 2) * n] = make_int4(b0, b1, b2, b3);
-      written += 4;
-      nb = 0;
-    }
+  int i;               // the slot
+  int cnt;             // entries kept so far (the last cnt % 4 of them still in b0..b3)
+  int b0, b1, b2, b3;  // the group being filled
+  __device__ __forceinline__ void push(const KArgs& a, int j) {
+    const int k = cnt & 3;
+    b0 = k == 0 ? j : b0;
+    b1 = k == 1 ? j : b1;
+    b2 = k == 2 ? j : b2;
+    b3 = k == 3 ? j : b3;
+    if (++cnt & 3) return;
+    ((int4*)a.nbr_in)[(size_t)((cnt >> 2) - 1) * (size_t)a.n + i] = make_int4(b0, b1, b2, b3);
   }
-  __device__ __forceinline__ void take(const int4& cur, unsigned keep) {
-    if (keep & 1u) push(cur.x);
-    if (keep & 2u) push(cur.y);
-    if (keep & 4u) push(cur.z);
-    if (keep & 8u) push(cur.w);
+  __device__ __forceinline__ void take(const KArgs& a, const int4& cur, unsigned keep) {
+    if (keep & 1u) push(a, cur.x);
+    if (keep & 2u) push(a, cur.y);
+    if (keep & 4u) push(a, cur.z);
+    if (keep & 8u) push(a, cur.w);
   }
   // the row is never longer than the Verlet-list row it comes from, so it fits the same capacity
-  __device__ __forceinline__ void finish(const KArgs& a, int i, const uint4& si) {
-    if (nb) out[(size_t)(written >> 2) * n] = make_int4(b0, b1, b2, b3);
-    a.nbr_in_count[i] = written + nb;
+  __device__ __forceinline__ void finish(const KArgs& a, const uint4& si) {
+    if (cnt & 3) ((int4*)a.nbr_in)[(size_t)(cnt >> 2) * (size_t)a.n + i] = make_int4(b0, b1, b2, b3);
+    a.nbr_in_count[i] = cnt;
     a.fxp_prune[i] = si;
   }
 };
@@ -639,15 +635,20 @@ struct LocalRows {
   }
 };
 
-// keep (PRUNE): the entries of the group closer than rc + prune_skin, as bits 0..3.
-template <bool LIVE, class Rows, bool PRUNE = false>
-__device__ __forceinline__ void iso_group(const KArgs& a, const uint4& si, const int4& cur, int lim, const Rows& R,
-                                          IsoAcc& A, unsigned* keep = nullptr) {
-  uint4 sj[4];
+// The partners' coordinates of a group of four list entries.
+template <class Rows>
+__device__ __forceinline__ void gather4(const KArgs& a, const Rows& R, const int4& cur, uint4 sj[4]) {
   sj[0] = R.coords(a, (unsigned)cur.x);
   sj[1] = R.coords(a, (unsigned)cur.y);
   sj[2] = R.coords(a, (unsigned)cur.z);
   sj[3] = R.coords(a, (unsigned)cur.w);
+}
+
+// One group of four list entries of particle si, from their gathered coordinates sj.  LIVE: some entries
+// may lie past the count.  keep (PRUNE): the entries closer than rc + prune_skin, as bits 0..3.
+template <bool LIVE, bool PRUNE = false>
+__device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, const uint4 sj[4], int lim,
+                                            IsoAcc& A, unsigned* keep = nullptr) {
   float r2[4], dx[4], dy[4], dz[4];
 #pragma unroll
   for (int u = 0; u < 4; u++) {
@@ -745,21 +746,29 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
 #pragma unroll
     for (int d = 2; d < kListPrefetch; d++)
       if (l + d * TPP < ng) R.prefetch(l + d * TPP, n);
+    // the gathers of each group are issued one group ahead, so that their latency overlaps the
+    // arithmetic of the group before
     int g = l;
+    uint4 sj[4];
+    gather4(a, R, cur, sj);
     for (; g < nfull; g += TPP) {  // groups of four entries that are all in the list
       const int4 nxt = R.group(g + TPP, ng, n);
       if (g + kListPrefetch * TPP < ng) R.prefetch(g + kListPrefetch * TPP, n);
+      uint4 sn[4];
+      gather4(a, R, nxt, sn);  // the next group's coordinates are in flight during this group's arithmetic
       unsigned keep = 0u;
-      iso_group<false, Rows, Sink::kPrune>(a, si, cur, 4, R, A, &keep);
-      if (Sink::kPrune) sink->take(cur, keep);
+      iso_group_c<false, Sink::kPrune>(a, si, sj, 4, A, &keep);
+      if (Sink::kPrune) sink->take(a, cur, keep);
       cur = nxt;
+#pragma unroll
+      for (int u = 0; u < 4; u++) sj[u] = sn[u];
     }
     if (g < ng) {  // the partial last group
       unsigned keep = 0u;
-      iso_group<true, Rows, Sink::kPrune>(a, si, cur, cnt - 4 * g, R, A, &keep);
-      if (Sink::kPrune) sink->take(cur, keep);
+      iso_group_c<true, Sink::kPrune>(a, si, sj, cnt - 4 * g, A, &keep);
+      if (Sink::kPrune) sink->take(a, cur, keep);
     }
-    if (Sink::kPrune) sink->finish(a, i, si);
+    if (Sink::kPrune) sink->finish(a, si);
   }
   if (A.bmin <= a.rwca2_band_s) {
     // pairs near rc: take the side of the exact FP64 definition, re-walking this lane's entries
@@ -840,9 +849,8 @@ __device__ __forceinline__ void vertex_iso_inner_eval(const KArgs& a, int i, boo
   if (prune) {
     const GlobalRows R = global_rows(a, i, false);
     InnerPrune S;
-    S.out = (int4*)a.nbr_in + min(i, a.n - 1);
-    S.n = (size_t)a.n;
-    S.written = S.nb = 0;
+    S.i = i;
+    S.cnt = 0;
     S.b0 = S.b1 = S.b2 = S.b3 = 0;
     vertex_iso_cubic_rows<1>(a, i, R, res, &S);
   } else {
