@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kBChunk) k_b_edge_acc(BatchDev b) {
   }
 }
 
-__global__ void __launch_bounds__(kBForce) k_b_forces(BatchDev b) {
+__global__ void __launch_bounds__(kBForce, 6) k_b_forces(BatchDev b) {
   __shared__ KArgs ka;
   __shared__ int s_item, s_rep;
   if (threadIdx.x == 0) s_rep = -1;
