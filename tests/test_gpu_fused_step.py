@@ -235,3 +235,25 @@ def test_pruned_steps_follow_the_oracle(use_graph, tpp):
     dp = pos - plain.positions()[0]
     dp -= s.box * np.rint(dp / s.box)
     assert np.abs(dp).max() < 1e-8
+
+
+@pytest.mark.parametrize("name", ["lj_tiny_box", "lj_noncubic", "wca20000"])
+def test_pruned_steps_on_small_and_noncubic_boxes(name):
+    """The inner list on a 500-particle box (a 5x5x5 grid of half cells, every row wrapping), on WCA, and
+    (switched off: non-cubic) on a non-cubic box: 120 steps stay on the separate kernels' trajectory to
+    rounding, and the status is clean."""
+    s = _system(name)
+    a = Sim(s, B.MD_MIXED, fuse_step=1, prune_skin=0.1 if name != "wca20000" else 0.08)
+    b = Sim(s, B.MD_MIXED, fuse_step=0)
+    for sim in (a, b):
+        sim.prepare(B.MD_VERTEX)
+        sim.step(120, B.MD_VERTEX)
+    sa = a.status()
+    assert sa[B.MD_STATUS_CODE] == 0, sa
+    if name == "lj_noncubic":
+        assert sa[B.MD_STATUS_PRUNES] == 0
+    else:
+        assert sa[B.MD_STATUS_PRUNES] >= 2
+    d = a.positions()[0] - b.positions()[0]
+    d -= s.box * np.rint(d / s.box)
+    assert np.abs(d).max() < 1e-8
