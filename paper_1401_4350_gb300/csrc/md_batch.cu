@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kBChunk) k_b_edge_acc(BatchDev b) {
   }
 }
 
-__global__ void __launch_bounds__(kBForce, 6) k_b_forces(BatchDev b) {
+__global__ void __launch_bounds__(kBForce) k_b_forces(BatchDev b) {
   __shared__ KArgs ka;
   __shared__ int s_item, s_rep;
   if (threadIdx.x == 0) s_rep = -1;
@@ -309,17 +309,17 @@ __global__ void __launch_bounds__(kBForce, 6) k_b_forces(BatchDev b) {
         edge_mixed_body<false, 1>(ka, first / 32 + (threadIdx.x >> 5), kBForce / 32, min(E, first + kBEdgePairs));
     } else if (kind & KIND_CUBIC) {
       switch (kind & 7) {
-        case KIND_V1: vertex_iso_mixed_body<1, true>(ka, gt); break;
-        case KIND_V2: vertex_iso_mixed_body<2, true>(ka, gt); break;
-        case KIND_V4: vertex_iso_mixed_body<4, true>(ka, gt); break;
-        default: vertex_iso_mixed_body<8, true>(ka, gt); break;
+        case KIND_V1: vertex_iso_mixed_body<1, true, false>(ka, gt); break;
+        case KIND_V2: vertex_iso_mixed_body<2, true, false>(ka, gt); break;
+        case KIND_V4: vertex_iso_mixed_body<4, true, false>(ka, gt); break;
+        default: vertex_iso_mixed_body<8, true, false>(ka, gt); break;
       }
     } else {
       switch (kind & 7) {
-        case KIND_V1: vertex_iso_mixed_body<1, false>(ka, gt); break;
-        case KIND_V2: vertex_iso_mixed_body<2, false>(ka, gt); break;
-        case KIND_V4: vertex_iso_mixed_body<4, false>(ka, gt); break;
-        default: vertex_iso_mixed_body<8, false>(ka, gt); break;
+        case KIND_V1: vertex_iso_mixed_body<1, false, false>(ka, gt); break;
+        case KIND_V2: vertex_iso_mixed_body<2, false, false>(ka, gt); break;
+        case KIND_V4: vertex_iso_mixed_body<4, false, false>(ka, gt); break;
+        default: vertex_iso_mixed_body<8, false, false>(ka, gt); break;
       }
     }
   }

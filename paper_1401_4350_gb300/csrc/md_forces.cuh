@@ -724,7 +724,9 @@ __device__ __forceinline__ void store_iso(const KArgs& a, int gt, int tpp, const
   }
 }
 
-template <int TPP, class Rows, class Sink = NoPrune>
+// AHEAD: gather each group's partner coordinates one group ahead (more registers, more loads in flight;
+// the batched kernel, which runs at a larger register budget per thread, keeps the plain order).
+template <int TPP, class Rows, class Sink = NoPrune, bool AHEAD = true>
 __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R, IsoResult& res,
                                                       Sink* sink = nullptr) {
   const int i = gt / TPP, l = gt % TPP;
@@ -750,20 +752,26 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
     // arithmetic of the group before
     int g = l;
     uint4 sj[4];
-    gather4(a, R, cur, sj);
+    if (AHEAD) gather4(a, R, cur, sj);
     for (; g < nfull; g += TPP) {  // groups of four entries that are all in the list
       const int4 nxt = R.group(g + TPP, ng, n);
       if (g + kListPrefetch * TPP < ng) R.prefetch(g + kListPrefetch * TPP, n);
       uint4 sn[4];
-      gather4(a, R, nxt, sn);  // the next group's coordinates are in flight during this group's arithmetic
+      if (AHEAD)
+        gather4(a, R, nxt, sn);  // the next group's coordinates are in flight during this group's arithmetic
+      else
+        gather4(a, R, cur, sj);
       unsigned keep = 0u;
       iso_group_c<false, Sink::kPrune>(a, si, sj, 4, A, &keep);
       if (Sink::kPrune) sink->take(a, cur, keep);
       cur = nxt;
+      if (AHEAD) {
 #pragma unroll
-      for (int u = 0; u < 4; u++) sj[u] = sn[u];
+        for (int u = 0; u < 4; u++) sj[u] = sn[u];
+      }
     }
     if (g < ng) {  // the partial last group
+      if (!AHEAD) gather4(a, R, cur, sj);
       unsigned keep = 0u;
       iso_group_c<true, Sink::kPrune>(a, si, sj, cnt - 4 * g, A, &keep);
       if (Sink::kPrune) sink->take(a, cur, keep);
@@ -835,11 +843,11 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
   }
 }
 
-template <int TPP>
+template <int TPP, bool AHEAD = true>
 __device__ __forceinline__ void vertex_iso_cubic_eval(const KArgs& a, int gt, IsoResult& res) {
   if (!full_list_current(a)) return;
   const GlobalRows R = global_rows(a, gt / TPP, false);
-  vertex_iso_cubic_rows<TPP>(a, gt, R, res);
+  vertex_iso_cubic_rows<TPP, GlobalRows, NoPrune, AHEAD>(a, gt, R, res);
 }
 
 // The fused step's walk with an inner list (one thread per particle, cubic box): the inner list, or,
@@ -889,10 +897,10 @@ __device__ __forceinline__ void vertex_iso_local_body(const KArgs& a, uint4* hal
 }
 
 // The isotropic mixed vertex evaluation over the int32 full list (cubic boxes: the integer-r^2 path)
-template <int TPP, bool CUBIC>
+template <int TPP, bool CUBIC, bool AHEAD = true>
 __device__ __forceinline__ void vertex_iso_mixed_eval(const KArgs& a, int gt, IsoResult& res) {
   if (CUBIC) {
-    vertex_iso_cubic_eval<TPP>(a, gt, res);
+    vertex_iso_cubic_eval<TPP, AHEAD>(a, gt, res);
     return;
   }
   if (!full_list_current(a)) return;
@@ -989,10 +997,10 @@ __device__ __forceinline__ void vertex_iso_mixed_eval(const KArgs& a, int gt, Is
   }
 }
 
-template <int TPP, bool CUBIC>
+template <int TPP, bool CUBIC, bool AHEAD = true>
 __device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
   IsoResult res;
-  vertex_iso_mixed_eval<TPP, CUBIC>(a, gt, res);
+  vertex_iso_mixed_eval<TPP, CUBIC, AHEAD>(a, gt, res);
   store_iso(a, gt, TPP, res);
 }
 
