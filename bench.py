@@ -318,8 +318,9 @@ def run_ours(args, rank, world, dist):
         "roofline": roofline,
         "e2e": e2e,
         # one call of K fused steps: the opening integrate (its last block decides), K - 1 fused step
-        # kernels each followed by a one-warp decision kernel, then the last forces and the closing
-        # integrate; a rebuild adds 9 cell and 2 Verlet kernels
+        # kernels each followed by a one-warp decision kernel, then the fused closing launch (the last
+        # forces and the closing half kick) and its decision kernel; a rebuild adds 9 cell and 2 Verlet
+        # kernels
         "gpu_launches": 2 * args.steps + 1 + 11 * rebuilds,
         "clocks": clocks,
         "graph": not args.direct,

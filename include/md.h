@@ -359,7 +359,7 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
  * returns.  The results are the same as with separate kernels: positions, velocities and the
  * rebuild decisions bit for bit, and the energy totals too (exact sums of per-particle terms).
  * The per-particle force, energy and virial words are written only by the last force evaluation of
- * a call.
+ * a call, which is fused with the closing half kick too.
  *
  * md_time_step_kernel -- mean duration (ms, CUDA events on `stream`; synchronises) of `reps` launches
  * of what md_step_verlet runs once per step for `path` besides the rebuild: the fused kernel and the

@@ -913,8 +913,11 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
     }
   }
   const KArgs& c = alt ? b : a;
-  if (e == cudaSuccess && fused) e = launch_forces(c, path, p->block_size, st);  // forces of the last step
-  if (e == cudaSuccess) e = launch_integrate(c, 2, 0, 0ULL, st);
+  if (fused) {  // forces of the last step, stored, and its closing half kick: one kernel (and the decision)
+    if (e == cudaSuccess) e = launch_step_fused(c, p->block_size, 0, 0ULL, st, true);
+  } else if (e == cudaSuccess) {
+    e = launch_integrate(c, 2, 0, 0ULL, st);
+  }
   if (e == cudaSuccess && alt) {  // the caller's positions and the primary coordinates hold the state again
     e = cudaMemcpyAsync(a.pos, b.pos, 32 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.fxp, b.fxp, 16 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);

@@ -426,17 +426,19 @@ __device__ __forceinline__ void step_decide_body(const KArgs& a, int mode, bool 
   }
   if (lane == 0) {
     if (mode == 1 || mode == 2) a.status[MD_STATUS_STEPS] += 1;
+    // a fused launch pruned the inner list if a prune was pending when it started
+    const bool pending = a.inner && a.scr_words[SCR_PRUNE] != 0u;
+    const bool pruned = after_fused && pending;
+    if (pruned) a.status[MD_STATUS_PRUNES] += 1;
     if (drift) {
       const unsigned g = __uint_as_float(m) > a.disp_thr2 ? 1u : 0u;
       a.scr_words[SCR_GATE] = g;
       a.status[MD_STATUS_REBUILDS] += (int)g;
-      if (a.inner) {
-        const bool pending = a.scr_words[SCR_PRUNE] != 0u;
-        const bool pruned = after_fused && pending;
-        if (pruned) a.status[MD_STATUS_PRUNES] += 1;
+      if (a.inner)
         a.scr_words[SCR_PRUNE] = (g || (pending && !pruned) || __uint_as_float(mp) > a.prune_thr2) ? 1u : 0u;
-      }
       if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle, g);
+    } else if (pruned) {
+      a.scr_words[SCR_PRUNE] = 0u;  // nothing moved in this launch: the new inner list holds
     }
   }
 }

@@ -183,7 +183,9 @@ cudaError_t launch_integrate(const KArgs& a, int mode, int use_cond, unsigned lo
                              cudaStream_t st);
 // The fused force + integrate step (MIDDLE phase) of the isotropic mixed vertex path: reads pos/fxp,
 // writes the drifted state to pos_alt/fxp_alt; then the one-warp step decision.
-cudaError_t launch_step_fused(const KArgs& a, int block, int use_cond, unsigned long long cond_handle, cudaStream_t st);
+// last = true: the closing phase of a call (the last forces, stored, then the closing half kick; no drift).
+cudaError_t launch_step_fused(const KArgs& a, int block, int use_cond, unsigned long long cond_handle, cudaStream_t st,
+                              bool last = false);
 // The step decision as a one-warp kernel (after the fused step kernel).
 cudaError_t launch_decide(const KArgs& a, int mode, int use_cond, unsigned long long cond_handle, cudaStream_t st);
 cudaError_t launch_get_forces(const KArgs& a, double* fout, double* tout, cudaStream_t st);

@@ -18,7 +18,9 @@
 
 namespace mdgb {
 
-template <int TPP, bool CUBIC>
+// LAST: the closing phase of a call instead: the forces of the last step (also stored, for the caller and
+// the next call's opening kick), its closing half kick and its energies; no drift.
+template <int TPP, bool CUBIC, bool LAST>
 __global__ void __launch_bounds__(256, 4) k_vertex_step_mixed(KArgs a) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   // the owner of each particle integrates it (its force is zero if the list was not current, which
@@ -36,30 +38,40 @@ __global__ void __launch_bounds__(256, 4) k_vertex_step_mixed(KArgs a) {
     vertex_iso_inner_eval(a, gt, a.scr_words[SCR_PRUNE] != 0u, res);
   else
     vertex_iso_mixed_eval<TPP, CUBIC>(a, gt, res);
-  integrate_core<true>(a, 1, i, make_double4_32a(res.fx, res.fy, res.fz, res.e), res.w);
+  if (LAST) store_iso(a, gt, TPP, res);
+  integrate_core<true>(a, LAST ? 2 : 1, i, make_double4_32a(res.fx, res.fy, res.fz, res.e), res.w);
 }
 
-cudaError_t launch_step_fused(const KArgs& a, int block, int use_cond, unsigned long long cond_handle, cudaStream_t st) {
-  if (block <= 0) block = 64;  // measured at LJ 1M: 64 slightly ahead of 128 and 256
+template <bool LAST>
+static void launch_fused_kernel(const KArgs& a, int block, cudaStream_t st) {
   const int64_t threads = (int64_t)a.n * a.tpp;
   const int grid = (int)((threads + block - 1) / block);
   if (a.cubic) {
     switch (a.tpp) {
-      case 1: k_vertex_step_mixed<1, true><<<grid, block, 0, st>>>(a); break;
-      case 2: k_vertex_step_mixed<2, true><<<grid, block, 0, st>>>(a); break;
-      case 4: k_vertex_step_mixed<4, true><<<grid, block, 0, st>>>(a); break;
-      default: k_vertex_step_mixed<8, true><<<grid, block, 0, st>>>(a); break;
+      case 1: k_vertex_step_mixed<1, true, LAST><<<grid, block, 0, st>>>(a); break;
+      case 2: k_vertex_step_mixed<2, true, LAST><<<grid, block, 0, st>>>(a); break;
+      case 4: k_vertex_step_mixed<4, true, LAST><<<grid, block, 0, st>>>(a); break;
+      default: k_vertex_step_mixed<8, true, LAST><<<grid, block, 0, st>>>(a); break;
     }
   } else {
     switch (a.tpp) {
-      case 1: k_vertex_step_mixed<1, false><<<grid, block, 0, st>>>(a); break;
-      case 2: k_vertex_step_mixed<2, false><<<grid, block, 0, st>>>(a); break;
-      case 4: k_vertex_step_mixed<4, false><<<grid, block, 0, st>>>(a); break;
-      default: k_vertex_step_mixed<8, false><<<grid, block, 0, st>>>(a); break;
+      case 1: k_vertex_step_mixed<1, false, LAST><<<grid, block, 0, st>>>(a); break;
+      case 2: k_vertex_step_mixed<2, false, LAST><<<grid, block, 0, st>>>(a); break;
+      case 4: k_vertex_step_mixed<4, false, LAST><<<grid, block, 0, st>>>(a); break;
+      default: k_vertex_step_mixed<8, false, LAST><<<grid, block, 0, st>>>(a); break;
     }
   }
+}
+
+cudaError_t launch_step_fused(const KArgs& a, int block, int use_cond, unsigned long long cond_handle, cudaStream_t st,
+                              bool last) {
+  if (block <= 0) block = 64;  // measured at LJ 1M: 64 slightly ahead of 128 and 256
+  if (last)
+    launch_fused_kernel<true>(a, block, st);
+  else
+    launch_fused_kernel<false>(a, block, st);
   const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? launch_decide(a, 1, use_cond, cond_handle, st) : e;
+  return e == cudaSuccess ? launch_decide(a, last ? 2 : 1, use_cond, cond_handle, st) : e;
 }
 
 }  // namespace mdgb
