@@ -231,28 +231,21 @@ def run_ours(args, rank, world, dist):
                                "prunes": prunes, "pair_evals_per_s": pairs * 1e3 / step_ms,
                                "step_kernel_ms": kernel_ms, "force_kernel_ms": force_ms, "fuse_step": 1,
                                "prune_skin": PRUNE_SKIN, "mean_inner_list": inner_entries / n}
-    # ---- end to end through the C ABI with host-resident state ----
-    pos_h = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
-    vel_h = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
+    # ---- end to end through the C ABI with host-resident state: md_step_verlet_host, one step per call,
+    # positions and velocities ([n][3] FP64 each, pinned) copied in and out by the call, energies out ----
+    pos_h, vel_h = sim.slot_state_host(pin=True)
     en_h = torch.empty(B.MD_ENERGY_WORDS, dtype=torch.float64, pin_memory=True)
-    pos_h.copy_(sim.pos)
-    vel_h.copy_(sim.vel)
-    energy_dev = sim.view("energy", torch.float64, B.MD_ENERGY_WORDS)
     e2e_steps = max(10, min(args.steps // 10, 300))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        sim.pos.copy_(pos_h, non_blocking=True)
-        sim.vel.copy_(vel_h, non_blocking=True)
-        sim.step(1, headline_path, use_graph=True)
-        pos_h.copy_(sim.pos, non_blocking=True)
-        vel_h.copy_(sim.vel, non_blocking=True)
-        en_h.copy_(energy_dev, non_blocking=True)
+        sim.step_host(pos_h, vel_h, 1, headline_path, use_graph=True, host_energy=en_h)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    assert np.isfinite(en_h.numpy()[:4]).all()
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 2 * n * 32,
-           "d2h_bytes_per_step": 2 * n * 32 + 8 * B.MD_ENERGY_WORDS}
+    assert np.isfinite(en_h.numpy()[:4]).all() and sim.status()[B.MD_STATUS_CODE] == 0
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 2 * n * 24,
+           "d2h_bytes_per_step": 2 * n * 24 + 8 * B.MD_ENERGY_WORDS,
+           "api": "md_step_verlet_host, 1 step per call"}
     del sim
     torch.cuda.empty_cache()
 

@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
         "md_autotune_system": ([_P, _S, _V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _V],
                                ctypes.c_int),
         "md_step_verlet": ([_P, _S, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _V], ctypes.c_int),
+        "md_step_verlet_host": ([_P, _S, _V, _V, _V, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _V],
+                                ctypes.c_int),
         "md_time_step_kernel": ([_P, _S, _V, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _V],
                                 ctypes.c_int),
         "md_prepare": ([_P, _S, _V, ctypes.c_int32, _V], ctypes.c_int),
@@ -219,6 +221,15 @@ def md_forces_vertex_newton(p, s, ws, stream=None):
 def md_step_verlet(p, s, ws, nsteps, path=MD_VERTEX, use_graph=True, stream=None):
     return _check(load().md_step_verlet(ctypes.byref(p), ctypes.byref(s), _ptr(ws), int(nsteps), int(path),
                                         int(bool(use_graph)), _stream(stream)))
+
+
+def md_step_verlet_host(p, s, ws, host_pos, host_vel, host_energy=None, nsteps=1, path=MD_VERTEX, use_graph=True,
+                        stream=None):
+    """md_step_verlet on a host-resident state: host_pos / host_vel are [n][3] float64 host arrays (pinned
+    torch tensors give the full copy bandwidth), read and then overwritten in stream order."""
+    return _check(load().md_step_verlet_host(ctypes.byref(p), ctypes.byref(s), _ptr(ws), _ptr(host_pos),
+                                             _ptr(host_vel), _ptr(host_energy), int(nsteps), int(path),
+                                             int(bool(use_graph)), _stream(stream)))
 
 
 def md_time_step_kernel(p, s, ws, path=MD_VERTEX, reps=20, stream=None) -> float:

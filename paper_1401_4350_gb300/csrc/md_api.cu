@@ -745,6 +745,30 @@ static const int md_tune_tpp[MD_TUNE_CANDIDATES] = {1, 1, 1, 2, 2, 2, 4, 4, 4, 8
 static const int md_tune_block[MD_TUNE_CANDIDATES] = {64, 128, 256, 64, 128, 256, 64, 128, 256, 64, 128, 256,
                                                       128, 256, 128, 256};
 
+// Host-resident state: the rows cross the host link as three FP64 words each ([n][3], x y z), and
+// these two kernels convert between that packed form and the device rows [n][4] (the fourth word, unused
+// by every kernel, is written as 0).  src/dst hold pos then vel: [2][n][3].
+__global__ void k_state_unpack(const double* __restrict__ src, double4_32a* __restrict__ pos,
+                               double4_32a* __restrict__ vel, int n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * (int64_t)n) return;
+  const double* r = src + 3 * t;
+  const double4_32a v = make_double4_32a(r[0], r[1], r[2], 0.0);
+  if (t < n) pos[t] = v;
+  else vel[t - n] = v;
+}
+
+__global__ void k_state_pack(const double4_32a* __restrict__ pos, const double4_32a* __restrict__ vel,
+                             double* __restrict__ dst, int n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * (int64_t)n) return;
+  const double4_32a v = t < n ? pos[t] : vel[t - n];
+  double* r = dst + 3 * t;
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+}
+
 extern "C" {
 
 int md_abi_version(void) { return MD_ABI_VERSION; }
@@ -923,6 +947,44 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.fxp, b.fxp, 16 * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
   }
   return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_step_verlet");
+}
+
+int md_step_verlet_host(const md_params* p, md_state* s, void* ws, double* host_pos, double* host_vel,
+                        double* host_energy, int32_t nsteps, int32_t path, int32_t use_graph, void* stream) {
+  int rc = check(p);
+  if (rc == MD_OK) rc = check_state(p, s, ws);
+  if (rc != MD_OK) return rc;
+  if (!host_pos || !host_vel) { set_error("host_pos and host_vel must be non-NULL"); return MD_ERR_INVALID; }
+  if (is_patchy(p->model)) {
+    set_error("md_step_verlet_host carries positions and velocities only: isotropic models (MD_LJ, MD_WCA)");
+    return MD_ERR_INVALID;
+  }
+  if ((rc = check_path(p, path)) != MD_OK) return rc;
+  if (nsteps < 0) { set_error("nsteps must be >= 0"); return MD_ERR_INVALID; }
+  Layout L;
+  make_layout(p, &L);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)p->n, rows = 24 * n;
+  // staging: the reorder scratch of the cell build (64 n bytes for isotropic models), which is free
+  // between the kernels of md_step_verlet
+  double* stage = (double*)((char*)ws + L.tmp_d4);
+  const int block = 256, grid = (int)((2 * n + block - 1) / block);
+  cudaError_t e = cudaMemcpyAsync(stage, host_pos, rows, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 3 * n, host_vel, rows, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_state_unpack<<<grid, block, 0, st>>>(stage, (double4_32a*)s->pos, (double4_32a*)s->vel, p->n);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "md_step_verlet_host (copy in)");
+  if ((rc = md_step_verlet(p, s, ws, nsteps, path, use_graph, stream)) != MD_OK) return rc;
+  k_state_pack<<<grid, block, 0, st>>>((const double4_32a*)s->pos, (const double4_32a*)s->vel, stage, p->n);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_pos, stage, rows, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_vel, stage + 3 * n, rows, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && host_energy)
+    e = cudaMemcpyAsync(host_energy, (char*)ws + L.pub.energy, sizeof(double) * MD_ENERGY_WORDS,
+                        cudaMemcpyDeviceToHost, st);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_step_verlet_host (copy out)");
 }
 
 int md_time_step_kernel(const md_params* p, md_state* s, void* ws, int32_t path, int32_t reps, float* ms_out,

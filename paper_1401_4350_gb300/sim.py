@@ -148,6 +148,24 @@ class Simulation:
     def step(self, nsteps: int, path=B.MD_VERTEX, use_graph=True):
         B.md_step_verlet(self.params, self.state(), self.ws, nsteps, path, use_graph, self._st())
 
+    def step_host(self, host_pos, host_vel, nsteps: int, path=B.MD_VERTEX, use_graph=True, host_energy=None):
+        """nsteps with the state in host memory: host_pos / host_vel are contiguous [n][3] float64 CPU tensors
+        (pinned for full bandwidth) in slot order, read and overwritten in stream order (synchronise the
+        stream before reading them); host_energy, if given, receives the MD_ENERGY_WORDS energy words."""
+        for t in (host_pos, host_vel):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or tuple(t.shape) != (self.system.n, 3) or not t.is_contiguous():
+                raise ValueError("host_pos and host_vel must be contiguous [n][3] float64 CPU tensors")
+        B.md_step_verlet_host(self.params, self.state(), self.ws, host_pos, host_vel, host_energy, nsteps, path,
+                              use_graph, self._st())
+
+    def slot_state_host(self, pin=True):
+        """The current (pos, vel) as [n][3] float64 CPU tensors in slot order, the layout step_host takes."""
+        pos = torch.empty((self.system.n, 3), dtype=torch.float64, pin_memory=pin)
+        vel = torch.empty((self.system.n, 3), dtype=torch.float64, pin_memory=pin)
+        pos.copy_(self.pos[:, :3])
+        vel.copy_(self.vel[:, :3])
+        return pos, vel
+
     def status(self):
         return B.md_read_status(self.params, self.ws, self._st())
 

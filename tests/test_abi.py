@@ -210,6 +210,25 @@ def test_newton_path_needs_copies(lib):
     assert "path must be" in B.last_error()
 
 
+def test_step_verlet_host_validation(lib):
+    """md_step_verlet_host refuses on the host, before any copy: missing host arrays, patchy models, bad
+    paths and step counts."""
+    fake = 1 << 20
+    st = B.md_state(fake, fake, 0, 0, fake)
+    f = B.load().md_step_verlet_host
+    p = _lj_params()
+    h = ctypes.c_void_p(1 << 21)
+    args = lambda hp, hv, nsteps=1, path=B.MD_VERTEX: (ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(fake), hp, hv,
+                                                       None, nsteps, path, 1, None)
+    assert f(*args(None, h)) == B.MD_ERR_INVALID and "host_pos" in B.last_error()
+    assert f(*args(h, None)) == B.MD_ERR_INVALID and "host_vel" in B.last_error()
+    assert f(*args(h, h, nsteps=-1)) == B.MD_ERR_INVALID and "nsteps" in B.last_error()
+    assert f(*args(h, h, path=9)) == B.MD_ERR_INVALID and "path" in B.last_error()
+    p = make_params(systems.make_patchy(2000, 0.3, seed=3), B.MD_MIXED)
+    st = B.md_state(fake, fake, fake, fake, fake)
+    assert f(*args(h, h)) == B.MD_ERR_INVALID and "isotropic" in B.last_error()
+
+
 def _grid_params(ncell):
     p = _lj_params(500)
     p.n = 2000000  # the grid is capped at 4 n + 27 cells; no memory is allocated here
