@@ -353,22 +353,22 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
 /*
  * md_step_verlet_host -- md_step_verlet for a caller whose state lives in host memory (Sec. Methods:
  * the same velocity-Verlet steps; only where the state is kept differs).  In stream order on `stream`:
- * copies host_pos and host_vel in, runs md_step_verlet(p, s, ws, nsteps, path, use_graph, stream),
- * and copies the new positions and velocities back into the same host arrays, and the MD_ENERGY_WORDS
+ * brings host_pos and host_vel in, runs md_step_verlet(p, s, ws, nsteps, path, use_graph, stream),
+ * and writes the new positions and velocities back into the same host arrays, and the MD_ENERGY_WORDS
  * energy words into host_energy (if not NULL).
  *   host_pos, host_vel  [n][3] FP64 (x, y, z), row k = slot k of the workspace (particle s->id[k]).
  *                       A rebuild inside the call reorders the slots, so what comes back is in the
  *                       new slot order; passing it back unchanged continues the run.  Page-locked
- *                       memory gives the full copy bandwidth; pageable memory makes the copies
- *                       synchronous.  The caller keeps ownership and must not touch the arrays until
- *                       the stream has been synchronised.
+ *                       arrays (cudaHostAlloc, cudaHostRegister) are read and written by the library's
+ *                       kernels directly over the host link; pageable arrays are copied through a
+ *                       staging area of the workspace (synchronous copies).  The caller keeps
+ *                       ownership and must not touch the arrays until the stream has been synchronised.
  *   s->pos, s->vel      device rows [n][4]: overwritten with the host state (fourth word 0), and
  *                       holding the new state afterwards as after md_step_verlet.
  * Same preconditions as md_step_verlet: the workspace's cells, lists and forces must be current for the
- * state being passed in (md_prepare, or the previous call of either function on this state).  The
- * copies are staged through the cell build's scratch in the workspace; isotropic models only
- * (MD_ERR_INVALID for patchy models, whose orientations this call does not carry).  Returns MD_OK,
- * MD_ERR_INVALID (host-side checks, nothing enqueued) or MD_ERR_CUDA.
+ * state being passed in (md_prepare, or the previous call of either function on this state).  Isotropic
+ * models only (MD_ERR_INVALID for patchy models, whose orientations this call does not carry).  Returns
+ * MD_OK, MD_ERR_INVALID (host-side checks, nothing enqueued) or MD_ERR_CUDA.
  */
 int md_step_verlet_host(const md_params* p, md_state* s, void* ws, double* host_pos, double* host_vel,
                         double* host_energy, int32_t nsteps, int32_t path, int32_t use_graph, void* stream);

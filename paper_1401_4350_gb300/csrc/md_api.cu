@@ -747,26 +747,40 @@ static const int md_tune_block[MD_TUNE_CANDIDATES] = {64, 128, 256, 64, 128, 256
 
 // Host-resident state: the rows cross the host link as three FP64 words each ([n][3], x y z), and
 // these two kernels convert between that packed form and the device rows [n][4] (the fourth word, unused
-// by every kernel, is written as 0).  src/dst hold pos then vel: [2][n][3].
-__global__ void k_state_unpack(const double* __restrict__ src, double4_32a* __restrict__ pos,
-                               double4_32a* __restrict__ vel, int n) {
+// by every kernel, is written as 0).  One thread per FP64 word of the packed arrays (m = 3 n words
+// each, pos then vel), so a warp reads or writes 256 contiguous bytes of them.  The packed side is either
+// the caller's page-locked host memory itself (through its device address) or a staging copy in the
+// workspace.
+__global__ void k_state_in(const double* __restrict__ src_pos, const double* __restrict__ src_vel,
+                           double* __restrict__ pos, double* __restrict__ vel, int64_t m) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * (int64_t)n) return;
-  const double* r = src + 3 * t;
-  const double4_32a v = make_double4_32a(r[0], r[1], r[2], 0.0);
-  if (t < n) pos[t] = v;
-  else vel[t - n] = v;
+  if (t >= 2 * m) return;
+  const bool second = t >= m;
+  const int64_t k = second ? t - m : t;
+  const double x = (second ? src_vel : src_pos)[k];
+  double* d = (second ? vel : pos) + 4 * (k / 3) + k % 3;
+  d[0] = x;
+  if (k % 3 == 2) d[1] = 0.0;
 }
 
-__global__ void k_state_pack(const double4_32a* __restrict__ pos, const double4_32a* __restrict__ vel,
-                             double* __restrict__ dst, int n) {
+__global__ void k_state_out(const double* __restrict__ pos, const double* __restrict__ vel,
+                            double* __restrict__ dst_pos, double* __restrict__ dst_vel, int64_t m) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * (int64_t)n) return;
-  const double4_32a v = t < n ? pos[t] : vel[t - n];
-  double* r = dst + 3 * t;
-  r[0] = v.x;
-  r[1] = v.y;
-  r[2] = v.z;
+  if (t >= 2 * m) return;
+  const bool second = t >= m;
+  const int64_t k = second ? t - m : t;
+  (second ? dst_vel : dst_pos)[k] = (second ? vel : pos)[4 * (k / 3) + k % 3];
+}
+
+// The device address of host memory that kernels can read and write directly (page-locked by
+// cudaHostAlloc or cudaHostRegister), else NULL (pageable memory, or not host memory).
+static void* host_device_view(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 extern "C" {
@@ -965,26 +979,38 @@ int md_step_verlet_host(const md_params* p, md_state* s, void* ws, double* host_
   make_layout(p, &L);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = (size_t)p->n, rows = 24 * n;
-  // staging: the reorder scratch of the cell build (64 n bytes for isotropic models), which is free
-  // between the kernels of md_step_verlet
-  double* stage = (double*)((char*)ws + L.tmp_d4);
-  const int block = 256, grid = (int)((2 * n + block - 1) / block);
-  cudaError_t e = cudaMemcpyAsync(stage, host_pos, rows, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(stage + 3 * n, host_vel, rows, cudaMemcpyHostToDevice, st);
+  const int64_t m = 3 * (int64_t)n;
+  const int block = 256, grid = (int)((2 * m + block - 1) / block);
+  // page-locked arrays are read and written by the kernels themselves; pageable ones are copied through
+  // the reorder scratch of the cell build (64 n bytes for isotropic models, free between the kernels of
+  // md_step_verlet)
+  double* const dev_pos = (double*)host_device_view(host_pos);
+  double* const dev_vel = (double*)host_device_view(host_vel);
+  const bool direct = dev_pos && dev_vel;
+  double* const stage = (double*)((char*)ws + L.tmp_d4);
+  double* const in_pos = direct ? dev_pos : stage;
+  double* const in_vel = direct ? dev_vel : stage + m;
+  cudaError_t e = cudaSuccess;
+  if (!direct) {
+    e = cudaMemcpyAsync(stage, host_pos, rows, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage + m, host_vel, rows, cudaMemcpyHostToDevice, st);
+  }
   if (e == cudaSuccess) {
-    k_state_unpack<<<grid, block, 0, st>>>(stage, (double4_32a*)s->pos, (double4_32a*)s->vel, p->n);
+    k_state_in<<<grid, block, 0, st>>>(in_pos, in_vel, s->pos, s->vel, m);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess) return cuda_fail(e, "md_step_verlet_host (copy in)");
+  if (e != cudaSuccess) return cuda_fail(e, "md_step_verlet_host (state in)");
   if ((rc = md_step_verlet(p, s, ws, nsteps, path, use_graph, stream)) != MD_OK) return rc;
-  k_state_pack<<<grid, block, 0, st>>>((const double4_32a*)s->pos, (const double4_32a*)s->vel, stage, p->n);
+  k_state_out<<<grid, block, 0, st>>>(s->pos, s->vel, in_pos, in_vel, m);
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host_pos, stage, rows, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host_vel, stage + 3 * n, rows, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && !direct) {
+    e = cudaMemcpyAsync(host_pos, stage, rows, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_vel, stage + m, rows, cudaMemcpyDeviceToHost, st);
+  }
   if (e == cudaSuccess && host_energy)
     e = cudaMemcpyAsync(host_energy, (char*)ws + L.pub.energy, sizeof(double) * MD_ENERGY_WORDS,
                         cudaMemcpyDeviceToHost, st);
-  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_step_verlet_host (copy out)");
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "md_step_verlet_host (state out)");
 }
 
 int md_time_step_kernel(const md_params* p, md_state* s, void* ws, int32_t path, int32_t reps, float* ms_out,
