@@ -45,6 +45,10 @@ MUTANTS = {
     "thermostat_selection_inverted": ("if (!(u < th->prob)) continue;", "if (u < th->prob) continue;"),
     "box_muller_radius": ("double r = sqrt(-2.0 * log(unit_open(a)));", "double r = sqrt(-log(unit_open(a)));"),
     "philox_round_count": ("for (int r = 0; r < 10; r++) {\n    uint64_t p0", "for (int r = 0; r < 9; r++) {\n    uint64_t p0"),
+    "philox_multiplier": ("(uint64_t)0xD2511F53u * c0", "(uint64_t)0xD2511F55u * c0"),
+    "philox_weyl_constant": ("k0 += 0x9E3779B9u;", "k0 += 0x9E3779BBu;"),
+    "philox_output_word_order": ("out[0] = c0; out[1] = c1;", "out[0] = c1; out[1] = c0;"),
+    "philox_key_word_mixed": ("c2 = hi0 ^ c3 ^ k1;", "c2 = hi0 ^ c3 ^ k0;"),
 }
 
 FAST_PINS = [
@@ -70,14 +74,11 @@ FAST_PINS = [
     lambda: [pow_pins.test_refresh_sets_maxwell_boltzmann_momenta_from_the_draws(k) for k in ("lj", "pow")],
     pow_pins.test_refresh_probability_and_schedule,
     pow_pins.test_thermostat_normals_are_standard,
+    pow_pins.test_philox_known_answer_vectors,
 ]
 
-# Philox itself is only pinned statistically (and bit for bit against the GPU); a changed round count
-# still looks random, so that one mutant must be caught by the GPU comparison instead.
-GPU_ONLY = {"philox_round_count"}
 
-
-@pytest.mark.parametrize("name", sorted(set(MUTANTS) - GPU_ONLY))
+@pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path):
     before, after = MUTANTS[name]
     src = open(SRC).read()
