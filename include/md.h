@@ -361,7 +361,9 @@ int md_step_verlet(const md_params* p, md_state* s, void* ws, int32_t nsteps, in
  *                       new slot order; passing it back unchanged continues the run.  Page-locked
  *                       arrays (cudaHostAlloc, cudaHostRegister) are read and written by the library's
  *                       kernels directly over the host link; pageable arrays are copied through a
- *                       staging area of the workspace (synchronous copies).  The caller keeps
+ *                       staging area of the workspace (synchronous copies).  Device or managed
+ *                       allocations are rejected with MD_ERR_INVALID (their state belongs in s->pos,
+ *                       s->vel and md_step_verlet).  The caller keeps
  *                       ownership and must not touch the arrays until the stream has been synchronised.
  *   s->pos, s->vel      device rows [n][4]: overwritten with the host state (fourth word 0), and
  *                       holding the new state afterwards as after md_step_verlet.
@@ -504,6 +506,9 @@ int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream);
  * Limit: n <= MD_STATIC_MAX_N, else MD_ERR_INVALID with a message.  The call allocates nothing
  * (no cudaMalloc, cudaFree or allocating library routine).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * The address is cached per device together with the id of the CUDA context it was taken in; a call
+ * made in another context (after cudaDeviceReset, or once the primary context was released and created
+ * again) looks it up anew, since the array may then sit elsewhere.
  * All calls share the one array, which keeps the last call's contents (the counts that must start at
  * zero are cleared by each call): calls whose kernels may overlap on the GPU race and must be
  * serialised by the caller.

@@ -774,13 +774,24 @@ __global__ void k_state_out(const double* __restrict__ pos, const double* __rest
 
 // The device address of host memory that kernels can read and write directly (page-locked by
 // cudaHostAlloc or cudaHostRegister), else NULL (pageable memory, or not host memory).
-static void* host_device_view(const void* p) {
+// What kind of memory a caller's host array is: page-locked host memory (its device address in *view),
+// pageable host memory (*view = null: it goes through staging copies), or memory that is not host memory
+// at all (device or managed allocations: MD_ERR_INVALID, since the staging copies are host-to-device and
+// device-to-host copies and would be undefined for them).
+static int host_device_view(const void* p, const char* name, void** view) {
+  *view = nullptr;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    return MD_OK;  // not known to CUDA: pageable host memory
   }
-  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    set_error("%s is %s memory; md_step_verlet_host takes host arrays (use md_step_verlet for device state)", name,
+              at.type == cudaMemoryTypeDevice ? "device" : "managed");
+    return MD_ERR_INVALID;
+  }
+  if (at.type == cudaMemoryTypeHost) *view = at.devicePointer;
+  return MD_OK;
 }
 
 extern "C" {
@@ -984,8 +995,12 @@ int md_step_verlet_host(const md_params* p, md_state* s, void* ws, double* host_
   // page-locked arrays are read and written by the kernels themselves; pageable ones are copied through
   // the reorder scratch of the cell build (64 n bytes for isotropic models, free between the kernels of
   // md_step_verlet)
-  double* const dev_pos = (double*)host_device_view(host_pos);
-  double* const dev_vel = (double*)host_device_view(host_vel);
+  void *view_pos = nullptr, *view_vel = nullptr;
+  if ((rc = host_device_view(host_pos, "host_pos", &view_pos)) != MD_OK ||
+      (rc = host_device_view(host_vel, "host_vel", &view_vel)) != MD_OK)
+    return rc;
+  double* const dev_pos = (double*)view_pos;
+  double* const dev_vel = (double*)view_vel;
   const bool direct = dev_pos && dev_vel;
   double* const stage = (double*)((char*)ws + L.tmp_d4);
   double* const in_pos = direct ? dev_pos : stage;

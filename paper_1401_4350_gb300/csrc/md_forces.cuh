@@ -131,14 +131,19 @@ __device__ __forceinline__ PairOut<R> iso_pair(const KArgs& a, const Vec3<R>& d,
 }
 
 // Cubic boxes, fixed-point units u = L / 2^32.  The squared separation is the exact 64-bit integer
-// sum of squares of the coordinate differences, rounded once to FP32: the steep repulsive core
+// sum of squares of the coordinate differences, converted to FP32 (one rounding, or two in boxes
+// smaller than 16 rv: see below): the steep repulsive core
 // multiplies the relative error of r^2 by up to ~10 in the force, so r^2 is not formed from rounded
 // components.
 __device__ __forceinline__ float exact_r2u(int dx, int dy, int dz) {
   const unsigned long long s = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
                                (unsigned long long)((long long)dz * dz);
-  // hi * 2^32 + lo with one rounding: hi < 2^24 (exact in FP32) whenever the pair is within a few
-  // rv of a box edge of more than ~5 rv, and lo's conversion error (< 2^8) is far below ulp(s)
+  // hi * 2^32 + lo.  s = |d|^2 2^64 / L^2, so hi < 2^24 (exact in FP32) iff |d| < L / 16: for every
+  // list pair (|d| < rv) when the box edge exceeds 16 rv, and then the sum carries one rounding (lo's
+  // conversion error, < 2^7, is far below ulp(s)).  In smaller boxes hi itself may round first, so r^2
+  // carries at most two roundings, a relative error below 2^-23 = 1.2e-7: far inside the 1e-5 relative
+  // band around rc^2 in which the cut-off is decided again in FP64, and of the order of the FP32 pair
+  // arithmetic's own roundings in the force.
   const unsigned hi = (unsigned)(s >> 32), lo = (unsigned)s;
   return __fmaf_rn(__uint2float_rn(hi), 4294967296.0f, __uint2float_rn(lo));
 }

@@ -13,6 +13,8 @@
 // leaves the previous call's contents in it; the counts that must start at zero are cleared by each
 // call.  Calls whose kernels overlap on the GPU (different streams, or different host threads on
 // one device) race on the array and must be serialised by the caller.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "md_internal.cuh"
@@ -32,9 +34,45 @@ constexpr size_t kStaticBytes = kStaticD4 + kStaticCount + 4 * kStaticInts + kSt
 static __device__ __align__(256) unsigned char g_cells_scratch[kStaticBytes];
 
 static std::mutex g_static_mu;
-static void* g_static_ptr[256] = {};
+struct StaticSlot {
+  void* ptr;                  // device address of the array in the context below
+  unsigned long long ctx_id;  // that context's id (0: unknown, look the address up on every call)
+};
+static StaticSlot g_static_slot[256] = {};
 
-// Device address of the scratch on the current device (looked up on the first call per device).
+// Id of the context current on this thread, or 0 when it cannot be read.  The array lives in the copy of
+// this library's device code loaded into a context; a device reset, or a primary context released and
+// created again, loads it anew, possibly at another address, and the new context has another id.  The
+// driver calls are reached through the runtime's entry-point lookup, so the library needs no link-time
+// dependency on the driver library.
+static unsigned long long current_context_id() {
+  typedef CUresult (*get_current_t)(CUcontext*);
+  typedef CUresult (*get_id_t)(CUcontext, unsigned long long*);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (get_current_t)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (get_id_t)f;
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch in the context current on this thread: looked up with
+// cudaGetSymbolAddress on the first call per device, and again whenever the current context is not the
+// one the cached address was taken in.
 static int static_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -47,16 +85,19 @@ static int static_scratch(void** out) {
     return MD_ERR_INVALID;
   }
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  StaticSlot& slot = g_static_slot[dev];
+  const unsigned long long ctx = current_context_id();
+  if (!slot.ptr || ctx == 0 || ctx != slot.ctx_id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_cells_scratch);
+    e = cudaGetSymbolAddress(&p, g_cells_scratch);  // makes the device's primary context current if none is
     if (e != cudaSuccess || p == nullptr) {
       set_error("md_build_cells_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
       return MD_ERR_CUDA;
     }
-    g_static_ptr[dev] = p;
+    slot.ptr = p;
+    slot.ctx_id = current_context_id();
   }
-  *out = g_static_ptr[dev];
+  *out = slot.ptr;
   return MD_OK;
 }
 

@@ -64,3 +64,22 @@ def test_zero_steps_round_trip():
     torch.cuda.synchronize()
     assert torch.equal(hp, hp0) and torch.equal(hv, hv0)
     assert torch.equal(sim.pos[:, :3].cpu(), hp0)
+
+
+def test_device_arrays_are_rejected():
+    """Device (or managed) arrays are not host arrays: the call refuses them before enqueueing anything,
+    instead of staging them through host-to-device copies of the wrong kind."""
+    s = systems.make_lj(4000, 0.85, 1.0, seed=14)
+    sim = Simulation(s, B.MD_MIXED)
+    sim.prepare(B.MD_VERTEX)
+    dp = sim.pos[:, :3].contiguous()
+    dv = sim.vel[:, :3].contiguous()
+    pos0 = sim.pos.clone()
+    with pytest.raises(B.MDError) as err:
+        B.md_step_verlet_host(sim.params, sim.state(), sim.ws, dp, dv, None, 1, B.MD_VERTEX, True, sim._st())
+    assert err.value.code == B.MD_ERR_INVALID and "device" in str(err.value)
+    hp, hv = sim.slot_state_host()
+    with pytest.raises(B.MDError):
+        B.md_step_verlet_host(sim.params, sim.state(), sim.ws, hp, dv, None, 1, B.MD_VERTEX, True, sim._st())
+    torch.cuda.synchronize()
+    assert torch.equal(sim.pos, pos0) and sim.status()[B.MD_STATUS_STEPS] == 0

@@ -23,7 +23,11 @@ def _lib():
     B.load()
 
 
-def _static_build(s, precision):
+def _static_build(s, precision, stream=None):
+    """Runs md_build_cells_static twice on one copy of the state (on `stream`, default the current stream)
+    and md_build_cells once on another, and checks that the results agree bit for bit, and that the
+    second call changed the device's free memory by nothing (the first may load the library's device
+    code, and with it the static array, into the context)."""
     import torch
     from paper_1401_4350_gb300.sim import Simulation
     ref = Simulation(s, precision)  # the ordinary entry point, with a workspace
@@ -36,8 +40,15 @@ def _static_build(s, precision):
     if s.kind == systems.PATCHY:
         patch_lab = torch.zeros((s.n, B.MD_MAX_PATCH, 8 if precision == B.MD_FP64 else 4),
                                 dtype=torch.float32 if precision == B.MD_FP64 else torch.int32, device="cuda")
-    B.md_build_cells_static(mine.params, mine.state(), cell_start, fxp, patch_lab)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    B.md_build_cells_static(mine.params, mine.state(), cell_start, fxp, patch_lab, st)
     torch.cuda.synchronize()
+    # a second call on the state the first one sorted: the build is deterministic and a sorted state
+    # sorts to itself, so the result is the same; it must not allocate
+    free0 = torch.cuda.mem_get_info()[0]
+    B.md_build_cells_static(mine.params, mine.state(), cell_start, fxp, patch_lab, st)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     assert torch.equal(mine.pos, ref.pos) and torch.equal(mine.vel, ref.vel) and torch.equal(mine.id, ref.id)
     if s.kind == systems.PATCHY:
         assert torch.equal(mine.quat, ref.quat) and torch.equal(mine.angmom, ref.angmom)
@@ -45,6 +56,7 @@ def _static_build(s, precision):
         assert torch.equal(patch_lab.view(torch.uint8).flatten(), ref.view("patch_lab", torch.uint8, nb))
     assert torch.equal(cell_start, ref.view("cell_start", torch.int32, ncell + 1))
     assert torch.equal(fxp.flatten(), ref.view("fxp", torch.int32, 4 * s.n))
+    return ncell
 
 
 @pytest.mark.parametrize("precision", [B.MD_MIXED, B.MD_FP64])
@@ -57,6 +69,16 @@ def test_static_cell_build_matches_workspace_build_twice(precision):
 def test_static_cell_build_patchy():
     for prec in (B.MD_MIXED, B.MD_FP64):
         _static_build(systems.make_patchy(2500, 0.3, seed=62), prec)
+
+
+def test_static_cell_build_at_its_limits_on_a_side_stream():
+    """n = MD_STATIC_MAX_N in a gas so dilute that the cell grid is capped (4 n + 27 cells): the largest
+    particle and cell counts the static array is sized for, on a stream other than the default one."""
+    import torch
+    s = systems.make_wca(B.MD_STATIC_MAX_N, 0.005, seed=64)
+    side = torch.cuda.Stream()
+    ncell = _static_build(s, B.MD_MIXED, stream=side)
+    assert 2 * s.n < ncell <= 4 * s.n + 27
 
 
 def test_static_cell_build_rejects_sizes_beyond_its_limit():
