@@ -199,7 +199,8 @@ typedef struct md_ws_layout {
   size_t cell_start;     /* int32[ncells + 1]: first slot of each cell (cell-sorted order)     */
   size_t fxp;            /* uint32[n][4]: positions as fractions of the box edge times 2^32   */
   size_t fxp_build;      /* uint32[n][4]: the same at the last Verlet build                   */
-  size_t patch_lab;      /* float[n][MD_MAX_PATCH][4]: lab-frame patch sites (patchy, mixed)  */
+  size_t patch_lab;      /* lab-frame patch sites (patchy): double4 [n][MD_MAX_PATCH] (FP64); mixed:
+                            int4 [n][MD_MAX_PATCH] fixed-point offsets, then the double4 block   */
   size_t nbr;            /* int32[ceil(max_neigh/4)][n][4]: full list; entry k of slot i at ((k/4)*n+i)*4+k%4.
                             Block-local format: uint16 at the same entry position; the Newton list:
                             the same layout with the rows of md_forces_vertex_newton              */
@@ -502,7 +503,8 @@ int md_autotune(void* ws, int32_t* path_out, int32_t* tpp_out, void* stream);
  * place, as by md_build_cells) and the outputs:
  *   cell_start  int32[ncell_total + 1]  (ncell from md_workspace_layout)
  *   fxp         uint32[n][4], 16-byte aligned
- *   patch_lab   patchy only: [n][MD_MAX_PATCH] int4 (MD_MIXED) or double4 (MD_FP64), 32-byte aligned
+ *   patch_lab   patchy only, 32-byte aligned: [n][MD_MAX_PATCH] double4 (MD_FP64); MD_MIXED: [n][MD_MAX_PATCH]
+ *               int4 fixed-point sites followed by [n][MD_MAX_PATCH] double4 (64 + 128 bytes per particle)
  * Limit: n <= MD_STATIC_MAX_N, else MD_ERR_INVALID with a message.  The call allocates nothing
  * (no cudaMalloc, cudaFree or allocating library routine).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress), so make that first call before any stream capture.

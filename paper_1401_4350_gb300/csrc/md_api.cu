@@ -176,7 +176,8 @@ static void make_layout(const md_params* p, Layout* L) {
   cell_dims(p, nc);
   const size_t n = (size_t)p->n;
   const size_t ncell = (size_t)nc[0] * nc[1] * nc[2];
-  const size_t fe = p->precision == MD_MIXED ? 4 : 8;  // patch sites: int4 (mixed) or double4
+  // patch sites: double4 (FP64); mixed: int4 fixed-point offsets, followed by the double4 block
+  const size_t fe = p->precision == MD_MIXED ? 12 : 8;
   const bool patchy = is_patchy(p->model);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -321,9 +322,6 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     a.eps_p_d = p->eps_p;
     a.pgain_d = 5.0 * p->eps_p / (p->delta * p->delta);
     a.inv_delta2_f = f32(a.inv_delta2_d);
-    a.eps_p_f = f32(a.eps_p_d);
-    a.pgain_f = f32(a.pgain_d);
-    a.half_log2e_f = f32(-0.5 / log(2.0));
     double R = 0.0;
     for (int k = 0; k < p->n_patch; k++) {
       const double r = sqrt(p->patch[k][0] * p->patch[k][0] + p->patch[k][1] * p->patch[k][1] +
@@ -331,23 +329,25 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
       if (r > R) R = r;
       for (int c = 0; c < 3; c++) a.patch_body[k][c] = p->patch[k][c];
     }
-    // every patch term is exactly zero once (r_ab / delta)^10 exceeds 177.4 (FP32: exp2 argument
-    // below -128, flushed) or 1600 (FP64: exp argument below -800, underflow)
+    // patch terms beyond (r_ab / delta)^10 = 177.4 (exp(-q^5 / 2) < 2^-128: force, torque and energy below
+    // 1e-34) are skipped in mixed precision; beyond 1600 every FP64 term is exactly zero (exp underflow)
     double reach_f = 2.0 * R + p->delta * pow(128.0 * 2.0 * log(2.0), 0.1);
     double reach_d = 2.0 * R + p->delta * pow(1600.0, 0.1);
-    a.patch_qcut_f = 3.0e38f;
     a.patch_qcut_d = 1.0e300;
     if (p->model == MD_PATCHY_POW) {
       // truncated patch pairs: nothing beyond r_ab = patch_rc, so no centre pair beyond 2 R + patch_rc
       a.pow_core = 1;
       const double q = (p->patch_rc / p->delta) * (p->patch_rc / p->delta);
       a.patch_qcut_d = q;
-      a.patch_qcut_f = f32(q);
       if (2.0 * R + p->patch_rc < reach_f) reach_f = 2.0 * R + p->patch_rc;
       if (2.0 * R + p->patch_rc < reach_d) reach_d = 2.0 * R + p->patch_rc;
     }
     a.patch_reach2_f = f32(reach_f * reach_f);
     a.patch_reach2_d = reach_d * reach_d;
+    // mixed precision: a patch pair goes on to its FP64 evaluation when its FP32 q = (r_ab / delta)^2 is
+    // below the smaller of the FP32 zero point (q^5 = 177.4) and the truncation, widened by 1e-5 so that
+    // the FP64 decision is the one that counts
+    a.patch_q32_f = f32(fmin(pow(128.0 * 2.0 * log(2.0), 0.2), a.patch_qcut_d) * (1.0 + 1e-5));
   }
   a.thermo_every = p->thermostat_every;
   a.seed = p->seed;
@@ -387,6 +387,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     a.fxp_prune = (uint4*)(w + L.pub.fxp_prune);
   }
   a.patch_lab = (void*)(w + L.pub.patch_lab);
+  set_patch_sites(a, a.patch_lab);
   a.nbr = (int32_t*)(w + L.pub.nbr);
   a.nbr_count = (int32_t*)(w + L.pub.nbr_count);
   a.half_start = (int64_t*)(w + L.pub.half_start);
@@ -425,7 +426,7 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
   a.pos_alt = nullptr; a.fxp_alt = nullptr; a.inner = 0; a.nbr_in = nullptr; a.nbr_in_count = nullptr;
   a.fxp_prune = nullptr;
-  a.patch_lab = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
+  a.patch_lab = nullptr; a.patch_lab_d = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
   a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
   a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr; a.local_ok = 0; a.local_tab = nullptr;
   a.scr_words = nullptr; a.acc_slots = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;

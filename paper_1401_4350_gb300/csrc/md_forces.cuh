@@ -251,8 +251,15 @@ __device__ __forceinline__ PairOut<double> patchy_pair(const KArgs& a, const Vec
   return o;
 }
 
-// Mixed precision: every patch-pair separation is the exact 32-bit integer sum ds + p_b - p_a of
-// fixed-point centre difference and site offsets, converted to FP32 once; the rest is FP32.
+// Mixed precision.  Every patch-pair separation is first formed as the exact 32-bit integer sum
+// ds + p_b - p_a of fixed-point centre difference and site offsets, and q = (r_ab / delta)^2 from it in
+// FP32; a patch pair whose q shows that its term is exactly zero in FP32 (or truncated) is skipped.  The
+// few that remain (the bonds) are evaluated in FP64 from the FP64 positions and lab-frame sites:
+// (r_ab / delta)^10 multiplies the relative error of r_ab by ten, and the 2^-33 L quantisation of the
+// fixed-point coordinates alone would leave the strongest torques of a box of L = 96 sigma about 4e-5 of
+// the rms torque (over all particles) off.  In FP64 each pair's force, torques and energy carry one
+// rounding to FP32.  The centre core is FP32 (WCA) or FP64 ((sigma/r)^200, whose exponent amplifies even
+// the fixed-point quantisation of r).
 template <int NP, bool WANT_TJ>
 __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, const int3& ds, const Vec3<float>& d,
                                                             float r2, const IPatches<NP>& Pi, int i, int j) {
@@ -261,9 +268,6 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
   o.e = o.w = 0.f;
   if (!(r2 < a.rc2_f)) return o;
   if (a.pow_core) {
-    // (sigma/r)^200 multiplies the relative error of r by 200: even the 2^-33 L quantisation of the
-    // fixed-point coordinates would show, so this term is FP64 from the FP64 positions; only its
-    // result is rounded to FP32
     const Vec3<double> dd = sep_fp64(a.pos[i], a.pos[j], a);
     double fs, pe;
     pow_core_terms(a, dd.x * dd.x + dd.y * dd.y + dd.z * dd.z, fs, pe);
@@ -281,51 +285,57 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
   }
   if (r2 < a.patch_reach2_f) {
     const IPatches<NP> Pj = load_ipatches<NP>(a, j);
-    const float ux = a.fxp_unit[0], uy = a.fxp_unit[1], uz = a.fxp_unit[2];
-    Vec3<float> Fb[NP];
-#pragma unroll
-    for (int b = 0; b < NP; b++) Fb[b] = {0.f, 0.f, 0.f};
+    const double4_32a* li = a.patch_lab_d + (size_t)i * MD_MAX_PATCH;
+    const double4_32a* lj = a.patch_lab_d + (size_t)j * MD_MAX_PATCH;
+    Vec3<double> F = {0.0, 0.0, 0.0}, ti = {0.0, 0.0, 0.0}, tj = {0.0, 0.0, 0.0}, dd = {0.0, 0.0, 0.0};
+    double e = 0.0;
+    bool any = false;
 #pragma unroll
     for (int pa = 0; pa < NP; pa++) {
-      Vec3<float> Fa = {0.f, 0.f, 0.f};
       const int bx = ds.x - Pi.p[pa].x, by = ds.y - Pi.p[pa].y, bz = ds.z - Pi.p[pa].z;
 #pragma unroll
       for (int b = 0; b < NP; b++) {
         const int sx = bx + Pj.p[b].x, sy = by + Pj.p[b].y, sz = bz + Pj.p[b].z;
-        const Vec3<float> s = {(float)sx * ux, (float)sy * uy, (float)sz * uz};
         float q;
         if (a.cubic) {
-          // |s|^2 exactly in 64-bit integer units, converted once: q carries one rounding, which
-          // matters because (r/delta)^10 multiplies its relative error by five
           const unsigned long long r2i = (unsigned long long)((long long)sx * sx) +
                                          (unsigned long long)((long long)sy * sy) +
                                          (unsigned long long)((long long)sz * sz);
           q = __ull2float_rn(r2i) * a.u2_over_delta2;
         } else {
-          q = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_f;
+          const float x = (float)sx * a.fxp_unit[0], y = (float)sy * a.fxp_unit[1], z = (float)sz * a.fxp_unit[2];
+          q = (x * x + y * y + z * z) * a.inv_delta2_f;
         }
-        if (!(q < a.patch_qcut_f)) continue;  // truncated patch pair (MD_PATCHY_POW)
-        const float q2 = q * q, q4 = q2 * q2, q5 = q4 * q;
-        const float ex = fexp2_approx(a.half_log2e_f * q5);
-        o.e -= a.eps_p_f * ex;
-        const float g = a.pgain_f * q4 * ex;
-        Fa.x += g * s.x; Fa.y += g * s.y; Fa.z += g * s.z;
-        if (WANT_TJ) { Fb[b].x -= g * s.x; Fb[b].y -= g * s.y; Fb[b].z -= g * s.z; }
+        if (!(q < a.patch_q32_f)) continue;  // zero in FP32, or truncated (MD_PATCHY_POW)
+        if (!any) {
+          dd = sep_fp64(a.pos[i], a.pos[j], a);
+          any = true;
+        }
+        const double4_32a A = li[pa], Bs = lj[b];
+        const Vec3<double> s = {dd.x + Bs.x - A.x, dd.y + Bs.y - A.y, dd.z + Bs.z - A.z};
+        const double qd = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_d;
+        if (!(qd < a.patch_qcut_d)) continue;  // truncated patch pair (MD_PATCHY_POW), decided in FP64
+        const double q2 = qd * qd, q4 = q2 * q2, q5 = q4 * qd;
+        const double ex = exp(-0.5 * q5);
+        e -= a.eps_p_d * ex;
+        const double g = a.pgain_d * q4 * ex;  // force on site a: g * s
+        const Vec3<double> f = {g * s.x, g * s.y, g * s.z};
+        F.x += f.x; F.y += f.y; F.z += f.z;
+        ti.x += A.y * f.z - A.z * f.y;
+        ti.y += A.z * f.x - A.x * f.z;
+        ti.z += A.x * f.y - A.y * f.x;
+        if (WANT_TJ) {
+          tj.x -= Bs.y * f.z - Bs.z * f.y;
+          tj.y -= Bs.z * f.x - Bs.x * f.z;
+          tj.z -= Bs.x * f.y - Bs.y * f.x;
+        }
       }
-      o.F.x += Fa.x; o.F.y += Fa.y; o.F.z += Fa.z;
-      const Vec3<float> p = {(float)Pi.p[pa].x * ux, (float)Pi.p[pa].y * uy, (float)Pi.p[pa].z * uz};
-      o.ti.x += p.y * Fa.z - p.z * Fa.y;
-      o.ti.y += p.z * Fa.x - p.x * Fa.z;
-      o.ti.z += p.x * Fa.y - p.y * Fa.x;
     }
-    if (WANT_TJ) {
-#pragma unroll
-      for (int b = 0; b < NP; b++) {
-        const Vec3<float> p = {(float)Pj.p[b].x * ux, (float)Pj.p[b].y * uy, (float)Pj.p[b].z * uz};
-        o.tj.x += p.y * Fb[b].z - p.z * Fb[b].y;
-        o.tj.y += p.z * Fb[b].x - p.x * Fb[b].z;
-        o.tj.z += p.x * Fb[b].y - p.y * Fb[b].x;
-      }
+    if (any) {
+      o.F = {(float)((double)o.F.x + F.x), (float)((double)o.F.y + F.y), (float)((double)o.F.z + F.z)};
+      o.e = (float)((double)o.e + e);
+      o.ti = {(float)ti.x, (float)ti.y, (float)ti.z};
+      if (WANT_TJ) o.tj = {(float)tj.x, (float)tj.y, (float)tj.z};
     }
   }
   o.w = -(d.x * o.F.x + d.y * o.F.y + d.z * o.F.z);

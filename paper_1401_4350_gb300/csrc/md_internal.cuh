@@ -7,7 +7,8 @@
 //   pos_alt/fxp_alt      the second position / fixed-point buffers of fused steps (fuse_step = 1):
 //                        a fused launch reads pos/fxp and writes pos_alt/fxp_alt, and the next
 //                        launch runs with the two swapped
-//   patch_lab            float4 or double4_32a [n][MD_MAX_PATCH]  lab-frame patch sites
+//   patch_lab            lab-frame patch sites: double4_32a [n][MD_MAX_PATCH] (FP64); mixed: int4
+//                        [n][MD_MAX_PATCH] fixed-point offsets, then the double4_32a block
 //   nbr                  int32   [ceil(max_neigh/4)][n][4] full list: entry k of slot i at
 //                        ((k/4) n + i) 4 + k%4 (int4 groups, coalesced per warp)
 //   pairs                int2    [max_pairs]    half list (i, j), i < j, sorted by i
@@ -102,14 +103,13 @@ struct KArgs {
   double rwca2_lo_d, rwca2_hi_d;
   // patchy
   double inv_delta2_d, eps_p_d, pgain_d;  // 1/delta^2, eps_p, 5 eps_p / delta^2
-  float inv_delta2_f, eps_p_f, pgain_f;
-  float half_log2e_f;                     // -0.5 * log2(e): exp(-q5/2) = exp2(half_log2e * q5)
+  float inv_delta2_f;
   double patch_reach2_d;                  // centre distance^2 beyond which every patch term vanishes
   float patch_reach2_f;
+  float patch_q32_f;                      // mixed: FP32 q below which a patch pair is evaluated in FP64
   double patch_body[MD_MAX_PATCH][3];
   int32_t pow_core;                       // MD_PATCHY_POW: (sigma/r)^200 centre repulsion instead of WCA
-  float patch_qcut_f;                     // MD_PATCHY_POW: (patch_rc / delta)^2 (3e38: no cut-off)
-  double patch_qcut_d;
+  double patch_qcut_d;                    // MD_PATCHY_POW: (patch_rc / delta)^2 (1e300: no cut-off)
   // thermostat (momentum refresh)
   int32_t thermo_every;
   uint32_t seed;
@@ -133,6 +133,7 @@ struct KArgs {
   double4_32a* pos_alt;  // fused steps: where the drift of this launch writes (else null)
   uint4* fxp_alt;
   void* patch_lab;
+  double4_32a* patch_lab_d;  // the FP64 lab-frame sites [n][MD_MAX_PATCH] (in mixed precision after the int4 block)
   int32_t* nbr;
   int32_t* nbr_count;
   int64_t* half_start;
@@ -161,6 +162,14 @@ struct KArgs {
   double4_32a* tmp_d4;       // [4][n] gather buffers
   int32_t* tmp_i;        // [n]
 };
+
+// Where the FP64 lab-frame patch sites are in a patch_lab block of n particles: the block itself (FP64), or
+// after its [n][MD_MAX_PATCH] int4 fixed-point sites (mixed).
+inline void set_patch_sites(KArgs& a, void* patch_lab) {
+  a.patch_lab_d = !patch_lab ? nullptr
+                  : a.precision == MD_MIXED ? (double4_32a*)((char*)patch_lab + (size_t)16 * MD_MAX_PATCH * (size_t)a.n)
+                                            : (double4_32a*)patch_lab;
+}
 
 // Host-side helpers implemented in md_api.cu
 void set_error(const char* fmt, ...);
@@ -244,12 +253,6 @@ __device__ __forceinline__ double drcp_refined(double x) {
   return fma(y, fma(-x, y, 1.0), y);
 }
 
-__device__ __forceinline__ float fexp2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // Error of s = a + b (s computed in round-to-nearest): a + b = s + two_sum_err(a, b, s) exactly.
 __device__ __forceinline__ float two_sum_err(float a, float b, float s) {
   float bb = __fsub_rn(s, a);
@@ -270,9 +273,9 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float term) {
 namespace mdgb {
 
 // Lab-frame patch sites of one particle from its FP64 quaternion (w, x, y, z): p_lab = R(q) p_body,
-// computed in FP64.  MD_MIXED stores each site as a 32-bit fixed-point offset from the centre in the
-// units of the centre coordinates (box fraction times 2^32), so that a patch-pair separation
-// x_j + p_b - x_i - p_a is an exact integer sum; MD_FP64 stores the FP64 vector.
+// computed in FP64 and stored as FP64 vectors.  MD_MIXED also stores each site as a 32-bit fixed-point
+// offset from the centre in the units of the centre coordinates (box fraction times 2^32), so that a
+// patch-pair separation x_j + p_b - x_i - p_a is an exact integer sum for the FP32 screening of pairs.
 __device__ __forceinline__ void write_patch_lab(const KArgs& a, int i, const double4_32a& q) {
   const double w = q.x, x = q.y, y = q.z, z = q.w;
   const double R[3][3] = {{1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y)},
@@ -288,10 +291,8 @@ __device__ __forceinline__ void write_patch_lab(const KArgs& a, int i, const dou
       int4* out = (int4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
       out[p] = make_int4((int)to_fixed(v[0], a.fxp_scale[0]), (int)to_fixed(v[1], a.fxp_scale[1]),
                          (int)to_fixed(v[2], a.fxp_scale[2]), 0);
-    } else {
-      double4_32a* out = (double4_32a*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
-      out[p] = make_double4_32a(v[0], v[1], v[2], 0.0);
     }
+    a.patch_lab_d[(size_t)i * MD_MAX_PATCH + p] = make_double4_32a(v[0], v[1], v[2], 0.0);
   }
 }
 

@@ -157,6 +157,7 @@ extern "C" int md_build_cells_static(const md_params* p, md_state* s, int32_t* c
   a.cell_start = cell_start;
   a.fxp = (uint4*)fxp;
   a.patch_lab = patch_lab;
+  set_patch_sites(a, patch_lab);
   cudaError_t e = launch_build_cells(a, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     set_error("md_build_cells_static: %s", cudaGetErrorString(e));

@@ -68,7 +68,7 @@ def test_edge_store_forces_match_oracle(name, precision):
         assert E.sum() == pytest.approx(Ur, rel=1e-5, abs=1e-5 * s.n)
         assert W.sum() == pytest.approx(Wr, rel=1e-5, abs=1e-5 * s.n)
         if T is not None:
-            check_mixed(T, Tr, "torque", over_nonzero=True)
+            check_mixed(T, Tr, "torque")
 
 
 @pytest.mark.parametrize("precision", [B.MD_FP64, B.MD_MIXED])

@@ -75,7 +75,7 @@ def test_hilbert_forces_match_oracle(name, precision, path):
     else:
         check_mixed(F, Fr, "force")
         if T is not None:
-            check_mixed(T, Tr, "torque", over_nonzero=True)
+            check_mixed(T, Tr, "torque")
 
 
 def test_hilbert_steps_follow_row_major_steps():

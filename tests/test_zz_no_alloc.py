@@ -38,7 +38,9 @@ def _static_build(s, precision, stream=None):
     fxp = torch.zeros((s.n, 4), dtype=torch.int32, device="cuda")
     patch_lab = None
     if s.kind == systems.PATCHY:
-        patch_lab = torch.zeros((s.n, B.MD_MAX_PATCH, 8 if precision == B.MD_FP64 else 4),
+        # FP64: double4 sites; mixed: int4 fixed-point sites, then the double4 block (12 words per site)
+        rows = s.n if precision == B.MD_FP64 else 3 * s.n
+        patch_lab = torch.zeros((rows, B.MD_MAX_PATCH, 8 if precision == B.MD_FP64 else 4),
                                 dtype=torch.float32 if precision == B.MD_FP64 else torch.int32, device="cuda")
     st = stream if stream is not None else torch.cuda.current_stream()
     B.md_build_cells_static(mine.params, mine.state(), cell_start, fxp, patch_lab, st)
