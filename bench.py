@@ -69,7 +69,7 @@ class ClockSampler:
     def start(self):
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "50"]
             if self.uuid:
                 cmd += ["-i", self.uuid]
             self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
@@ -123,6 +123,23 @@ FUSED_BYTES_PER_PARTICLE = 180
 # Inner-list margin of the headline: pairs closer than rc + PRUNE_SKIN, pruned when a particle has moved
 # PRUNE_SKIN / 2 (measured at LJ 1M: 0.1 is the fastest of 0.05 ... 0.16)
 PRUNE_SKIN = 0.1
+# The headline runs in the liquid: fused steps from the initial lattice before anything is timed
+# (at LJ 1M about 0.25 s), whatever --warmup asks for beyond them.
+EQUILIBRATE_STEPS = 1000
+# Steady-state figure: the median of STEADY_REPEATS runs of STEADY_STEPS graph steps each, rebuilds and
+# prunes included (a rebuild comes about every 36 steps at LJ 1M, a prune about every 12).
+STEADY_REPEATS = 5
+STEADY_STEPS = 300
+# FP64 operations (DADD, DMUL, DFMA) of one LJ pair evaluation: 32, measured by ncu on the vertex kernel
+# (sum of the three thread-instruction counters over the list entries of the launch, LJ N = 262,144;
+# profiles/fp64_kernels_lj262k.md).  The vertex kernel evaluates every full-list entry (each pair twice),
+# the edge kernel each pair once (its segmented FP64 sums, about 27 more operations per pair, are not pair
+# arithmetic and are not counted).
+FP64_OPS_PER_PAIR_EVAL_LJ = 32
+# The FP64 pipe of GB300: 2 DFMA per clock per SM (ncu's peak_sustained of the DFMA counter, 304 per cycle
+# over 152 SMs); 1.67 was reached by a dependent-free DFMA microbenchmark.
+FP64_PER_CLK_SM = 2.0
+N_SM = 152
 
 
 def algorithmic_bytes_force(path: int, precision: int, n: int, full_entries: int, pairs: int) -> float:
@@ -132,13 +149,19 @@ def algorithmic_bytes_force(path: int, precision: int, n: int, full_entries: int
         # count 4 + own coordinates (fixed point 16, FP64 32) + force double4 32 + virial 8
         return 4.0 * full_entries + n * (4 + (16 if precision == B.MD_MIXED else 32) + 40)
     pos_b, out_b = (16, 32) if precision == B.MD_MIXED else (32, 64)
-    return 8.0 * pairs + 8.0 * (n + 1) + n * (pos_b + 2 * out_b)  # outputs: zeroed once, accumulated once
+    # half list in CSR form: 4 B per partner + the row starts; outputs zeroed once, accumulated once
+    return 4.0 * pairs + 8.0 * (n + 1) + n * (pos_b + 2 * out_b)
 
 
 def algorithmic_bytes_fused(n: int, entries: int, inner: bool = False) -> float:
     """Compulsory DRAM bytes of one fused force + integrate launch over a list of `entries` entries; a launch
     over the inner list also reads each particle's coordinates at the last prune (16 B)."""
     return 4.0 * entries + (FUSED_BYTES_PER_PARTICLE + (16 if inner else 0)) * n
+
+
+def fp64_peak_gops(sm_mhz: float) -> float:
+    """FP64-pipe operations per second of the whole GPU at the given SM clock (G op/s)."""
+    return FP64_PER_CLK_SM * N_SM * sm_mhz * 1e-3
 
 
 def run_ours(args, rank, world, dist):
@@ -157,50 +180,7 @@ def run_ours(args, rank, world, dist):
     system = make_system(rank)
     n = system.n
     stream = torch.cuda.current_stream()
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        return replica_max(dist, x, dev)
-
-    def time_steps(sim, path, k, sampler=None):
-        st0 = sim.status()
-        barrier()
-        if sampler:
-            sampler.start()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.step(k, path, use_graph=not args.direct)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        clocks = sampler.stop() if sampler else None
-        barrier()
-        st1 = sim.status()
-        assert st1[B.MD_STATUS_CODE] == 0, f"device status {st1}"
-        return e0.elapsed_time(e1), st1[B.MD_STATUS_REBUILDS] - st0[B.MD_STATUS_REBUILDS], clocks
-
-    def list_stats(sim, path=B.MD_VERTEX):
-        cnt = sim.view("nbr_count", torch.int32, n)
-        entries = int(cnt.sum().item())
-        if path == B.MD_VERTEX_NEWTON:  # the Newton list holds every pair once
-            return 2 * entries, entries
-        return entries, entries // 2
-
-    def force_launch_ms(sim, path, k):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        fn = {B.MD_VERTEX: sim.forces_vertex, B.MD_EDGE: sim.forces_edge,
-              B.MD_VERTEX_NEWTON: sim.forces_vertex_newton, B.MD_EDGE_STORE: sim.forces_edge_store}[path]
-        fn()
-        torch.cuda.synchronize()
-        for a, b in evs:
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize()
-        return statistics.mean(a.elapsed_time(b) for a, b in evs)
+    ctx = Ctx(stream, dist, dev)
 
     uuid = None
     try:
@@ -210,91 +190,72 @@ def run_ours(args, rank, world, dist):
     except Exception:
         uuid = None
 
-    results = {}
     # ---- headline: mixed precision, vertex path (the faster path on this workload), one fused
-    # force + integrate kernel per step over an inner list pruned to rc + PRUNE_SKIN ----
+    # force + integrate kernel per step over an inner list pruned to rc + PRUNE_SKIN, timed in the
+    # liquid that EQUILIBRATE_STEPS fused steps make of the initial lattice ----
     headline_path = B.MD_VERTEX
     sim = Simulation(system, B.MD_MIXED, trace_capacity=0, stream=stream, fuse_step=1, prune_skin=PRUNE_SKIN)
     sim.prepare(headline_path)
-    sim.step(max(args.warmup, 3), headline_path, use_graph=True)
     sampler = ClockSampler(uuid) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    sim.step(max(args.warmup, EQUILIBRATE_STEPS), headline_path, use_graph=True)
     p0 = sim.status()[B.MD_STATUS_PRUNES]
-    ms, rebuilds, clocks = time_steps(sim, headline_path, args.steps, sampler)
+    ms, rebuilds = ctx.time_steps(sim, headline_path, args.steps, use_graph=not args.direct)
     prunes = int(sim.status()[B.MD_STATUS_PRUNES] - p0)
-    ms = max_over_ranks(ms)
-    full_entries, pairs = list_stats(sim)
+    ms = ctx.max_over_ranks(ms)
+    steady = []
+    for _ in range(STEADY_REPEATS):
+        sms, sreb = ctx.time_steps(sim, headline_path, STEADY_STEPS)
+        steady.append((ctx.max_over_ranks(sms) / STEADY_STEPS, sreb))
+    clocks = sampler.stop() if sampler else None
+    sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+    full_entries, pairs = list_stats(sim, n)
     inner_entries = int(sim.view("nbr_in_count", torch.int32, n).sum().item())
-    kernel_ms = sim.time_step_kernel(headline_path, reps=min(args.steps, 200))
-    force_ms = force_launch_ms(sim, headline_path, min(args.steps, 200))
+    kernel_ms = sim.time_step_kernel(headline_path, reps=100)
+    force_ms = ctx.force_launch_ms(sim, headline_path, 50)
     step_ms = ms / args.steps
-    results["vertex_mixed"] = {"steps_per_s": 1e3 / step_ms, "ms_per_step": step_ms, "rebuilds": rebuilds,
-                               "prunes": prunes, "pair_evals_per_s": pairs * 1e3 / step_ms,
-                               "step_kernel_ms": kernel_ms, "force_kernel_ms": force_ms, "fuse_step": 1,
-                               "prune_skin": PRUNE_SKIN, "mean_inner_list": inner_entries / n}
+    steady_ms = statistics.median(x[0] for x in steady)
+    headline = {"steps_per_s": 1e3 / step_ms, "ms_per_step": step_ms, "rebuilds": rebuilds, "prunes": prunes,
+                "pair_evals_per_s": pairs * 1e3 / step_ms, "step_kernel_ms": kernel_ms, "force_kernel_ms": force_ms,
+                "fuse_step": 1, "prune_skin": PRUNE_SKIN, "mean_inner_list": inner_entries / n}
     # ---- end to end through the C ABI with host-resident state: md_step_verlet_host, one step per call,
     # positions and velocities ([n][3] FP64 each, pinned) copied in and out by the call, energies out ----
     pos_h, vel_h = sim.slot_state_host(pin=True)
     en_h = torch.empty(B.MD_ENERGY_WORDS, dtype=torch.float64, pin_memory=True)
-    e2e_steps = max(10, min(args.steps // 10, 300))
-    barrier()
+    e2e_calls = max(100, min(args.steps, 300))
+    sim.step_host(pos_h, vel_h, 1, headline_path, use_graph=True, host_energy=en_h)  # graphs built
+    ctx.barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(e2e_calls):
         sim.step_host(pos_h, vel_h, 1, headline_path, use_graph=True, host_energy=en_h)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = ctx.max_over_ranks(time.perf_counter() - t0)
     assert np.isfinite(en_h.numpy()[:4]).all() and sim.status()[B.MD_STATUS_CODE] == 0
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 2 * n * 24,
-           "d2h_bytes_per_step": 2 * n * 24 + 8 * B.MD_ENERGY_WORDS,
+    e2e = {"value": world * e2e_calls / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 2 * n * 24,
+           "d2h_bytes_per_step": 2 * n * 24 + 8 * B.MD_ENERGY_WORDS, "calls": e2e_calls,
            "api": "md_step_verlet_host, 1 step per call"}
+    liquid = sim.positions()  # the equilibrated state, in the original order
     del sim
     torch.cuda.empty_cache()
 
-    # ---- the other decompositions / precisions on the same workload (one GPU only) ----
-    if not args.no_variants and world == 1:
-        NW, ES = B.MD_VERTEX_NEWTON, B.MD_EDGE_STORE
-        HIL = {"cell_order": B.MD_ORDER_HILBERT}
-        for name, path, precision, k, opts in (
-                ("vertex_mixed_fused_full_list", B.MD_VERTEX, B.MD_MIXED, min(args.steps, 1000), {"fuse_step": 1}),
-                ("vertex_mixed_separate_kernels", B.MD_VERTEX, B.MD_MIXED, min(args.steps, 1000), {"fuse_step": 0}),
-                ("vertex_mixed_hilbert", B.MD_VERTEX, B.MD_MIXED, min(args.steps, 1000),
-                 dict(HIL, prune_skin=PRUNE_SKIN)),
-                ("edge_mixed", B.MD_EDGE, B.MD_MIXED, min(args.steps, 1000), {}),
-                ("edge_store_mixed", ES, B.MD_MIXED, min(args.steps, 300), {"edge_store": 1}),
-                ("vertex_newton_mixed_m1", NW, B.MD_MIXED, min(args.steps, 300), {"force_copies": 1}),
-                ("vertex_newton_mixed_m16", NW, B.MD_MIXED, min(args.steps, 300), {"force_copies": 16}),
-                ("vertex_fp64", B.MD_VERTEX, B.MD_FP64, min(args.steps, 40), {}),
-                ("edge_fp64", B.MD_EDGE, B.MD_FP64, min(args.steps, 40), {}),
-                ("vertex_newton_fp64_m16", NW, B.MD_FP64, min(args.steps, 40), {"force_copies": 16})):
-            v = Simulation(system, precision, stream=stream, **opts)
-            v.prepare(path)
-            v.step(3, path, use_graph=True)
-            vms, vreb, _ = time_steps(v, path, k)
-            vms = max_over_ranks(vms)
-            _, vpairs = list_stats(v, path)
-            fms = force_launch_ms(v, path, min(k, 20))
-            results[name] = {"steps_per_s": 1e3 * k / vms, "ms_per_step": vms / k, "rebuilds": vreb,
-                             "pair_evals_per_s": vpairs * 1e3 * k / vms, "force_kernel_ms": fms, "steps": k, **opts}
-            del v
-            torch.cuda.empty_cache()
-
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm, peak_source = hbm_peak()
     alg = algorithmic_bytes_fused(n, inner_entries, inner=True)
     achieved = alg / (kernel_ms * 1e-3) / 1e9
     force_alg = algorithmic_bytes_force(headline_path, B.MD_MIXED, n, full_entries, pairs)
+    # the survey's count of compulsory bytes for the vertex step: 4 B per full-list entry + 192 B per particle
+    survey_alg = 4.0 * full_entries + 192.0 * n
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": measured_traffic("k_vertex_step_mixed<1,true>", n, inner_entries),
-                "kernel": "k_vertex_step_mixed<1,true>",
+                "kernel": "k_vertex_step_mixed<1,true>", "state": f"liquid, after {EQUILIBRATE_STEPS} steps",
                 "algorithmic_bytes_per_launch": alg, "kernel_ms": kernel_ms,
-                "kernel_share_of_step": kernel_ms / step_ms,
+                "kernel_share_of_step": kernel_ms / steady_ms,
+                "frac_survey_bytes": survey_alg / (kernel_ms * 1e-3) / 1e9 / hbm,
+                "survey_bytes_per_launch": survey_alg,
                 "force_only": {"kernel": "k_vertex_iso_mixed<1,true>", "algorithmic_bytes_per_launch": force_alg,
                                "ms": force_ms, "achieved": force_alg / (force_ms * 1e-3) / 1e9,
                                "frac": force_alg / (force_ms * 1e-3) / 1e9 / hbm},
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
+                "peak_source": peak_source}
     value = job_throughput(world, args.steps, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -302,12 +263,16 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "precision": "mixed: FP32 pair arithmetic + compensated FP32 sums, FP64 integration and reductions",
         "pair_evals_per_s": world * pairs * args.steps / (ms * 1e-3),
+        "steady": {"ms_per_step": steady_ms, "steps_per_s": world * 1e3 / steady_ms, "repeats": STEADY_REPEATS,
+                   "steps_per_repeat": STEADY_STEPS, "ms_per_step_each": [x[0] for x in steady],
+                   "rebuilds_each": [x[1] for x in steady],
+                   "note": "median of the repeats; each repeat spans several rebuild and prune periods"},
         "config": {"workload": WORKLOAD, "n": n, "path": "vertex", "precision": "mixed",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (inner list ~0.26 GB + state ~0.2 GB per step)",
+                   "equilibrated_steps": max(args.warmup, EQUILIBRATE_STEPS),
                    "mean_full_list": full_entries / n, "mean_inner_list": inner_entries / n,
                    "prune_skin": PRUNE_SKIN, "unique_pairs": pairs},
-        "variants": results,
         "roofline": roofline,
         "e2e": e2e,
         # one call of K fused steps: the opening integrate (its last block decides), K - 1 fused step
@@ -318,15 +283,285 @@ def run_ours(args, rank, world, dist):
         "clocks": clocks,
         "graph": not args.direct,
     }
+    if not args.no_variants and world == 1:
+        line["variants"], line["accuracy"] = run_variants(ctx, system, liquid, headline, roofline, sm_mhz, args)
     if not args.no_batch and world == 1:
         line["batch"] = run_batch()
     if not args.no_sweep and world == 1:
         line["density_sweep"] = run_density_sweep()
-    if not args.no_variants and world == 1:
-        line["accuracy"] = run_accuracy()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system)
     return line
+
+
+class Ctx:
+    """Timing helpers on one stream, with the barrier and max over ranks of the weak-scaling run."""
+
+    def __init__(self, stream, dist, dev):
+        self.stream, self.dist, self.dev = stream, dist, dev
+
+    def barrier(self):
+        import torch
+        torch.cuda.synchronize()
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, x):
+        return replica_max(self.dist, x, self.dev)
+
+    def time_steps(self, sim, path, k, use_graph=True):
+        """ms of k md_step_verlet steps (CUDA events on the launching stream) and the rebuilds among them."""
+        import torch
+        from paper_1401_4350_gb300 import binding as B
+        st0 = sim.status()
+        self.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        sim.step(k, path, use_graph=use_graph)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        self.barrier()
+        st1 = sim.status()
+        assert st1[B.MD_STATUS_CODE] == 0, f"device status {st1}"
+        return e0.elapsed_time(e1), int(st1[B.MD_STATUS_REBUILDS] - st0[B.MD_STATUS_REBUILDS])
+
+    def force_launch_ms(self, sim, path, k):
+        """Mean ms of one force evaluation of `path` (the force entry point's kernels), CUDA events."""
+        import torch
+        from paper_1401_4350_gb300 import binding as B
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        fn = {B.MD_VERTEX: sim.forces_vertex, B.MD_EDGE: sim.forces_edge,
+              B.MD_VERTEX_NEWTON: sim.forces_vertex_newton, B.MD_EDGE_STORE: sim.forces_edge_store}[path]
+        fn()
+        torch.cuda.synchronize()
+        for a, b in evs:
+            a.record(self.stream)
+            fn()
+            b.record(self.stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def list_stats(sim, n, path=None):
+    """(full-list entries, unique pairs) of the lists the system holds."""
+    import torch
+    from paper_1401_4350_gb300 import binding as B
+    cnt = sim.view("nbr_count", torch.int32, n)
+    entries = int(cnt.sum().item())
+    if path == B.MD_VERTEX_NEWTON:  # the Newton list holds every pair once
+        return 2 * entries, entries
+    if path in (B.MD_EDGE, B.MD_EDGE_STORE):  # only the half list is built
+        pairs = int(sim.view("half_start", torch.int64, n + 1)[-1].item())
+        return 2 * pairs, pairs
+    return entries, entries // 2
+
+
+def hbm_peak():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s, an earlier GB300 measurement)"
+
+
+# The configurations of the scaling and regime study: name -> (factory, kind)
+def config_systems():
+    from paper_1401_4350_gb300 import systems
+    return {
+        "lj65536": lambda: systems.make_lj(65_536, 0.85, 1.0, seed=1001),
+        "lj262144": lambda: systems.make_lj(262_144, 0.85, 1.0, seed=1001),
+        "wca1m": lambda: systems.make_wca(1_048_576, 0.2, seed=1002),
+        "patchy262k": lambda: systems.make_patchy(262_144, 0.3, seed=1003),
+    }
+
+
+def with_state(s, pos, vel, quat=None, angmom=None):
+    """The system s with another state (positions wrapped into the box)."""
+    import dataclasses
+    import numpy as np
+    box = np.asarray(s.box, dtype=np.float64)
+    pos = np.mod(np.asarray(pos, dtype=np.float64), box)
+    pos[pos >= box] -= np.broadcast_to(box, pos.shape)[pos >= box]
+    return dataclasses.replace(s, pos=pos, vel=vel, quat=quat if quat is not None else s.quat,
+                               angmom=angmom if angmom is not None else s.angmom)
+
+
+def equilibrate(s, steps):
+    """The system after `steps` steps of its fastest mixed path (the liquid the variants are timed in)."""
+    import torch
+    from paper_1401_4350_gb300 import binding as B
+    from paper_1401_4350_gb300.sim import Simulation
+    from paper_1401_4350_gb300.systems import PATCHY_KINDS
+    patchy = s.kind in PATCHY_KINDS
+    path = B.MD_EDGE if patchy else B.MD_VERTEX
+    sim = Simulation(s, B.MD_MIXED, fuse_step=0 if patchy else 1)
+    sim.prepare(path)
+    sim.step(steps, path, use_graph=True)
+    assert sim.status()[B.MD_STATUS_CODE] == 0
+    x, v = sim.positions()
+    q, l = sim.orientations() if patchy else (None, None)
+    del sim
+    torch.cuda.empty_cache()
+    return with_state(s, x, v, q, l)
+
+
+def drift(s, precision, path, steps, opts):
+    """Energy drift of `steps` graph steps from the state s: least-squares slope of E_tot / N per 10^4 steps,
+    and the rms fluctuation of E_tot / N."""
+    import numpy as np
+    import torch
+    from paper_1401_4350_gb300 import binding as B
+    from paper_1401_4350_gb300.sim import Simulation
+    sim = Simulation(s, precision, trace_capacity=steps + 1, **opts)
+    sim.prepare(path)
+    sim.step(steps, path, use_graph=True)
+    assert sim.status()[B.MD_STATUS_CODE] == 0
+    tr = sim.trace()
+    rows = tr[(tr[:, 0] > 0) & (tr[:, 0] <= steps)]
+    rows = rows[np.argsort(rows[:, 0])]
+    e = (rows[:, 1] + rows[:, 2]) / s.n
+    del sim
+    torch.cuda.empty_cache()
+    return {"per_1e4_steps": float(np.polyfit(rows[:, 0], e, 1)[0]) * 1e4, "rms_fluctuation": float(np.std(e)),
+            "steps": steps}
+
+
+def run_variants(ctx, system1m, liquid1m, headline, headline_roofline, sm_mhz, args):
+    """Every (configuration, path, precision) on one GPU, each timed in the liquid of its configuration
+    (EQUILIBRATE_STEPS steps of its fastest mixed path): steps/s of md_step_verlet (graph), pair-evals/s, the
+    dominant kernel's time and its roofline fraction; then the accuracy of each mixed result against the
+    FP64 path on the same state (max force and torque error over the rms over all particles) and the
+    energy drift of both precisions."""
+    import numpy as np
+    import torch
+    from paper_1401_4350_gb300 import binding as B
+    from paper_1401_4350_gb300.sim import Simulation
+    from paper_1401_4350_gb300.systems import PATCHY_KINDS
+
+    hbm, _ = hbm_peak()
+    fp64_peak = fp64_peak_gops(sm_mhz)
+    systems_eq = {"lj1m": with_state(system1m, *liquid1m)}
+    for name, make in config_systems().items():
+        systems_eq[name] = equilibrate(make(), EQUILIBRATE_STEPS)
+    out = {}
+
+    def run(key, s, path, precision, k, opts, what="force"):
+        n = s.n
+        sim = Simulation(s, precision, stream=ctx.stream, **opts)
+        sim.prepare(path)
+        sim.step(3, path, use_graph=True)
+        ms, reb = ctx.time_steps(sim, path, k)
+        entries, pairs = list_stats(sim, n, path)
+        fused = opts.get("fuse_step", 1) == 1 and path == B.MD_VERTEX and precision == B.MD_MIXED and \
+            s.kind not in PATCHY_KINDS
+        patchy = s.kind in PATCHY_KINDS
+        r = {"steps_per_s": 1e3 * k / ms, "ms_per_step": ms / k, "rebuilds": reb, "steps": k,
+             "pair_evals_per_s": pairs * 1e3 * k / ms, "n": n, "mean_full_list": entries / n,
+             "path": {B.MD_VERTEX: "vertex", B.MD_EDGE: "edge", B.MD_VERTEX_NEWTON: "vertex_newton",
+                      B.MD_EDGE_STORE: "edge_store"}[path],
+             "precision": "mixed" if precision == B.MD_MIXED else "fp64",
+             "l2": "inputs larger than L2" if n >= 262_144 else "inputs fit in L2 (129 MB)", **opts}
+        if fused:
+            inner = opts.get("prune_skin", 0.0) > 0
+            walked = int(sim.view("nbr_in_count", torch.int32, n).sum().item()) if inner else entries
+            kms = sim.time_step_kernel(path, reps=50)
+            alg = algorithmic_bytes_fused(n, walked, inner)
+            r["roofline"] = {"bound": "hbm", "kernel": "k_vertex_step_mixed", "kernel_ms": kms,
+                             "algorithmic_bytes_per_launch": alg, "achieved": alg / (kms * 1e-3) / 1e9,
+                             "peak": hbm, "unit": "GB/s", "frac": alg / (kms * 1e-3) / 1e9 / hbm}
+        else:
+            fms = ctx.force_launch_ms(sim, path, 5 if precision == B.MD_FP64 else 20)
+            kname = {(B.MD_VERTEX, B.MD_MIXED): "k_vertex_iso_mixed" if not patchy else "k_vertex_mixed",
+                     (B.MD_EDGE, B.MD_MIXED): "k_edge_mixed", (B.MD_VERTEX, B.MD_FP64): "k_vertex_fp64",
+                     (B.MD_EDGE, B.MD_FP64): "k_edge_fp64", (B.MD_VERTEX_NEWTON, B.MD_MIXED): "k_vertex_newton_mixed",
+                     (B.MD_VERTEX_NEWTON, B.MD_FP64): "k_vertex_newton_fp64",
+                     (B.MD_EDGE_STORE, B.MD_MIXED): "k_edge_store"}.get((path, precision), "force kernels")
+            if precision == B.MD_FP64 and not patchy and path in (B.MD_VERTEX, B.MD_EDGE):
+                evals = entries if path == B.MD_VERTEX else pairs
+                ops = FP64_OPS_PER_PAIR_EVAL_LJ * evals
+                r["roofline"] = {"bound": "alu", "kernel": kname, "kernel_ms": fms, "unit": "G FP64 op/s",
+                                 "fp64_ops_per_launch": ops, "achieved": ops / (fms * 1e-3) / 1e9,
+                                 "peak": fp64_peak, "frac": ops / (fms * 1e-3) / 1e9 / fp64_peak,
+                                 "ops_per_pair_eval": FP64_OPS_PER_PAIR_EVAL_LJ,
+                                 "peak_source": f"{FP64_PER_CLK_SM} FP64 op/clk/SM (ncu peak_sustained) x {N_SM} "
+                                                f"SMs x {sm_mhz:.0f} MHz (median SM clock of the headline run)"}
+            else:
+                alg = algorithmic_bytes_force(path if path in (B.MD_VERTEX, B.MD_EDGE) else B.MD_EDGE, precision,
+                                              n, entries, pairs)
+                r["roofline"] = {"bound": "hbm", "kernel": kname, "kernel_ms": fms,
+                                 "algorithmic_bytes_per_launch": alg, "achieved": alg / (fms * 1e-3) / 1e9,
+                                 "peak": hbm, "unit": "GB/s", "frac": alg / (fms * 1e-3) / 1e9 / hbm}
+        del sim
+        torch.cuda.empty_cache()
+        out[key] = r
+        return r
+
+    MIX, F64, VX, ED = B.MD_MIXED, B.MD_FP64, B.MD_VERTEX, B.MD_EDGE
+    ksteps = lambda prec, n: (max(20, min(200, int(2e8 / n))) if prec == MIX else max(5, min(40, int(2e7 / n))))
+    for name in ("lj65536", "lj262144", "lj1m", "wca1m", "patchy262k"):
+        s = systems_eq[name]
+        patchy = s.kind in PATCHY_KINDS
+        for path, prec in ((VX, MIX), (ED, MIX), (VX, F64), (ED, F64)):
+            key = f"{name}_{'vertex' if path == VX else 'edge'}_{'mixed' if prec == MIX else 'fp64'}"
+            if name == "lj1m" and path == VX and prec == MIX:
+                out[key] = dict(headline, roofline={k: headline_roofline[k] for k in
+                                                    ("bound", "kernel", "kernel_ms", "algorithmic_bytes_per_launch",
+                                                     "achieved", "peak", "unit", "frac")},
+                                n=s.n, path="vertex", precision="mixed", note="the headline run")
+                continue
+            opts = {"fuse_step": 0}  # separate force and integrate kernels
+            if path == VX and prec == MIX and not patchy:
+                # the fused step; LJ over the inner list as in the headline
+                opts = {"fuse_step": 1, "prune_skin": PRUNE_SKIN if s.kind == 0 else 0.0}
+            run(key, s, path, prec, ksteps(prec, s.n), opts)
+    # other decompositions on the 1M LJ liquid
+    s = systems_eq["lj1m"]
+    NW, ES = B.MD_VERTEX_NEWTON, B.MD_EDGE_STORE
+    for key, path, prec, k, opts in (
+            ("lj1m_vertex_mixed_fused_full_list", VX, MIX, 200, {"fuse_step": 1}),
+            ("lj1m_vertex_mixed_separate_kernels", VX, MIX, 200, {"fuse_step": 0}),
+            ("lj1m_vertex_mixed_hilbert", VX, MIX, 200, {"fuse_step": 1, "prune_skin": PRUNE_SKIN,
+                                                          "cell_order": B.MD_ORDER_HILBERT}),
+            ("lj1m_edge_store_mixed", ES, MIX, 50, {"edge_store": 1, "fuse_step": 0}),
+            ("lj1m_vertex_newton_mixed_m1", NW, MIX, 50, {"force_copies": 1, "fuse_step": 0}),
+            ("lj1m_vertex_newton_mixed_m16", NW, MIX, 50, {"force_copies": 16, "fuse_step": 0}),
+            ("lj1m_vertex_newton_fp64_m16", NW, F64, 10, {"force_copies": 16, "fuse_step": 0})):
+        run(key, s, path, prec, k, opts)
+
+    # ---- accuracy: mixed against FP64 on each liquid state; drift of both precisions ----
+    acc = {}
+    for name in ("lj65536", "lj262144", "lj1m", "wca1m", "patchy262k"):
+        s = systems_eq[name]
+        patchy = s.kind in PATCHY_KINDS
+        res = {}
+        ref = Simulation(s, F64, fuse_step=0)
+        ref.prepare(VX)
+        Fr, _, Tr, _ = ref.forces()
+        del ref
+        torch.cuda.empty_cache()
+        frms = float(np.sqrt((Fr ** 2).sum(1).mean()))
+        trms = float(np.sqrt((Tr ** 2).sum(1).mean())) if patchy else None
+        for pname, path in (("vertex", VX), ("edge", ED)):
+            sim = Simulation(s, MIX, fuse_step=0)
+            sim.prepare(path)
+            F, _, T, _ = sim.forces()
+            del sim
+            torch.cuda.empty_cache()
+            res[f"{pname}_max_force_error_frms"] = float(np.abs(F - Fr).max()) / frms
+            if patchy:
+                res[f"{pname}_max_torque_error_trms"] = float(np.abs(T - Tr).max()) / trms
+        if patchy:
+            res["torque_rms_over"] = "all particles"
+        dsteps = 1000
+        mixed_opts = {"fuse_step": 0} if patchy else {"fuse_step": 1, "prune_skin": PRUNE_SKIN if s.kind == 0 else 0.0}
+        res["drift_mixed"] = drift(s, MIX, ED if patchy else VX, dsteps, mixed_opts)
+        res["drift_fp64"] = drift(s, F64, VX, dsteps, {"fuse_step": 0})
+        res["drift_mixed"]["path"] = "edge" if patchy else "vertex"
+        acc[name] = res
+    acc["definitions"] = ("force error: max over particles and components of |F_mixed - F_fp64| / F_rms (torque: "
+                          "the same over tau_rms of all particles), both on the liquid state of the row; drift: "
+                          "least-squares slope of E_tot / N over 1000 graph steps from that state, per 10^4 steps")
+    return out, acc
 
 
 def kernel_source_digest() -> str:
@@ -353,62 +588,6 @@ def measured_traffic(kernel: str, n: int, entries: int):
     alg_now = 4.0 * entries + per * n
     alg_cap = 4.0 * rec["list_entries"] + per * rec["n"]
     return rec["dram_bytes_per_launch"] * alg_now / alg_cap
-
-
-def run_accuracy(n_drift: int = 65536, drift_steps: int = 2000, snapshot_steps: int = 1000):
-    """Force error of the mixed path against the FP64 path on the headline system's initial state and after
-    `snapshot_steps` headline steps, and energy drift (least-squares slope of E_tot / N per 10^4 steps) of
-    both precisions on LJ N = 65,536 (mixed: the headline's fused steps over the inner list)."""
-    import numpy as np
-    import torch
-    from paper_1401_4350_gb300 import binding as B
-    from paper_1401_4350_gb300 import systems
-    from paper_1401_4350_gb300.sim import Simulation
-    out = {}
-    s = make_system(0)
-    F = {}
-    for prec in (B.MD_MIXED, B.MD_FP64):
-        sim = Simulation(s, prec)
-        sim.prepare(B.MD_VERTEX)
-        F[prec] = sim.forces()[0]
-        del sim
-        torch.cuda.empty_cache()
-    frms = float(np.sqrt((F[B.MD_FP64] ** 2).sum(1).mean()))
-    out["max_force_error_mixed_vs_fp64_frms"] = float(np.abs(F[B.MD_MIXED] - F[B.MD_FP64]).max()) / frms
-    # the same after the headline's steps: the liquid the timed run sees
-    run = Simulation(s, B.MD_MIXED, fuse_step=1, prune_skin=PRUNE_SKIN)
-    run.prepare(B.MD_VERTEX)
-    run.step(snapshot_steps, B.MD_VERTEX, use_graph=True)
-    x, v = run.positions()
-    del run
-    torch.cuda.empty_cache()
-    for prec in (B.MD_MIXED, B.MD_FP64):
-        sim = Simulation(s, prec)
-        sim.load_state(x, v)
-        sim.prepare(B.MD_VERTEX)
-        F[prec] = sim.forces()[0]
-        del sim
-        torch.cuda.empty_cache()
-    frms = float(np.sqrt((F[B.MD_FP64] ** 2).sum(1).mean()))
-    out[f"max_force_error_mixed_vs_fp64_frms_step{snapshot_steps}"] = \
-        float(np.abs(F[B.MD_MIXED] - F[B.MD_FP64]).max()) / frms
-    small = systems.make_lj(n_drift, 0.85, 1.0, seed=1001)
-    drift = {}
-    for name, prec in (("fp64", B.MD_FP64), ("mixed", B.MD_MIXED)):
-        sim = Simulation(small, prec, trace_capacity=drift_steps + 1,
-                         prune_skin=PRUNE_SKIN if prec == B.MD_MIXED else 0.0)
-        sim.prepare(B.MD_VERTEX)
-        sim.step(drift_steps, B.MD_VERTEX, use_graph=True)
-        tr = sim.trace()
-        rows = tr[(tr[:, 0] > 0) & (tr[:, 0] <= drift_steps)]
-        rows = rows[np.argsort(rows[:, 0])]
-        e = (rows[:, 1] + rows[:, 2]) / n_drift
-        slope = float(np.polyfit(rows[:, 0], e, 1)[0]) * 1e4
-        drift[name] = {"per_1e4_steps": slope, "rms_fluctuation": float(np.std(e)), "steps": drift_steps}
-        del sim
-        torch.cuda.empty_cache()
-    out["energy_drift_lj65536"] = drift
-    return out
 
 
 def run_density_sweep(n: int = 131072, steps: int = 200):
@@ -448,7 +627,7 @@ def run_density_sweep(n: int = 131072, steps: int = 200):
     return out
 
 
-def run_batch(steps: int = 50, fp64_steps: int = 5):
+def run_batch(steps: int = 50, fp64_steps: int = 5, drift_steps: int = 1000):
     """512 replicas (N log-uniform in [500, 32768], rho ~ U(0.2, 0.9), every fourth WCA at rho 0.2, the
     rest LJ rc 2.5): mixed-precision batched path, autotuned, against looping the plain FP64
     single-system path over the same replicas.  Also the batch's max force error against FP64."""
@@ -460,7 +639,7 @@ def run_batch(steps: int = 50, fp64_steps: int = 5):
 
     reps = [systems.make_replica(*spec) for spec in systems.batch_specs(512)]
     n_total = sum(s.n for s in reps)
-    bs = BatchSimulation(reps)
+    bs = BatchSimulation(reps, trace_capacity=drift_steps + 1)
     t0 = time.perf_counter()
     paths, tpps = bs.autotune()
     tune_s = time.perf_counter() - t0
@@ -485,6 +664,16 @@ def run_batch(steps: int = 50, fp64_steps: int = 5):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1)
     assert all(bs.replica_status(r)[B.MD_STATUS_CODE] == 0 for r in range(len(reps)))
+    # energy drift of every replica over the next drift_steps batched steps: slope of E_tot / N per 10^4 steps
+    s0 = int(bs.replica_status(0)[B.MD_STATUS_STEPS])
+    bs.step(drift_steps)
+    slopes = []
+    for r, s in enumerate(reps):
+        tr = bs.replica_trace(r)
+        rows = tr[(tr[:, 0] > s0) & (tr[:, 0] <= s0 + drift_steps)]
+        rows = rows[np.argsort(rows[:, 0])]
+        slopes.append(float(np.polyfit(rows[:, 0], (rows[:, 1] + rows[:, 2]) / s.n, 1)[0]) * 1e4)
+    slopes = np.abs(np.array(slopes))
     bs.release()
     del bs
     torch.cuda.empty_cache()
@@ -510,6 +699,8 @@ def run_batch(steps: int = 50, fp64_steps: int = 5):
             "replica_steps_per_s": batch_rs, "particle_steps_per_s": n_total * steps / (batch_ms * 1e-3),
             "fp64_loop_replica_steps_per_s": loop_rs, "speedup_vs_fp64_loop": batch_rs / loop_rs,
             "max_force_error_vs_fp64_frms": worst, "autotune_s": tune_s,
+            "energy_drift_per_1e4_steps": {"median_abs": float(np.median(slopes)), "max_abs": float(slopes.max()),
+                                           "steps": drift_steps, "over": "every replica, E_tot / N"},
             "chosen": {"edge": int(sum(1 for p in paths if p == B.MD_EDGE)),
                        "vertex_tpp1": int(sum(1 for p, t in zip(paths, tpps) if p == B.MD_VERTEX and t == 1)),
                        "vertex_tpp2": int(sum(1 for p, t in zip(paths, tpps) if p == B.MD_VERTEX and t == 2)),

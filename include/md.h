@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 4
+#define MD_ABI_VERSION 5
 
 /* Return / status codes. */
 enum {
@@ -206,7 +206,8 @@ typedef struct md_ws_layout {
                             the same layout with the rows of md_forces_vertex_newton              */
   size_t nbr_count;      /* int32[n]: full-list length per slot                               */
   size_t half_start;     /* int64[n + 1]: half-list row offsets                               */
-  size_t pairs;          /* int32[max_pairs][2]: half list (i, j), i < j, sorted by i          */
+  size_t half_j;         /* int32[max_pairs]: half list in CSR form, row i (the partners j > i
+                            of slot i) at half_j[half_start[i] .. half_start[i + 1])            */
   size_t force;          /* double[n][4] (Fx, Fy, Fz, E_i): the force result of either precision */
   size_t virial;         /* double[n] W_i: half of each pair virial -r_ij.F_ij                  */
   size_t torque;         /* double[n][4] (tx, ty, tz, 0), patchy                                */
@@ -220,7 +221,7 @@ typedef struct md_ws_layout {
                             blocks of max_pairs entries: A = (F_ij, e_ij), B = (tau_i, w_ij) and,
                             patchy, C = (tau_j, 0); float[4] (mixed) or double[4] (FP64) each    */
   size_t jstart;         /* int64[n + 1]: rows of the by-partner index (edge_store = 1)          */
-  size_t jedge;          /* int32[max_pairs]: half-list positions k with pairs[k].j = i, row i in
+  size_t jedge;          /* int32[max_pairs]: half-list positions k with half_j[k] = i, row i in
                             increasing partner order (edge_store = 1)                           */
   size_t local_tab;      /* block-local full list: per block of MD_LOCAL_BLOCK slots an int32[4]
                             header (U cells, H halo slots, status, 0) and int32[MD_LOCAL_MAX_CELLS][2]

@@ -56,7 +56,7 @@ class md_ws_layout(ctypes.Structure):
     _fields_ = [("total", ctypes.c_size_t), ("ncell", ctypes.c_int32 * 3), ("force_elem", ctypes.c_int32)] + [
         (name, ctypes.c_size_t) for name in
         ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr", "nbr_count", "half_start",
-         "pairs", "force", "virial", "torque", "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace",
+         "half_j", "force", "virial", "torque", "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace",
          "pos_alt", "fxp_alt", "nbr_in", "nbr_in_count", "fxp_prune", "scratch")]
 
 

@@ -197,7 +197,7 @@ static void make_layout(const md_params* p, Layout* L) {
   P.nbr = take(sizeof(int32_t) * 4 * n * (size_t)((p->max_neigh + 3) / 4));
   P.nbr_count = take(sizeof(int32_t) * n);
   P.half_start = take(sizeof(int64_t) * (n + 1));
-  P.pairs = take(8 * (size_t)p->max_pairs);
+  P.half_j = take(sizeof(int32_t) * (size_t)p->max_pairs);
   P.force = take(32 * n);
   P.virial = take(8 * n);
   P.torque = take(patchy ? 32 * n : 0);
@@ -304,6 +304,17 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
     const double fscale = -24.0 * p->eps / (u * ldexp(1.0, S));
     a.fscale_hi = f32(fscale);
     a.fscale_lo = f32(fscale - (double)a.fscale_hi);
+    // the accurate repulsive core: WCA (every interacting pair is in the steep core) in a cubic box
+    a.accurate_core = (p->model == MD_WCA && a.cubic) ? 1 : 0;
+    {
+      const double C = p->sigma * p->sigma / u2, kv = ldexp(1.0, S) / C, ke = -24.0 * p->eps * u / (p->sigma * p->sigma);
+      a.core_c_hi = f32(C);
+      a.core_c_lo = f32(C - (double)a.core_c_hi);
+      a.core_kv_hi = f32(kv);
+      a.core_kv_lo = f32(kv - (double)a.core_kv_hi);
+      a.core_ke_hi = f32(ke);
+      a.core_ke_lo = f32(ke - (double)a.core_ke_hi);
+    }
     const double rin = p->rc + p->prune_skin;
     a.rin2_s = f32(rin * rin * (1.0 + 1e-5) / unit2);
     a.prune_thr2 = f32(0.25 * p->prune_skin * p->prune_skin * (1.0 - 1e-4));
@@ -391,7 +402,7 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
   a.nbr = (int32_t*)(w + L.pub.nbr);
   a.nbr_count = (int32_t*)(w + L.pub.nbr_count);
   a.half_start = (int64_t*)(w + L.pub.half_start);
-  a.pairs = (int2*)(w + L.pub.pairs);
+  a.half_j = (int32_t*)(w + L.pub.half_j);
   a.force = (double4_32a*)(w + L.pub.force);
   a.virial = (double*)(w + L.pub.virial);
   a.torque = (double4_32a*)(w + L.pub.torque);
@@ -426,7 +437,7 @@ KArgs kernel_args_without_workspace(const md_params* p, const md_state* s) {
   a.status = nullptr; a.energy = nullptr; a.cell_start = nullptr; a.fxp = nullptr; a.fxp_build = nullptr;
   a.pos_alt = nullptr; a.fxp_alt = nullptr; a.inner = 0; a.nbr_in = nullptr; a.nbr_in_count = nullptr;
   a.fxp_prune = nullptr;
-  a.patch_lab = nullptr; a.patch_lab_d = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.pairs = nullptr;
+  a.patch_lab = nullptr; a.patch_lab_d = nullptr; a.nbr = nullptr; a.nbr_count = nullptr; a.half_start = nullptr; a.half_j = nullptr;
   a.force = nullptr; a.virial = nullptr; a.torque = nullptr; a.acc = nullptr; a.trace = nullptr;
   a.copies = nullptr; a.estore = nullptr; a.jstart = nullptr; a.jedge = nullptr; a.local_ok = 0; a.local_tab = nullptr;
   a.scr_words = nullptr; a.acc_slots = nullptr; a.cell_of = nullptr; a.rank = nullptr; a.perm = nullptr;

@@ -32,7 +32,7 @@ namespace mdgb {
 
 constexpr int kBChunk = 256;        // particles per chunk item (integrate, rebuild)
 constexpr int kBForce = 128;        // threads per force item
-constexpr int kBEdgePairs = 512;    // pairs per edge force item
+constexpr int kBEdgeRows = 128;     // half-list rows per edge force item (a span of 32 rows per warp)
 constexpr int kBGrid = 4;           // persistent blocks per SM
 
 // per-replica force kinds
@@ -280,6 +280,8 @@ __global__ void __launch_bounds__(kBChunk) k_b_edge_acc(BatchDev b) {
   }
 }
 
+static_assert(kBEdgeRows == (kBForce / 32) * kSpanRows, "an edge item is one span of rows per warp");
+
 __global__ void __launch_bounds__(kBForce) k_b_forces(BatchDev b) {
   __shared__ KArgs ka;
   __shared__ int s_item, s_rep;
@@ -303,10 +305,15 @@ __global__ void __launch_bounds__(kBForce) k_b_forces(BatchDev b) {
     if (kind & KIND_NEWTON) {
       vertex_newton_mixed_body<false, 1>(ka, gt);
     } else if (kind & KIND_EDGE) {
-      const int64_t E = min(ka.half_start[ka.n], ka.max_pairs);
-      const int64_t first = (int64_t)local * kBEdgePairs;
-      if (first < E)
-        edge_mixed_body<false, 1>(ka, first / 32 + (threadIdx.x >> 5), kBForce / 32, min(E, first + kBEdgePairs));
+      const int r0 = local * kBEdgeRows + (threadIdx.x >> 5) * kSpanRows;
+      if (r0 < ka.n) edge_mixed_span<false, 1>(ka, r0, half_pairs(ka));
+    } else if ((kind & KIND_CUBIC) && ka.accurate_core) {
+      switch (kind & 7) {
+        case KIND_V1: vertex_iso_mixed_body<1, true, false, true>(ka, gt); break;
+        case KIND_V2: vertex_iso_mixed_body<2, true, false, true>(ka, gt); break;
+        case KIND_V4: vertex_iso_mixed_body<4, true, false, true>(ka, gt); break;
+        default: vertex_iso_mixed_body<8, true, false, true>(ka, gt); break;
+      }
     } else if (kind & KIND_CUBIC) {
       switch (kind & 7) {
         case KIND_V1: vertex_iso_mixed_body<1, true, false>(ka, gt); break;
@@ -404,7 +411,7 @@ static void ctl_layout(int nrep, int integ_items, int force_items_cap, CtlLayout
 }
 
 static int force_items_of(const md_params& p, int path, int tpp) {
-  if (path == MD_EDGE) return (int)((p.max_pairs + kBEdgePairs - 1) / kBEdgePairs);
+  if (path == MD_EDGE) return (p.n + kBEdgeRows - 1) / kBEdgeRows;
   if (path == MD_VERTEX_NEWTON) tpp = 1;
   return (int)(((int64_t)p.n * tpp + kBForce - 1) / kBForce);
 }

@@ -45,30 +45,37 @@ static int sm_count() {
   return cached[dev];
 }
 
+// The isotropic mixed vertex kernel of a cubic box, with or without the accurate repulsive core.
+template <bool ACC>
+static void launch_vertex_iso_cubic(const KArgs& a, int grid, int block, cudaStream_t st) {
+  switch (a.tpp) {
+    case 1:
+      if (a.local_ok)  // either list format: the kernel reads which one the status records
+        k_vertex_iso_mixed<1, true, ACC><<<(a.n + MD_LOCAL_BLOCK - 1) / MD_LOCAL_BLOCK, MD_LOCAL_BLOCK,
+                                           sizeof(uint4) * kLocalSmem, st>>>(a);
+      else
+        k_vertex_iso_mixed<1, true, ACC><<<grid, block, 0, st>>>(a);
+      break;
+    case 2: k_vertex_iso_mixed<2, true, ACC><<<grid, block, 0, st>>>(a); break;
+    case 4: k_vertex_iso_mixed<4, true, ACC><<<grid, block, 0, st>>>(a); break;
+    default: k_vertex_iso_mixed<8, true, ACC><<<grid, block, 0, st>>>(a); break;
+  }
+}
+
 template <bool PATCHY, int NP>
 static void launch_vertex(const KArgs& a, int block, cudaStream_t st) {
   const int64_t threads = (int64_t)a.n * a.tpp;
   const int grid = (int)((threads + block - 1) / block);
   if (a.precision == MD_MIXED && !PATCHY) {
     if (a.cubic) {
-      switch (a.tpp) {
-        case 1:
-          if (a.local_ok)  // either list format: the kernel reads which one the status records
-            k_vertex_iso_mixed<1, true><<<(a.n + MD_LOCAL_BLOCK - 1) / MD_LOCAL_BLOCK, MD_LOCAL_BLOCK,
-                                          sizeof(uint4) * kLocalSmem, st>>>(a);
-          else
-            k_vertex_iso_mixed<1, true><<<grid, block, 0, st>>>(a);
-          break;
-        case 2: k_vertex_iso_mixed<2, true><<<grid, block, 0, st>>>(a); break;
-        case 4: k_vertex_iso_mixed<4, true><<<grid, block, 0, st>>>(a); break;
-        default: k_vertex_iso_mixed<8, true><<<grid, block, 0, st>>>(a); break;
-      }
+      if (a.accurate_core) launch_vertex_iso_cubic<true>(a, grid, block, st);
+      else launch_vertex_iso_cubic<false>(a, grid, block, st);
     } else {
       switch (a.tpp) {
-        case 1: k_vertex_iso_mixed<1, false><<<grid, block, 0, st>>>(a); break;
-        case 2: k_vertex_iso_mixed<2, false><<<grid, block, 0, st>>>(a); break;
-        case 4: k_vertex_iso_mixed<4, false><<<grid, block, 0, st>>>(a); break;
-        default: k_vertex_iso_mixed<8, false><<<grid, block, 0, st>>>(a); break;
+        case 1: k_vertex_iso_mixed<1, false, false><<<grid, block, 0, st>>>(a); break;
+        case 2: k_vertex_iso_mixed<2, false, false><<<grid, block, 0, st>>>(a); break;
+        case 4: k_vertex_iso_mixed<4, false, false><<<grid, block, 0, st>>>(a); break;
+        default: k_vertex_iso_mixed<8, false, false><<<grid, block, 0, st>>>(a); break;
       }
     }
   } else if (a.precision == MD_MIXED) {
@@ -88,12 +95,18 @@ static void launch_vertex(const KArgs& a, int block, cudaStream_t st) {
   }
 }
 
+// Blocks of the persistent edge kernels: one warp per span of 32 half-list rows, at most as many as are
+// resident on every SM at once.
+static int edge_grid(const KArgs& a, int block) {
+  const int64_t want = ((int64_t)a.n + block - 1) / block;  // (n / 32 spans) / (block / 32 warps)
+  const int64_t cap = (int64_t)sm_count() * (2048 / block);
+  return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
 template <bool PATCHY, int NP>
 static void launch_edge(const KArgs& a, int block, cudaStream_t st) {
-  // persistent grid: enough resident warps to cover every SM, pairs taken in warp-sized chunks
-  int64_t want = (a.max_pairs + block - 1) / block;
-  int64_t cap = (int64_t)sm_count() * (2048 / block);
-  const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  // persistent grid: enough resident warps to cover every SM, each taking spans of 32 half-list rows
+  const int grid = edge_grid(a, block);
   if (a.precision == MD_MIXED) k_edge_mixed<PATCHY, NP><<<grid, block, 0, st>>>(a);
   else k_edge_fp64<PATCHY, NP><<<grid, block, 0, st>>>(a);
 }
@@ -122,10 +135,7 @@ __global__ void k_edge_store_reduce(KArgs a) {
 
 template <bool PATCHY, int NP>
 static void launch_edge_store(const KArgs& a, int block, cudaStream_t st) {
-  int64_t want = (a.max_pairs + block - 1) / block;
-  int64_t cap = (int64_t)sm_count() * (2048 / block);
-  const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-  k_edge_store<PATCHY, NP><<<grid, block, 0, st>>>(a);
+  k_edge_store<PATCHY, NP><<<edge_grid(a, block), block, 0, st>>>(a);
 }
 
 template <bool PATCHY, int NP>

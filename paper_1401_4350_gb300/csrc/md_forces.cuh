@@ -148,6 +148,51 @@ __device__ __forceinline__ float exact_r2u(int dx, int dy, int dz) {
   return __fmaf_rn(__uint2float_rn(hi), 4294967296.0f, __uint2float_rn(lo));
 }
 
+// ---- accurate repulsive core (WCA, cubic boxes) --------------------------------------------------
+// In a sparse WCA fluid the largest forces are collisions at r ~ 0.85-0.9 sigma, tens of times the rms
+// force; the FP32 chain (sigma/r)^2 -> ^6 -> ^12 multiplies the roundings of r^2 and of the reciprocal by
+// six to twelve and leaves about 1e-6 of such a pair force, which is 1e-5 of the rms force.  For these
+// pairs the scalar part of the force is carried in unevaluated sums of two FP32 numbers (hi + lo, about
+// 2^-44 relative) from the exact integer r^2 on, and rounded to FP32 once at the end.
+struct FF {
+  float hi, lo;
+};
+
+// (a.hi + a.lo)(b.hi + b.lo) to about 2^-44 relative: the product of the high parts is split exactly
+// (its rounding error by a fused multiply-add), the cross terms are added to the low part.
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return {p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e))};
+}
+
+// For the exact integer squared separation s (units u^2) and t = C / s, C = sigma^2 / u^2: the force
+// scalar (2 t^7 - t^4) K, rounded once to FP32, and t^3, t^6 for the energy and virial sums.
+__device__ __forceinline__ float core_ff(const KArgs& a, unsigned long long s, float khi, float klo, float& t3f,
+                                         float& t6f) {
+  // s = h + l exactly up to the rounding of l (h is integer-valued, so s - h is an exact integer)
+  const float h = __ull2float_rn(s);
+  const float l = __ll2float_rn((long long)(s - __float2ull_rn(h)));
+  // t = C / (h + l): a refined quotient t0 and its correction from the remainder C - t0 (h + l)
+  const float y = frcp_refined(h);
+  const float t0 = __fmul_rn(a.core_c_hi, y);
+  const float rem = __fmaf_rn(-t0, l, __fadd_rn(__fmaf_rn(-t0, h, a.core_c_hi), a.core_c_lo));
+  const FF t = {t0, __fmul_rn(rem, y)};
+  const FF t3 = ff_mul(ff_mul(t, t), t);
+  // 2 t^7 - t^4 = t^4 (2 t^3 - 1); the rounding of 2 t^3 - 1 is kept (it cancels at the WCA cut-off)
+  const float wh = __fmaf_rn(2.f, t3.hi, -1.f);
+  const float wl = __fmaf_rn(2.f, t3.lo, two_sum_err(__fmul_rn(2.f, t3.hi), -1.f, wh));
+  const FF f = ff_mul(ff_mul(ff_mul(t3, t), {wh, wl}), {khi, klo});
+  t3f = __fadd_rn(t3.hi, t3.lo);
+  t6f = __fmul_rn(t3f, t3f);
+  return __fadd_rn(f.hi, f.lo);
+}
+
+__device__ __forceinline__ unsigned long long exact_s(int dx, int dy, int dz) {
+  return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+         (unsigned long long)((long long)dz * dz);
+}
+
 // Lennard-Jones terms in units u: returns t = -fs r^2 (dimensionless), fsu = -t / r2_u (so that the
 // force is fsu * d_u / u) and the shifted pair energy.
 __device__ __forceinline__ void lj_terms_u(const KArgs& a, float r2u, float& fsu, float& t, float& pe) {
@@ -165,13 +210,27 @@ __device__ __forceinline__ bool iso_inside_u(const KArgs& a, float r2u, int i, i
   return in;
 }
 
+// The isotropic pair of a cubic box through the accurate core: force, energy and -fs r^2.
+__device__ __forceinline__ void iso_core_ff(const KArgs& a, const int3& ds, Vec3<float>& F, float& e, float& w) {
+  float t3, t6;
+  const float g = core_ff(a, exact_s(ds.x, ds.y, ds.z), a.core_ke_hi, a.core_ke_lo, t3, t6);
+  F = {g * (float)ds.x, g * (float)ds.y, g * (float)ds.z};
+  e = a.lj_c4_f * (t6 - t3) - a.lj_shift_f;
+  w = a.lj_c24_f * (2.f * t6 - t3);
+}
+
 // Isotropic pair of a cubic box from the integer separation ds.
 __device__ __forceinline__ PairOut<float> iso_pair_cubic(const KArgs& a, const int3& ds, int i, int j) {
   PairOut<float> o;
   const float r2u = exact_r2u(ds.x, ds.y, ds.z);
+  const bool in = iso_inside_u(a, r2u, i, j);
+  if (a.accurate_core && in) {
+    iso_core_ff(a, ds, o.F, o.e, o.w);
+    o.ti = o.tj = {0.f, 0.f, 0.f};
+    return o;
+  }
   float fsu, t, pe;
   lj_terms_u(a, r2u, fsu, t, pe);
-  const bool in = iso_inside_u(a, r2u, i, j);
   const float g = in ? fsu * a.inv_unit_f : 0.f;
   o.F = {g * (float)ds.x, g * (float)ds.y, g * (float)ds.z};
   o.e = in ? pe : 0.f;
@@ -257,9 +316,11 @@ __device__ __forceinline__ PairOut<double> patchy_pair(const KArgs& a, const Vec
 // few that remain (the bonds) are evaluated in FP64 from the FP64 positions and lab-frame sites:
 // (r_ab / delta)^10 multiplies the relative error of r_ab by ten, and the 2^-33 L quantisation of the
 // fixed-point coordinates alone would leave the strongest torques of a box of L = 96 sigma about 4e-5 of
-// the rms torque (over all particles) off.  In FP64 each pair's force, torques and energy carry one
-// rounding to FP32.  The centre core is FP32 (WCA) or FP64 ((sigma/r)^200, whose exponent amplifies even
-// the fixed-point quantisation of r).
+// the rms torque (over all particles) off.  In a bonded patchy liquid the largest forces are those of
+// cores pressed together by bonds, tens of times the rms force, and plain FP32 arithmetic on the steep
+// core (about 1e-6 relative) would put them near 1e-5 of the rms force off: the WCA core goes through the
+// accurate core (cubic box) or FP64 (other boxes), the (sigma/r)^200 core through FP64.  A pair's FP64
+// terms are rounded to FP32 once.
 template <int NP, bool WANT_TJ>
 __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, const int3& ds, const Vec3<float>& d,
                                                             float r2, const IPatches<NP>& Pi, int i, int j) {
@@ -267,29 +328,29 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
   o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
   o.e = o.w = 0.f;
   if (!(r2 < a.rc2_f)) return o;
-  if (a.pow_core) {
-    const Vec3<double> dd = sep_fp64(a.pos[i], a.pos[j], a);
-    double fs, pe;
-    pow_core_terms(a, dd.x * dd.x + dd.y * dd.y + dd.z * dd.z, fs, pe);
-    o.F = {(float)(fs * dd.x), (float)(fs * dd.y), (float)(fs * dd.z)};
-    o.e = (float)pe;
-  } else if (a.cubic) {
-    const PairOut<float> c = iso_pair_cubic(a, ds, i, j);
-    o.F = c.F;
-    o.e = c.e;
-  } else if (iso_inside<float>(a, r2, i, j)) {
-    float fs, pe;
-    lj_terms(a, r2, fs, pe);
-    o.F = {fs * d.x, fs * d.y, fs * d.z};
-    o.e = pe;
+  Vec3<double> F = {0.0, 0.0, 0.0}, ti = {0.0, 0.0, 0.0}, tj = {0.0, 0.0, 0.0}, dd = {0.0, 0.0, 0.0};
+  double e = 0.0;
+  bool any = false;  // dd holds the FP64 separation and F, e the pair's FP64 terms
+  Vec3<float> Fc = {0.f, 0.f, 0.f};  // the core force and energy when they come from the accurate core
+  float ec = 0.f;
+  if (a.pow_core || (!a.cubic && r2 < a.rwca2_hi_f)) {
+    // FP64 core: the FP32 r^2 screens out the pairs clearly beyond its range, FP64 decides the rest
+    dd = sep_fp64(a.pos[i], a.pos[j], a);
+    any = true;
+    const double r2d = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
+    double fs = 0.0, pe = 0.0;
+    if (a.pow_core) pow_core_terms(a, r2d, fs, pe);
+    else if (r2d < a.rwca2_d) lj_terms(a, r2d, fs, pe);
+    F = {fs * dd.x, fs * dd.y, fs * dd.z};
+    e = pe;
+  } else if (a.cubic && iso_inside_u(a, exact_r2u(ds.x, ds.y, ds.z), i, j)) {
+    float wc;
+    iso_core_ff(a, ds, Fc, ec, wc);
   }
   if (r2 < a.patch_reach2_f) {
     const IPatches<NP> Pj = load_ipatches<NP>(a, j);
     const double4_32a* li = a.patch_lab_d + (size_t)i * MD_MAX_PATCH;
     const double4_32a* lj = a.patch_lab_d + (size_t)j * MD_MAX_PATCH;
-    Vec3<double> F = {0.0, 0.0, 0.0}, ti = {0.0, 0.0, 0.0}, tj = {0.0, 0.0, 0.0}, dd = {0.0, 0.0, 0.0};
-    double e = 0.0;
-    bool any = false;
 #pragma unroll
     for (int pa = 0; pa < NP; pa++) {
       const int bx = ds.x - Pi.p[pa].x, by = ds.y - Pi.p[pa].y, bz = ds.z - Pi.p[pa].z;
@@ -331,12 +392,15 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
         }
       }
     }
-    if (any) {
-      o.F = {(float)((double)o.F.x + F.x), (float)((double)o.F.y + F.y), (float)((double)o.F.z + F.z)};
-      o.e = (float)((double)o.e + e);
-      o.ti = {(float)ti.x, (float)ti.y, (float)ti.z};
-      if (WANT_TJ) o.tj = {(float)tj.x, (float)tj.y, (float)tj.z};
-    }
+  }
+  if (any) {
+    o.F = {(float)((double)Fc.x + F.x), (float)((double)Fc.y + F.y), (float)((double)Fc.z + F.z)};
+    o.e = (float)((double)ec + e);
+    o.ti = {(float)ti.x, (float)ti.y, (float)ti.z};
+    if (WANT_TJ) o.tj = {(float)tj.x, (float)tj.y, (float)tj.z};
+  } else {
+    o.F = Fc;
+    o.e = ec;
   }
   o.w = -(d.x * o.F.x + d.y * o.F.y + d.z * o.F.z);
   return o;
@@ -660,8 +724,9 @@ __device__ __forceinline__ void gather4(const KArgs& a, const Rows& R, const int
 }
 
 // One group of four list entries of particle si, from their gathered coordinates sj.  LIVE: some entries
-// may lie past the count.  keep (PRUNE): the entries closer than rc + prune_skin, as bits 0..3.
-template <bool LIVE, bool PRUNE = false>
+// may lie past the count.  keep (PRUNE): the entries closer than rc + prune_skin, as bits 0..3.  ACC: the
+// pairs inside the cut-off go through the accurate core instead of the packed FP32 arithmetic (WCA).
+template <bool LIVE, bool PRUNE = false, bool ACC = false>
 __device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, const uint4 sj[4], int lim,
                                             IsoAcc& A, unsigned* keep = nullptr) {
   float r2[4], dx[4], dy[4], dz[4];
@@ -686,8 +751,8 @@ __device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, con
     const float2 x = make_float2(r2[2 * h], r2[2 * h + 1]);
     const float2 off = __fadd2_rn(x, thr2);
     A.bmin = fminf(A.bmin, fminf(fabsf(off.x), fabsf(off.y)));
-    const bool in0 = (!LIVE || 2 * h < lim) && x.x < a.rwca2_s;
-    const bool in1 = (!LIVE || 2 * h + 1 < lim) && x.y < a.rwca2_s;
+    const bool in0 = !ACC && (!LIVE || 2 * h < lim) && x.x < a.rwca2_s;
+    const bool in1 = !ACC && (!LIVE || 2 * h + 1 < lim) && x.y < a.rwca2_s;
     float2 rn = neg_rcp2(x);
     rn.x = in0 ? rn.x : 0.f;  // pairs outside contribute exact zeros from here on
     rn.y = in1 ? rn.y : 0.f;
@@ -714,6 +779,21 @@ __device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, con
   kahan_add2(A.fx, A.cx, gx);
   kahan_add2(A.fy, A.cy, gy);
   kahan_add2(A.fz, A.cz, gz);
+  if (ACC) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      if (!((!LIVE || u < lim) && r2[u] < a.rwca2_s)) continue;  // the same FP32 decision as the packed path
+      const int ix = (int)(sj[u].x - si.x), iy = (int)(sj[u].y - si.y), iz = (int)(sj[u].z - si.z);
+      float t3, t6;
+      const float fs = core_ff(a, exact_s(ix, iy, iz), a.core_kv_hi, a.core_kv_lo, t3, t6);  // (2 s12 - s6) / r^2
+      kahan_add(A.fx.x, A.cx.x, fs * dx[u]);
+      kahan_add(A.fy.x, A.cy.x, fs * dy[u]);
+      kahan_add(A.fz.x, A.cz.x, fs * dz[u]);
+      A.s12.x += t6;
+      A.s6.x += t3;
+      A.nin += 1;
+    }
+  }
 }
 
 // (s + lo) * (hi + lo') with the product's rounding error kept: FP64 result from FP32 operations
@@ -741,7 +821,7 @@ __device__ __forceinline__ void store_iso(const KArgs& a, int gt, int tpp, const
 
 // AHEAD: gather each group's partner coordinates one group ahead (more registers, more loads in flight;
 // the batched kernel, which runs at a larger register budget per thread, keeps the plain order).
-template <int TPP, class Rows, class Sink = NoPrune, bool AHEAD = true>
+template <int TPP, class Rows, class Sink = NoPrune, bool AHEAD = true, bool ACC = false>
 __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R, IsoResult& res,
                                                       Sink* sink = nullptr) {
   const int i = gt / TPP, l = gt % TPP;
@@ -777,7 +857,7 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
       else
         gather4(a, R, cur, sj);
       unsigned keep = 0u;
-      iso_group_c<false, Sink::kPrune>(a, si, sj, 4, A, &keep);
+      iso_group_c<false, Sink::kPrune, ACC>(a, si, sj, 4, A, &keep);
       if (Sink::kPrune) sink->take(a, cur, keep);
       cur = nxt;
       if (AHEAD) {
@@ -788,7 +868,7 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
     if (g < ng) {  // the partial last group
       if (!AHEAD) gather4(a, R, cur, sj);
       unsigned keep = 0u;
-      iso_group_c<true, Sink::kPrune>(a, si, sj, cnt - 4 * g, A, &keep);
+      iso_group_c<true, Sink::kPrune, ACC>(a, si, sj, cnt - 4 * g, A, &keep);
       if (Sink::kPrune) sink->take(a, cur, keep);
     }
     if (Sink::kPrune) sink->finish(a, si);
@@ -858,15 +938,16 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
   }
 }
 
-template <int TPP, bool AHEAD = true>
+template <int TPP, bool AHEAD = true, bool ACC = false>
 __device__ __forceinline__ void vertex_iso_cubic_eval(const KArgs& a, int gt, IsoResult& res) {
   if (!full_list_current(a)) return;
   const GlobalRows R = global_rows(a, gt / TPP, false);
-  vertex_iso_cubic_rows<TPP, GlobalRows, NoPrune, AHEAD>(a, gt, R, res);
+  vertex_iso_cubic_rows<TPP, GlobalRows, NoPrune, AHEAD, ACC>(a, gt, R, res);
 }
 
 // The fused step's walk with an inner list (one thread per particle, cubic box): the inner list, or,
 // when a prune is due, the Verlet list, writing the new inner list on the way.
+template <bool ACC>
 __device__ __forceinline__ void vertex_iso_inner_eval(const KArgs& a, int i, bool prune, IsoResult& res) {
   if (!full_list_current(a)) return;
   if (prune) {
@@ -875,15 +956,16 @@ __device__ __forceinline__ void vertex_iso_inner_eval(const KArgs& a, int i, boo
     S.i = i;
     S.cnt = 0;
     S.b0 = S.b1 = S.b2 = S.b3 = 0;
-    vertex_iso_cubic_rows<1>(a, i, R, res, &S);
+    vertex_iso_cubic_rows<1, GlobalRows, InnerPrune, !ACC, ACC>(a, i, R, res, &S);
   } else {
     const GlobalRows R = global_rows(a, i, true);
-    vertex_iso_cubic_rows<1>(a, i, R, res);
+    vertex_iso_cubic_rows<1, GlobalRows, NoPrune, !ACC, ACC>(a, i, R, res);
   }
 }
 
 // The block-local list: the block (MD_LOCAL_BLOCK threads, one per slot) first stages its halo's
 // coordinates in shared memory, cell by cell, one warp per cell.
+template <bool ACC>
 __device__ __forceinline__ void vertex_iso_local_body(const KArgs& a, uint4* halo_smem) {
   const int t = threadIdx.x, b = blockIdx.x;
   const int i = b * MD_LOCAL_BLOCK + t;
@@ -907,15 +989,15 @@ __device__ __forceinline__ void vertex_iso_local_body(const KArgs& a, uint4* hal
   }
   __syncthreads();
   IsoResult res;
-  vertex_iso_cubic_rows<1>(a, i, R, res);
+  vertex_iso_cubic_rows<1, LocalRows, NoPrune, !ACC, ACC>(a, i, R, res);
   store_iso(a, i, 1, res);
 }
 
 // The isotropic mixed vertex evaluation over the int32 full list (cubic boxes: the integer-r^2 path)
-template <int TPP, bool CUBIC, bool AHEAD = true>
+template <int TPP, bool CUBIC, bool AHEAD = true, bool ACC = false>
 __device__ __forceinline__ void vertex_iso_mixed_eval(const KArgs& a, int gt, IsoResult& res) {
   if (CUBIC) {
-    vertex_iso_cubic_eval<TPP, AHEAD>(a, gt, res);
+    vertex_iso_cubic_eval<TPP, AHEAD, ACC>(a, gt, res);
     return;
   }
   if (!full_list_current(a)) return;
@@ -1012,22 +1094,24 @@ __device__ __forceinline__ void vertex_iso_mixed_eval(const KArgs& a, int gt, Is
   }
 }
 
-template <int TPP, bool CUBIC, bool AHEAD = true>
+template <int TPP, bool CUBIC, bool AHEAD = true, bool ACC = false>
 __device__ __forceinline__ void vertex_iso_mixed_body(const KArgs& a, int gt) {
   IsoResult res;
-  vertex_iso_mixed_eval<TPP, CUBIC, AHEAD>(a, gt, res);
+  vertex_iso_mixed_eval<TPP, CUBIC, AHEAD, ACC>(a, gt, res);
   store_iso(a, gt, TPP, res);
 }
 
-template <int TPP, bool CUBIC>
+// ACC: the accurate repulsive core (a.accurate_core, cubic boxes only)
+template <int TPP, bool CUBIC, bool ACC>
 __global__ void __launch_bounds__(256, 4) k_vertex_iso_mixed(KArgs a) {
   if (TPP == 1 && CUBIC && a.local_ok && (a.status[MD_STATUS_LISTS] & MD_LIST_FULL_LOCAL)) {
     // launched with MD_LOCAL_BLOCK threads and kLocalSmem halo slots of dynamic shared memory
     extern __shared__ uint4 halo_smem[];
-    vertex_iso_local_body(a, halo_smem);
+    vertex_iso_local_body<ACC>(a, halo_smem);
     return;
   }
-  vertex_iso_mixed_body<TPP, CUBIC>(a, blockIdx.x * blockDim.x + threadIdx.x);
+  // the accurate core is for sparse systems (short lists): no gathers one group ahead, fewer registers
+  vertex_iso_mixed_body<TPP, CUBIC, !ACC, ACC>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int TPP>
@@ -1144,21 +1228,69 @@ __device__ __forceinline__ void run_bounds(int key, int lane, bool& head, int& e
   end = above ? (__ffs(above) - 1) : 32;
 }
 
-// Pairs [32 warp, E) of the half list, warp-sized chunks strided by nwarps warps.
+// ---- the half list in CSR form ------------------------------------------------------------------
+// Row i of the half list holds the partners j > i of slot i at half_j[half_start[i] .. half_start[i + 1]).
+// A warp walks a span of 32 consecutive rows: lane l holds the start of row r0 + l, the span's pairs are
+// taken in warp-sized chunks, and the row of a pair is the last lane whose start is not above it (a
+// binary search over the lanes, five shuffles).  The rows of a chunk are consecutive, so lanes of equal
+// i form runs, as the warp-segmented i-side sums need.
+constexpr int kSpanRows = 32;
+
+struct HalfSpan {
+  int r0;          // first row of the span
+  int start;       // lane l: start of row r0 + l relative to e0 (rows past n: the span's end)
+  int64_t e0, e1;  // the span's pairs
+};
+
+__device__ __forceinline__ HalfSpan half_span(const KArgs& a, int r0, int64_t E) {
+  const int lane = threadIdx.x & 31;
+  HalfSpan S;
+  S.r0 = r0;
+  S.e0 = min(a.half_start[r0], E);
+  S.e1 = min(a.half_start[min(r0 + kSpanRows, a.n)], E);
+  S.start = (int)(min(a.half_start[min(r0 + lane, a.n)], E) - S.e0);
+  return S;
+}
+
+// Row of the pair at offset q of the span (0 <= q < e1 - e0); every lane of the warp must call it.
+__device__ __forceinline__ int half_row(const HalfSpan& S, int q) {
+  int lo = 0;
+#pragma unroll
+  for (int step = kSpanRows / 2; step > 0; step >>= 1) {
+    const int s = __shfl_sync(0xffffffffu, S.start, lo + step);
+    if (s <= q) lo += step;
+  }
+  return S.r0 + lo;
+}
+
+// One chunk of a span: this lane's pair (i, j), or (-1, -1) past the span's end or for an index that is
+// out of range (a list that was never built).  jn is the chunk's partner, loaded one chunk ahead.
+__device__ __forceinline__ int2 half_pair(const KArgs& a, const HalfSpan& S, int64_t base, int j) {
+  const int lane = threadIdx.x & 31;
+  const int i = half_row(S, (int)(base - S.e0) + lane);
+  if (base + lane >= S.e1 || (unsigned)j >= (unsigned)a.n) return make_int2(-1, -1);
+  return make_int2(i, j);
+}
+
+__device__ __forceinline__ int half_j_at(const KArgs& a, const HalfSpan& S, int64_t base) {
+  const int64_t e = base + (threadIdx.x & 31);
+  return e < S.e1 ? __ldcs(a.half_j + e) : -1;
+}
+
+// The pairs of the span of rows [r0, r0 + 32), one thread per pair.
 template <bool PATCHY, int NP>
-__device__ __forceinline__ void edge_mixed_body(const KArgs& a, int64_t warp, int64_t nwarps, int64_t E) {
+__device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t E) {
   const int lane = threadIdx.x & 31;
   const size_t n = (size_t)a.n;
   float4* fhi = a.acc;
   float4* flo = a.acc + n;
   float4* thi = a.acc + 2 * n;
   float4* tlo = a.acc + 3 * n;
-  int2 pn = (warp * 32 + lane < E) ? __ldcs(a.pairs + warp * 32 + lane) : make_int2(-1, -1);
-  for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
-    int2 p = pn;  // this chunk's pair; the next chunk's is loaded before the arithmetic
-    const int64_t en = base + nwarps * 32 + lane;
-    pn = en < E ? __ldcs(a.pairs + en) : make_int2(-1, -1);
-    if ((unsigned)p.x >= (unsigned)a.n || (unsigned)p.y >= (unsigned)a.n) p = make_int2(-1, -1);
+  const HalfSpan S = half_span(a, r0, E);
+  int jn = half_j_at(a, S, S.e0);
+  for (int64_t base = S.e0; base < S.e1; base += 32) {
+    const int2 p = half_pair(a, S, base, jn);  // this chunk's pair; the next chunk's partner is loaded now
+    jn = half_j_at(a, S, base + 32);
     const bool ok = p.x >= 0;
     PairOut<float> o;
     o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
@@ -1208,26 +1340,30 @@ __device__ __forceinline__ void edge_mixed_body(const KArgs& a, int64_t warp, in
   }
 }
 
+__device__ __forceinline__ int64_t half_pairs(const KArgs& a) { return min(a.half_start[a.n], a.max_pairs); }
+
 template <bool PATCHY, int NP>
 __global__ void __launch_bounds__(256) k_edge_mixed(KArgs a) {
-  const int64_t E = min(a.half_start[a.n], a.max_pairs);
-  edge_mixed_body<PATCHY, NP>(a, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                            ((int64_t)gridDim.x * blockDim.x) >> 5, E);
+  // persistent warps over the spans of 32 rows
+  const int64_t E = half_pairs(a);
+  const int spans = (a.n + kSpanRows - 1) / kSpanRows;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < spans; s += nw)
+    edge_mixed_span<PATCHY, NP>(a, s * kSpanRows, E);
 }
 
-// Pairs [32 warp, E) of the half list, warp-sized chunks strided by nwarps warps.
+// The pairs of the span of rows [r0, r0 + 32), one thread per pair, FP64.
 template <bool PATCHY, int NP>
-__device__ __forceinline__ void edge_fp64_body(const KArgs& a, int64_t warp, int64_t nwarps, int64_t E) {
+__device__ __forceinline__ void edge_fp64_span(const KArgs& a, int r0, int64_t E) {
   const int lane = threadIdx.x & 31;
   double* f = (double*)a.force;
   double* vir = a.virial;
   double* t = (double*)a.torque;
-  int2 pn = (warp * 32 + lane < E) ? __ldcs(a.pairs + warp * 32 + lane) : make_int2(-1, -1);
-  for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
-    int2 p = pn;  // this chunk's pair; the next chunk's is loaded before the arithmetic
-    const int64_t en = base + nwarps * 32 + lane;
-    pn = en < E ? __ldcs(a.pairs + en) : make_int2(-1, -1);
-    if ((unsigned)p.x >= (unsigned)a.n || (unsigned)p.y >= (unsigned)a.n) p = make_int2(-1, -1);
+  const HalfSpan S = half_span(a, r0, E);
+  int jn = half_j_at(a, S, S.e0);
+  for (int64_t base = S.e0; base < S.e1; base += 32) {
+    const int2 p = half_pair(a, S, base, jn);
+    jn = half_j_at(a, S, base + 32);
     const bool ok = p.x >= 0;
     PairOut<double> o;
     o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
@@ -1282,9 +1418,11 @@ __device__ __forceinline__ void edge_fp64_body(const KArgs& a, int64_t warp, int
 
 template <bool PATCHY, int NP>
 __global__ void __launch_bounds__(256) k_edge_fp64(KArgs a) {
-  const int64_t E = min(a.half_start[a.n], a.max_pairs);
-  edge_fp64_body<PATCHY, NP>(a, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                            ((int64_t)gridDim.x * blockDim.x) >> 5, E);
+  const int64_t E = half_pairs(a);
+  const int spans = (a.n + kSpanRows - 1) / kSpanRows;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < spans; s += nw)
+    edge_fp64_span<PATCHY, NP>(a, s * kSpanRows, E);
 }
 
 // Mixed edge path: FP32 atomic sums plus their compensation terms become the FP64 result.
@@ -1550,11 +1688,10 @@ __device__ __forceinline__ void newton_finalize_one(const KArgs& a, int i) {
 // ------------------------------------------------------------------------------------------------
 
 template <bool PATCHY, int NP>
-__device__ __forceinline__ void edge_store_mixed_one(const KArgs& a, int64_t k) {
+__device__ __forceinline__ void edge_store_mixed_one(const KArgs& a, int64_t k, int2 p) {
   float4* A = (float4*)a.estore;
   float4* Bk = A + a.max_pairs;
   float4* C = A + 2 * a.max_pairs;
-  int2 p = __ldcs(a.pairs + k);
   PairOut<float> o;
   o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
   o.e = o.w = 0.f;
@@ -1580,11 +1717,10 @@ __device__ __forceinline__ void edge_store_mixed_one(const KArgs& a, int64_t k) 
 }
 
 template <bool PATCHY, int NP>
-__device__ __forceinline__ void edge_store_fp64_one(const KArgs& a, int64_t k) {
+__device__ __forceinline__ void edge_store_fp64_one(const KArgs& a, int64_t k, int2 p) {
   double4_32a* A = (double4_32a*)a.estore;
   double4_32a* Bk = A + a.max_pairs;
   double4_32a* C = A + 2 * a.max_pairs;
-  int2 p = __ldcs(a.pairs + k);
   PairOut<double> o;
   o.F = o.ti = o.tj = {0.0, 0.0, 0.0};
   o.e = o.w = 0.0;
@@ -1607,10 +1743,21 @@ __device__ __forceinline__ void edge_store_fp64_one(const KArgs& a, int64_t k) {
 
 template <bool PATCHY, int NP>
 __global__ void __launch_bounds__(256) k_edge_store(KArgs a) {
-  const int64_t E = min(a.half_start[a.n], a.max_pairs);
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
-    if (a.precision == MD_MIXED) edge_store_mixed_one<PATCHY, NP>(a, k);
-    else edge_store_fp64_one<PATCHY, NP>(a, k);
+  // persistent warps over the spans of 32 rows; each pair's slot k of the store gets its terms
+  const int64_t E = half_pairs(a);
+  const int spans = (a.n + kSpanRows - 1) / kSpanRows;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int sp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); sp < spans; sp += nw) {
+    const HalfSpan S = half_span(a, sp * kSpanRows, E);
+    int jn = half_j_at(a, S, S.e0);
+    for (int64_t base = S.e0; base < S.e1; base += 32) {
+      const int2 p = half_pair(a, S, base, jn);
+      jn = half_j_at(a, S, base + 32);
+      const int64_t k = base + (threadIdx.x & 31);
+      if (k >= S.e1) continue;
+      if (a.precision == MD_MIXED) edge_store_mixed_one<PATCHY, NP>(a, k, p);
+      else edge_store_fp64_one<PATCHY, NP>(a, k, p);
+    }
   }
 }
 

@@ -11,7 +11,8 @@
 //                        [n][MD_MAX_PATCH] fixed-point offsets, then the double4_32a block
 //   nbr                  int32   [ceil(max_neigh/4)][n][4] full list: entry k of slot i at
 //                        ((k/4) n + i) 4 + k%4 (int4 groups, coalesced per warp)
-//   pairs                int2    [max_pairs]    half list (i, j), i < j, sorted by i
+//   half_start, half_j   int64 [n + 1], int32 [max_pairs]  half list in CSR form: row i holds the
+//                        partners j > i of slot i at half_j[half_start[i] .. half_start[i + 1])
 //   force / force_lo     float4 or double4_32a [n]  (F, E_i) and (compensation of F, W_i)
 //   torque / torque_lo   float4 or double4_32a [n]
 #pragma once
@@ -100,6 +101,10 @@ struct KArgs {
   float rwca2_s, rwca2_band_s;           // cut-off^2 and the half-width of its FP64-decided band
   float rwca2_lo_s, rwca2_hi_s;          // the band itself
   float fscale_hi, fscale_lo;            // -24 eps / (u 2^r2_shift) as an unevaluated FP32 sum
+  // accurate repulsive core (WCA in a cubic box): C = sigma^2 / u^2 and the force factors of the vertex
+  // (2^r2_shift / C) and pair (-24 eps u / sigma^2) paths, each as an unevaluated FP32 sum
+  int32_t accurate_core;
+  float core_c_hi, core_c_lo, core_kv_hi, core_kv_lo, core_ke_hi, core_ke_lo;
   double rwca2_lo_d, rwca2_hi_d;
   // patchy
   double inv_delta2_d, eps_p_d, pgain_d;  // 1/delta^2, eps_p, 5 eps_p / delta^2
@@ -137,7 +142,7 @@ struct KArgs {
   int32_t* nbr;
   int32_t* nbr_count;
   int64_t* half_start;
-  int2* pairs;
+  int32_t* half_j;       // half-list partners, rows from half_start
   double4_32a* force;   // (F, E_i) result, FP64
   double* virial;        // W_i result
   double4_32a* torque;   // (tau, 0) result, patchy

@@ -20,7 +20,8 @@ namespace mdgb {
 
 // LAST: the closing phase of a call instead: the forces of the last step (also stored, for the caller and
 // the next call's opening kick), its closing half kick and its energies; no drift.
-template <int TPP, bool CUBIC, bool LAST>
+// ACC: the accurate repulsive core (a.accurate_core, cubic boxes only).
+template <int TPP, bool CUBIC, bool LAST, bool ACC = false>
 __global__ void __launch_bounds__(256, 4) k_vertex_step_mixed(KArgs a) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   // the owner of each particle integrates it (its force is zero if the list was not current, which
@@ -35,9 +36,9 @@ __global__ void __launch_bounds__(256, 4) k_vertex_step_mixed(KArgs a) {
   }
   IsoResult res;
   if (TPP == 1 && CUBIC && a.inner)  // the inner list; pruned again from the Verlet list when due
-    vertex_iso_inner_eval(a, gt, a.scr_words[SCR_PRUNE] != 0u, res);
+    vertex_iso_inner_eval<ACC>(a, gt, a.scr_words[SCR_PRUNE] != 0u, res);
   else
-    vertex_iso_mixed_eval<TPP, CUBIC>(a, gt, res);
+    vertex_iso_mixed_eval<TPP, CUBIC, !ACC, ACC>(a, gt, res);
   if (LAST) store_iso(a, gt, TPP, res);
   integrate_core<true>(a, LAST ? 2 : 1, i, make_double4_32a(res.fx, res.fy, res.fz, res.e), res.w);
 }
@@ -46,7 +47,14 @@ template <bool LAST>
 static void launch_fused_kernel(const KArgs& a, int block, cudaStream_t st) {
   const int64_t threads = (int64_t)a.n * a.tpp;
   const int grid = (int)((threads + block - 1) / block);
-  if (a.cubic) {
+  if (a.cubic && a.accurate_core) {
+    switch (a.tpp) {
+      case 1: k_vertex_step_mixed<1, true, LAST, true><<<grid, block, 0, st>>>(a); break;
+      case 2: k_vertex_step_mixed<2, true, LAST, true><<<grid, block, 0, st>>>(a); break;
+      case 4: k_vertex_step_mixed<4, true, LAST, true><<<grid, block, 0, st>>>(a); break;
+      default: k_vertex_step_mixed<8, true, LAST, true><<<grid, block, 0, st>>>(a); break;
+    }
+  } else if (a.cubic) {
     switch (a.tpp) {
       case 1: k_vertex_step_mixed<1, true, LAST><<<grid, block, 0, st>>>(a); break;
       case 2: k_vertex_step_mixed<2, true, LAST><<<grid, block, 0, st>>>(a); break;

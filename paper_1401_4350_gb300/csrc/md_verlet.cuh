@@ -135,7 +135,8 @@ __device__ __forceinline__ void verlet_note_length(const KArgs& a, int cnt) {
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(a.status + MD_STATUS_NEED_NEIGH, m);
 }
 
-// Half-list entries (i, j), j > i, of slot i; slot 0 also records the list length and overflow.
+// Half-list row of slot i: its partners j > i in full-list order; slot 0 also records the list length
+// and overflow.
 __device__ __forceinline__ void verlet_half_one(const KArgs& a, int i) {
   if (i == 0) {
     const int64_t total = a.half_start[a.n];
@@ -149,7 +150,7 @@ __device__ __forceinline__ void verlet_half_one(const KArgs& a, int i) {
   for (int k = 0; k < cnt; k++) {
     const int j = a.nbr[nbr_index(k, i, n)];
     if (j > i) {
-      if (w < a.max_pairs) a.pairs[w] = make_int2(i, j);
+      if (w < a.max_pairs) a.half_j[w] = j;
       w++;
     }
   }
@@ -167,7 +168,7 @@ __device__ __forceinline__ void jindex_count_one(const KArgs& a, int j) {
 
 // Pair k of the half list into its partner's row (fill counters in a.rank, zeroed before).
 __device__ __forceinline__ void jindex_scatter_one(const KArgs& a, int64_t k) {
-  const int j = a.pairs[k].y;
+  const int j = a.half_j[k];
   if ((unsigned)j >= (unsigned)a.n) return;
   const int slot = atomicAdd(a.rank + j, 1);
   const int64_t w = a.jstart[j] + slot;

@@ -25,6 +25,7 @@ WORKLOADS = {
     "lj524288": lambda: systems.make_lj(524_288, 0.85, 1.0, seed=1001),
     "lj262144": lambda: systems.make_lj(262_144, 0.85, 1.0, seed=1001),
     "wca1m": lambda: systems.make_wca(1_048_576, 0.2, seed=1002),
+    "wca524288": lambda: systems.make_wca(524_288, 0.2, seed=1002),
     "patchy262k": lambda: systems.make_patchy(262_144, 0.3, seed=1003),
 }
 
@@ -40,7 +41,10 @@ def main(argv=None):
     ap.add_argument("--tpp", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--order", default="rows", choices=["rows", "hilbert"])
-    ap.add_argument("--equilibrate", type=int, default=0, help="MD steps (graph) before the timed launches")
+    ap.add_argument("--equilibrate", type=int, default=0, help="MD steps before the timed launches")
+    ap.add_argument("--direct", action="store_true",
+                    help="equilibrate with direct launches instead of graphs (so that ncu counts them and can skip "
+                         "them with -s)")
     a = ap.parse_args(argv)
     mdbuild.build()
     B.load()
@@ -52,7 +56,7 @@ def main(argv=None):
                      fuse_step=a.fuse, prune_skin=a.prune)
     sim.prepare(path)
     if a.equilibrate > 0:  # time the liquid rather than the initial lattice
-        sim.step(a.equilibrate, path, use_graph=True)
+        sim.step(a.equilibrate, path, use_graph=not a.direct)
         torch.cuda.synchronize()
     if a.what == "forces":
         fn = sim.forces_vertex if path == B.MD_VERTEX else sim.forces_edge

@@ -304,7 +304,9 @@ class Simulation:
         n = self.system.n
         hs = self.view("half_start", torch.int64, n + 1)
         total = int(hs[-1].item())
-        pairs = self.view("pairs", torch.int32, 2 * total).view(total, 2).long()
+        # rows of the CSR list: slot i holds half_start[i + 1] - half_start[i] partners
+        ii = torch.repeat_interleave(torch.arange(n, device=self.device), hs[1:] - hs[:-1])
+        pairs = torch.stack([ii, self.view("half_j", torch.int32, total).long()], 1)
         ids = self._order()
         oi, oj = ids[pairs[:, 0]], ids[pairs[:, 1]]
         a, b = torch.minimum(oi, oj), torch.maximum(oi, oj)
@@ -405,6 +407,15 @@ class BatchSimulation:
 
     def replica_status(self, r):
         return B.md_read_status(self.params[r], self._ws(r), self.stream)
+
+    def replica_trace(self, r):
+        """Replica r's energy trace: (step, K, U, W) rows, as md_step_verlet's trace of a single system."""
+        L = self.layouts[r]
+        cap = self.params[r].trace_capacity
+        off = self.ws_offsets[r] + L.trace
+        t = self.ws[off:off + 32 * cap].view(torch.float64).view(-1, 4)
+        torch.cuda.synchronize(self.device)
+        return t.cpu().numpy()
 
     def replica_energies(self, r):
         L = self.layouts[r]

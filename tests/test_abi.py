@@ -29,7 +29,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_abi_version(lib):
-    assert B.md_abi_version() == 4
+    assert B.md_abi_version() == 5
 
 
 def _lj_params(n=4000, precision=B.MD_MIXED):
@@ -94,7 +94,7 @@ def test_workspace_layout(lib, precision, kind):
     L = B.md_workspace_layout(p)
     assert L.total == B.md_workspace_bytes(p) > 0
     offs = [getattr(L, f) for f in ("status", "energy", "cell_start", "fxp", "fxp_build", "patch_lab", "nbr",
-                                    "nbr_count", "half_start", "pairs", "force", "virial", "torque",
+                                    "nbr_count", "half_start", "half_j", "force", "virial", "torque",
                                     "acc", "copies", "estore", "jstart", "jedge", "local_tab", "trace", "pos_alt",
                                     "fxp_alt", "nbr_in", "nbr_in_count", "fxp_prune", "scratch")]
     assert all(o % 256 == 0 for o in offs)

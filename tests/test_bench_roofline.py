@@ -27,8 +27,8 @@ def test_force_algorithmic_bytes():
     # vertex: 4 B per entry + count 4 + own coordinates (16 mixed, 32 FP64) + force and virial 40
     assert bench.algorithmic_bytes_force(B.MD_VERTEX, B.MD_MIXED, 10, 300, 150) == 4 * 300 + 10 * 60
     assert bench.algorithmic_bytes_force(B.MD_VERTEX, B.MD_FP64, 10, 300, 150) == 4 * 300 + 10 * 76
-    # edge: (i, j) 8 B per pair, row offsets, coordinates, outputs zeroed and accumulated once
-    assert bench.algorithmic_bytes_force(B.MD_EDGE, B.MD_MIXED, 10, 300, 150) == 8 * 150 + 8 * 11 + 10 * (16 + 64)
+    # edge: partner j 4 B per pair, row offsets, coordinates, outputs zeroed and accumulated once
+    assert bench.algorithmic_bytes_force(B.MD_EDGE, B.MD_MIXED, 10, 300, 150) == 4 * 150 + 8 * 11 + 10 * (16 + 64)
 
 
 def test_traffic_is_the_capture_at_its_own_size(monkeypatch):
@@ -55,3 +55,9 @@ def test_traffic_is_withheld_for_other_sources(monkeypatch):
 def test_digest_covers_the_step_kernel_sources():
     d = bench.kernel_source_digest()
     assert len(d) == 64 and int(d, 16) >= 0
+
+
+def test_fp64_peak_from_unit_counts():
+    # 2 FP64 operations per clock per SM on 152 SMs: 629.28 G op/s at 2070 MHz
+    assert bench.fp64_peak_gops(2070.0) == pytest.approx(2.0 * 152 * 2.070, rel=1e-12)
+    assert bench.FP64_OPS_PER_PAIR_EVAL_LJ == 32

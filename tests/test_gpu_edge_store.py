@@ -36,13 +36,13 @@ def test_partner_index_lists_each_pair_once_in_order(name):
     n = s.n
     hs = sim.view("half_start", torch.int64, n + 1).cpu().numpy()
     E = int(hs[-1])
-    pairs = sim.view("pairs", torch.int32, 2 * E).view(E, 2).cpu().numpy()
+    half_j = sim.view("half_j", torch.int32, E).cpu().numpy()
     js = sim.view("jstart", torch.int64, n + 1).cpu().numpy()
     je = sim.view("jedge", torch.int32, E).cpu().numpy()
     assert js[-1] == E
     assert np.array_equal(np.sort(je), np.arange(E))            # every pair exactly once
     owner = np.repeat(np.arange(n), np.diff(js))
-    assert np.array_equal(pairs[je, 1], owner)                  # in its partner's row
+    assert np.array_equal(half_j[je], owner)                    # in its partner's row
     rows_sorted = np.all((np.diff(je) > 0) | (np.diff(owner) != 0))
     assert rows_sorted                                          # increasing within a row
 

@@ -404,3 +404,73 @@ def test_cutoff_band_fixup_with_threads_per_particle(tpp):
     assert outer - inner >= 5  # the configuration does exercise the band
     _, (F, _, _, _) = run_forces(s, B.MD_MIXED, B.MD_VERTEX, tpp=tpp)
     check_mixed(F, Fr, f"force tpp={tpp}")
+
+
+_liquid = {}
+
+
+def _bonded_patchy_liquid():
+    """patchy6000 after 1000 steps at kT = 0.15 (mixed edge path): patches have bonded and pressed cores
+    together, so the largest forces are many times the rms force, the hardest state for the mixed gate."""
+    if "patchy" not in _liquid:
+        import dataclasses
+        s = get_sys("patchy6000")
+        sim = Sim(s, B.MD_MIXED, fuse_step=0)
+        sim.prepare(B.MD_EDGE)
+        sim.step(1000, B.MD_EDGE, True)
+        assert sim.status()[B.MD_STATUS_CODE] == 0
+        x, v = sim.positions()
+        q, l = sim.orientations()
+        liq = dataclasses.replace(s, pos=np.mod(x, s.box), vel=v, quat=q, angmom=l, name="patchy6000_liquid")
+        _liquid["patchy"] = (liq, oracle.forces(liq.pos, model_of(liq), quat=liq.quat, use_cells=True))
+    return _liquid["patchy"]
+
+
+@pytest.mark.parametrize("path", [B.MD_VERTEX, B.MD_EDGE])
+def test_patchy_bonded_liquid_mixed_matches_oracle(path):
+    s, (Fr, Tr, Er, (Ur, Wr, _)) = _bonded_patchy_liquid()
+    fr2 = (Fr ** 2).sum(1)
+    assert np.sqrt(fr2.max() / fr2.mean()) > 5  # the heavy tail this test is about
+    _, (F, E, T, W) = run_forces(s, B.MD_MIXED, path)
+    check_mixed(F, Fr, "force (bonded liquid)")
+    check_mixed(T, Tr, "torque (bonded liquid)")
+    assert E.sum() == pytest.approx(Ur, rel=1e-5, abs=1e-5 * s.n)
+
+
+def _wca_gas_after_collisions():
+    """wca20000 after 1000 steps (fused mixed vertex path): collisions at r ~ 0.85-0.9 sigma give forces
+    many times the rms force, which is what the accurate repulsive core is for."""
+    if "wca" not in _liquid:
+        import dataclasses
+        s = get_sys("wca20000")
+        sim = Sim(s, B.MD_MIXED, fuse_step=1)
+        sim.prepare(B.MD_VERTEX)
+        sim.step(1000, B.MD_VERTEX, True)
+        assert sim.status()[B.MD_STATUS_CODE] == 0
+        x, v = sim.positions()
+        liq = dataclasses.replace(s, pos=np.mod(x, s.box), vel=v, name="wca20000_liquid")
+        _liquid["wca"] = (liq, oracle.forces(liq.pos, model_of(liq), use_cells=True))
+    return _liquid["wca"]
+
+
+@pytest.mark.parametrize("path", [B.MD_VERTEX, B.MD_EDGE, B.MD_VERTEX_NEWTON, B.MD_EDGE_STORE])
+def test_wca_gas_mixed_matches_oracle(path):
+    s, (Fr, _, Er, (Ur, Wr, _)) = _wca_gas_after_collisions()
+    fr2 = (Fr ** 2).sum(1)
+    assert np.sqrt(fr2.max() / fr2.mean()) > 5  # the heavy tail this test is about
+    _, (F, E, _, W) = run_forces(s, B.MD_MIXED, path)
+    check_mixed(F, Fr, "force (WCA gas)")
+    assert E.sum() == pytest.approx(Ur, rel=1e-5, abs=1e-5 * s.n)
+    assert W.sum() == pytest.approx(Wr, rel=1e-5, abs=1e-5 * s.n)
+
+
+def test_wca_gas_fused_step_forces_match_oracle():
+    """The fused step kernel's own forces (the last launch of a call) on the WCA gas."""
+    s, _ = _wca_gas_after_collisions()
+    sim = Sim(s, B.MD_MIXED, fuse_step=1)
+    sim.prepare(B.MD_VERTEX)
+    sim.step(20, B.MD_VERTEX, True)
+    x, _ = sim.positions()
+    F, _, _, _ = sim.forces()
+    Fr, _, _, _ = oracle.forces(np.mod(x, s.box), model_of(s), use_cells=True)
+    check_mixed(F, Fr, "force (WCA gas, fused step)")
