@@ -142,9 +142,16 @@ FP64_PER_CLK_SM = 2.0
 N_SM = 152
 
 
-def algorithmic_bytes_force(path: int, precision: int, n: int, full_entries: int, pairs: int) -> float:
+def algorithmic_bytes_force(path: int, precision: int, n: int, full_entries: int, pairs: int,
+                            patchy: bool = False) -> float:
     """Compulsory DRAM bytes of one force launch (lists, per-particle arrays once, outputs once)."""
     from paper_1401_4350_gb300 import binding as B
+    if patchy and precision == B.MD_MIXED:
+        # + the three fixed-point patch sites (48 B) and the torque output (vertex: 32 B written; edge: the
+        # FP32 torque sum and its compensation, zeroed once and accumulated once)
+        if path == B.MD_VERTEX:
+            return 4.0 * full_entries + n * (4 + 16 + 48 + 40 + 32)
+        return 4.0 * pairs + 8.0 * (n + 1) + n * (16 + 48 + 2 * 32 + 2 * 32)
     if path == B.MD_VERTEX:
         # count 4 + own coordinates (fixed point 16, FP64 32) + force double4 32 + virial 8
         return 4.0 * full_entries + n * (4 + (16 if precision == B.MD_MIXED else 32) + 40)
@@ -487,10 +494,13 @@ def run_variants(ctx, system1m, liquid1m, headline, headline_roofline, sm_mhz, a
                                                 f"SMs x {sm_mhz:.0f} MHz (median SM clock of the headline run)"}
             else:
                 alg = algorithmic_bytes_force(path if path in (B.MD_VERTEX, B.MD_EDGE) else B.MD_EDGE, precision,
-                                              n, entries, pairs)
+                                              n, entries, pairs, patchy=patchy)
                 r["roofline"] = {"bound": "hbm", "kernel": kname, "kernel_ms": fms,
                                  "algorithmic_bytes_per_launch": alg, "achieved": alg / (fms * 1e-3) / 1e9,
                                  "peak": hbm, "unit": "GB/s", "frac": alg / (fms * 1e-3) / 1e9 / hbm}
+                if patchy and precision == B.MD_MIXED:
+                    r["roofline"]["note"] = ("latency-bound, not bandwidth-bound: ncu shows 19-28 % occupancy, issue "
+                                             "29-33 % and no pipe above 32 % (profiles/k_patchy_mixed_262k.md)")
         del sim
         torch.cuda.empty_cache()
         out[key] = r

@@ -170,9 +170,13 @@ __device__ __forceinline__ FF ff_mul(FF a, FF b) {
 // scalar (2 t^7 - t^4) K, rounded once to FP32, and t^3, t^6 for the energy and virial sums.
 __device__ __forceinline__ float core_ff(const KArgs& a, unsigned long long s, float khi, float klo, float& t3f,
                                          float& t6f) {
-  // s = h + l exactly up to the rounding of l (h is integer-valued, so s - h is an exact integer)
-  const float h = __ull2float_rn(s);
-  const float l = __ll2float_rn((long long)(s - __float2ull_rn(h)));
+  // s = h + l up to the rounding of l, from 32-bit conversions only (64-bit integer conversions run on the
+  // FP64 pipe): s = sh 2^32 + sl, sh's FP32 value rounded (when sh >= 2^24) with its exact remainder r
+  const unsigned sh = (unsigned)(s >> 32), sl = (unsigned)s;
+  const float hh = __uint2float_rn(sh);
+  const int r = (int)(sh - __float2uint_rn(hh));
+  const float h = __fmul_rn(hh, 4294967296.0f);
+  const float l = __fmaf_rn(__int2float_rn(r), 4294967296.0f, __uint2float_rn(sl));
   // t = C / (h + l): a refined quotient t0 and its correction from the remainder C - t0 (h + l)
   const float y = frcp_refined(h);
   const float t0 = __fmul_rn(a.core_c_hi, y);
@@ -321,6 +325,41 @@ __device__ __forceinline__ PairOut<double> patchy_pair(const KArgs& a, const Vec
 // core (about 1e-6 relative) would put them near 1e-5 of the rms force off: the WCA core goes through the
 // accurate core (cubic box) or FP64 (other boxes), the (sigma/r)^200 core through FP64.  A pair's FP64
 // terms are rounded to FP32 once.
+// The FP64 terms of one mixed patchy pair: force on i, torques on i and j, energy, and the FP64 separation dd.
+struct PairFP64 {
+  Vec3<double> F, ti, tj, dd;
+  double e;
+};
+
+// The patch pairs of (i, j) flagged in `mask` (bit NP pa + b) in FP64 from the FP64 lab-frame sites; P.dd
+// must hold the FP64 separation.  Out of line: it runs for the few bonds only, and nine inlined copies of it
+// in the unrolled screening made instruction fetch the patchy kernels' main stall.
+template <int NP>
+__device__ __noinline__ void patch_bonds_fp64(const KArgs& a, int i, int j, unsigned mask, PairFP64& P) {
+  const double4_32a* li = a.patch_lab_d + (size_t)i * MD_MAX_PATCH;
+  const double4_32a* lj = a.patch_lab_d + (size_t)j * MD_MAX_PATCH;
+  while (mask) {
+    const int k = __ffs(mask) - 1;
+    mask &= mask - 1u;
+    const double4_32a A = li[k / NP], Bs = lj[k % NP];
+    const Vec3<double> s = {P.dd.x + Bs.x - A.x, P.dd.y + Bs.y - A.y, P.dd.z + Bs.z - A.z};
+    const double qd = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_d;
+    if (!(qd < a.patch_qcut_d)) continue;  // truncated patch pair (MD_PATCHY_POW), decided in FP64
+    const double q2 = qd * qd, q4 = q2 * q2, q5 = q4 * qd;
+    const double ex = exp(-0.5 * q5);
+    P.e -= a.eps_p_d * ex;
+    const double g = a.pgain_d * q4 * ex;  // force on site a: g * s
+    const Vec3<double> f = {g * s.x, g * s.y, g * s.z};
+    P.F.x += f.x; P.F.y += f.y; P.F.z += f.z;
+    P.ti.x += A.y * f.z - A.z * f.y;
+    P.ti.y += A.z * f.x - A.x * f.z;
+    P.ti.z += A.x * f.y - A.y * f.x;
+    P.tj.x -= Bs.y * f.z - Bs.z * f.y;
+    P.tj.y -= Bs.z * f.x - Bs.x * f.z;
+    P.tj.z -= Bs.x * f.y - Bs.y * f.x;
+  }
+}
+
 template <int NP, bool WANT_TJ>
 __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, const int3& ds, const Vec3<float>& d,
                                                             float r2, const IPatches<NP>& Pi, int i, int j) {
@@ -328,29 +367,30 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
   o.F = o.ti = o.tj = {0.f, 0.f, 0.f};
   o.e = o.w = 0.f;
   if (!(r2 < a.rc2_f)) return o;
-  Vec3<double> F = {0.0, 0.0, 0.0}, ti = {0.0, 0.0, 0.0}, tj = {0.0, 0.0, 0.0}, dd = {0.0, 0.0, 0.0};
-  double e = 0.0;
-  bool any = false;  // dd holds the FP64 separation and F, e the pair's FP64 terms
+  PairFP64 P;
+  P.F = P.ti = P.tj = P.dd = {0.0, 0.0, 0.0};
+  P.e = 0.0;
+  bool any = false;                  // P holds the FP64 separation and the pair's FP64 terms
   Vec3<float> Fc = {0.f, 0.f, 0.f};  // the core force and energy when they come from the accurate core
   float ec = 0.f;
   if (a.pow_core || (!a.cubic && r2 < a.rwca2_hi_f)) {
     // FP64 core: the FP32 r^2 screens out the pairs clearly beyond its range, FP64 decides the rest
-    dd = sep_fp64(a.pos[i], a.pos[j], a);
+    P.dd = sep_fp64(a.pos[i], a.pos[j], a);
     any = true;
-    const double r2d = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
+    const double r2d = P.dd.x * P.dd.x + P.dd.y * P.dd.y + P.dd.z * P.dd.z;
     double fs = 0.0, pe = 0.0;
     if (a.pow_core) pow_core_terms(a, r2d, fs, pe);
     else if (r2d < a.rwca2_d) lj_terms(a, r2d, fs, pe);
-    F = {fs * dd.x, fs * dd.y, fs * dd.z};
-    e = pe;
+    P.F = {fs * P.dd.x, fs * P.dd.y, fs * P.dd.z};
+    P.e = pe;
   } else if (a.cubic && iso_inside_u(a, exact_r2u(ds.x, ds.y, ds.z), i, j)) {
     float wc;
     iso_core_ff(a, ds, Fc, ec, wc);
   }
   if (r2 < a.patch_reach2_f) {
+    // screening: which patch pairs can be non-zero in FP32 (or are not truncated)
     const IPatches<NP> Pj = load_ipatches<NP>(a, j);
-    const double4_32a* li = a.patch_lab_d + (size_t)i * MD_MAX_PATCH;
-    const double4_32a* lj = a.patch_lab_d + (size_t)j * MD_MAX_PATCH;
+    unsigned mask = 0u;
 #pragma unroll
     for (int pa = 0; pa < NP; pa++) {
       const int bx = ds.x - Pi.p[pa].x, by = ds.y - Pi.p[pa].y, bz = ds.z - Pi.p[pa].z;
@@ -359,45 +399,27 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
         const int sx = bx + Pj.p[b].x, sy = by + Pj.p[b].y, sz = bz + Pj.p[b].z;
         float q;
         if (a.cubic) {
-          const unsigned long long r2i = (unsigned long long)((long long)sx * sx) +
-                                         (unsigned long long)((long long)sy * sy) +
-                                         (unsigned long long)((long long)sz * sz);
-          q = __ull2float_rn(r2i) * a.u2_over_delta2;
+          q = exact_r2u(sx, sy, sz) * a.u2_over_delta2;  // 32-bit conversions (screening only)
         } else {
           const float x = (float)sx * a.fxp_unit[0], y = (float)sy * a.fxp_unit[1], z = (float)sz * a.fxp_unit[2];
           q = (x * x + y * y + z * z) * a.inv_delta2_f;
         }
-        if (!(q < a.patch_q32_f)) continue;  // zero in FP32, or truncated (MD_PATCHY_POW)
-        if (!any) {
-          dd = sep_fp64(a.pos[i], a.pos[j], a);
-          any = true;
-        }
-        const double4_32a A = li[pa], Bs = lj[b];
-        const Vec3<double> s = {dd.x + Bs.x - A.x, dd.y + Bs.y - A.y, dd.z + Bs.z - A.z};
-        const double qd = (s.x * s.x + s.y * s.y + s.z * s.z) * a.inv_delta2_d;
-        if (!(qd < a.patch_qcut_d)) continue;  // truncated patch pair (MD_PATCHY_POW), decided in FP64
-        const double q2 = qd * qd, q4 = q2 * q2, q5 = q4 * qd;
-        const double ex = exp(-0.5 * q5);
-        e -= a.eps_p_d * ex;
-        const double g = a.pgain_d * q4 * ex;  // force on site a: g * s
-        const Vec3<double> f = {g * s.x, g * s.y, g * s.z};
-        F.x += f.x; F.y += f.y; F.z += f.z;
-        ti.x += A.y * f.z - A.z * f.y;
-        ti.y += A.z * f.x - A.x * f.z;
-        ti.z += A.x * f.y - A.y * f.x;
-        if (WANT_TJ) {
-          tj.x -= Bs.y * f.z - Bs.z * f.y;
-          tj.y -= Bs.z * f.x - Bs.x * f.z;
-          tj.z -= Bs.x * f.y - Bs.y * f.x;
-        }
+        if (q < a.patch_q32_f) mask |= 1u << (NP * pa + b);
       }
+    }
+    if (mask) {
+      if (!any) {
+        P.dd = sep_fp64(a.pos[i], a.pos[j], a);
+        any = true;
+      }
+      patch_bonds_fp64<NP>(a, i, j, mask, P);
     }
   }
   if (any) {
-    o.F = {(float)((double)Fc.x + F.x), (float)((double)Fc.y + F.y), (float)((double)Fc.z + F.z)};
-    o.e = (float)((double)ec + e);
-    o.ti = {(float)ti.x, (float)ti.y, (float)ti.z};
-    if (WANT_TJ) o.tj = {(float)tj.x, (float)tj.y, (float)tj.z};
+    o.F = {(float)((double)Fc.x + P.F.x), (float)((double)Fc.y + P.F.y), (float)((double)Fc.z + P.F.z)};
+    o.e = (float)((double)ec + P.e);
+    o.ti = {(float)P.ti.x, (float)P.ti.y, (float)P.ti.z};
+    if (WANT_TJ) o.tj = {(float)P.tj.x, (float)P.tj.y, (float)P.tj.z};
   } else {
     o.F = Fc;
     o.e = ec;
@@ -497,20 +519,25 @@ __device__ __forceinline__ void vertex_mixed_body(const KArgs& a, int gt) {
       uint4 sj[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) sj[u] = __ldg(a.fxp + (jj[u] >= 0 ? jj[u] : i));
-#pragma unroll
+      // the four gathers are issued together; the patchy pair (long: nine patch-pair screenings) is then
+      // evaluated in a rolled loop, one copy of its code instead of four, which keeps instruction fetch off
+      // the patchy kernel's stall list; the entry's values are picked by selects, not by local memory
+#pragma unroll 1
       for (int u = 0; u < 4; u++) {
-        if (jj[u] < 0) continue;
-        const Vec3<float> d = sep_mixed(si, sj[u], a);
+        const int j = u == 0 ? jj[0] : u == 1 ? jj[1] : u == 2 ? jj[2] : jj[3];
+        if (j < 0) continue;
+        const uint4 sju = u == 0 ? sj[0] : u == 1 ? sj[1] : u == 2 ? sj[2] : sj[3];
+        const Vec3<float> d = sep_mixed(si, sju, a);
         const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
         if (PATCHY) {
-          const int3 ds = make_int3((int)(sj[u].x - si.x), (int)(sj[u].y - si.y), (int)(sj[u].z - si.z));
-          const PairOut<float> o = patchy_pair_mixed<(PATCHY ? NP : 1), false>(a, ds, d, r2, Pi, i, jj[u]);
+          const int3 ds = make_int3((int)(sju.x - si.x), (int)(sju.y - si.y), (int)(sju.z - si.z));
+          const PairOut<float> o = patchy_pair_mixed<(PATCHY ? NP : 1), false>(a, ds, d, r2, Pi, i, j);
           comp_add(F, o.F);
           comp_add(T, o.ti);
           e += o.e;
           w += o.w;
         } else {
-          const PairOut<float> o = iso_pair<float>(a, d, r2, i, jj[u]);
+          const PairOut<float> o = iso_pair<float>(a, d, r2, i, j);
           comp_add(F, o.F);
           e += o.e;
           w += o.w;
@@ -532,7 +559,7 @@ __device__ __forceinline__ void vertex_mixed_body(const KArgs& a, int gt) {
 }
 
 template <int TPP, bool PATCHY, int NP>
-__global__ void __launch_bounds__(256) k_vertex_mixed(KArgs a) {
+__global__ void __launch_bounds__(256, 3) k_vertex_mixed(KArgs a) {
   vertex_mixed_body<TPP, PATCHY, NP>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -1188,16 +1215,21 @@ __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
                : "memory");
 }
 
-// hi += (v.xyz, v.w); the rounding errors of the three force components go to lo.xyz, and `extra`
-// is added to lo.w (the per-particle virial).
-__device__ __forceinline__ void comp_atomic(float4* hi, float4* lo, float4 v, float extra) {
-  const float4 old = atom_add_v4(hi, v);
+// The second half of comp_atomic: from the value `old` an atomic hi += v returned, the rounding errors of
+// the three force components go to lo.xyz, and `extra` to lo.w (the per-particle virial).
+__device__ __forceinline__ void comp_finish(float4* lo, float4 old, float4 v, float extra) {
   float4 err;
   err.x = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
   err.y = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
   err.z = two_sum_err(old.z, v.z, __fadd_rn(old.z, v.z));
   err.w = extra;
   if (err.x != 0.f || err.y != 0.f || err.z != 0.f || err.w != 0.f) red_add_v4(lo, err);
+}
+
+// hi += (v.xyz, v.w); the rounding errors of the three force components go to lo.xyz, and `extra`
+// is added to lo.w (the per-particle virial).
+__device__ __forceinline__ void comp_atomic(float4* hi, float4* lo, float4 v, float extra) {
+  comp_finish(lo, atom_add_v4(hi, v), v, extra);
 }
 
 // Segmented suffix sum over lanes with equal key: after the call the first lane of each run holds
@@ -1315,10 +1347,13 @@ __device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t 
     const bool nz = o.F.x != 0.f || o.F.y != 0.f || o.F.z != 0.f || eh != 0.f || wh != 0.f ||
                     (PATCHY && (o.ti.x != 0.f || o.ti.y != 0.f || o.ti.z != 0.f || o.tj.x != 0.f ||
                                 o.tj.y != 0.f || o.tj.z != 0.f));
-    // j side: one atomic per contributing pair
+    // j side: one atomic per contributing pair.  Its returned old value (for the compensation) is used only
+    // after the i side's warp sums, so that their shuffles overlap the atomic's round trip to L2.
+    const float4 vj = make_float4(-o.F.x, -o.F.y, -o.F.z, eh), tvj = make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f);
+    float4 oldj = make_float4(0.f, 0.f, 0.f, 0.f), toldj = oldj;
     if (nz) {
-      comp_atomic(fhi + p.y, flo + p.y, make_float4(-o.F.x, -o.F.y, -o.F.z, eh), wh);
-      if (PATCHY) comp_atomic(thi + p.y, tlo + p.y, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f), 0.f);
+      oldj = atom_add_v4(fhi + p.y, vj);
+      if (PATCHY) toldj = atom_add_v4(thi + p.y, tvj);
     }
     // i side: one atomic per run of equal i within the warp
     bool head;
@@ -1336,6 +1371,10 @@ __device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t 
         comp_atomic(fhi + p.x, flo + p.x, make_float4(fx, fy, fz, es), ws);
         if (PATCHY) comp_atomic(thi + p.x, tlo + p.x, make_float4(tx, ty, tz, 0.f), 0.f);
       }
+    }
+    if (nz) {
+      comp_finish(flo + p.y, oldj, vj, wh);
+      if (PATCHY) comp_finish(tlo + p.y, toldj, tvj, 0.f);
     }
   }
 }
