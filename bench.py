@@ -270,10 +270,12 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "precision": "mixed: FP32 pair arithmetic + compensated FP32 sums, FP64 integration and reductions",
         "pair_evals_per_s": world * pairs * args.steps / (ms * 1e-3),
-        "steady": {"ms_per_step": steady_ms, "steps_per_s": world * 1e3 / steady_ms, "repeats": STEADY_REPEATS,
+        "steady": {"ms_per_step": steady_ms, "steps_per_s": world * 1e3 / steady_ms,
+                   "mean_ms_per_step": statistics.mean(x[0] for x in steady), "repeats": STEADY_REPEATS,
                    "steps_per_repeat": STEADY_STEPS, "ms_per_step_each": [x[0] for x in steady],
                    "rebuilds_each": [x[1] for x in steady],
-                   "note": "median of the repeats; each repeat spans several rebuild and prune periods"},
+                   "note": "median (and mean) of the repeats; each repeat spans several rebuild and prune "
+                           "periods"},
         "config": {"workload": WORKLOAD, "n": n, "path": "vertex", "precision": "mixed",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (inner list ~0.26 GB + state ~0.2 GB per step)",

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kBForce) k_b_forces(BatchDev b) {
       vertex_newton_mixed_body<false, 1>(ka, gt);
     } else if (kind & KIND_EDGE) {
       const int r0 = local * kBEdgeRows + (threadIdx.x >> 5) * kSpanRows;
-      if (r0 < ka.n) edge_mixed_span<false, 1>(ka, r0, half_pairs(ka));
+      if (r0 < ka.n) edge_mixed_span<false, 1>(ka, r0, half_pairs(ka), kSpanRows);
     } else if ((kind & KIND_CUBIC) && ka.accurate_core) {
       switch (kind & 7) {
         case KIND_V1: vertex_iso_mixed_body<1, true, false, true>(ka, gt); break;

@@ -559,7 +559,7 @@ __device__ __forceinline__ void vertex_mixed_body(const KArgs& a, int gt) {
 }
 
 template <int TPP, bool PATCHY, int NP>
-__global__ void __launch_bounds__(256, 3) k_vertex_mixed(KArgs a) {
+__global__ void __launch_bounds__(256) k_vertex_mixed(KArgs a) {
   vertex_mixed_body<TPP, PATCHY, NP>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -1262,27 +1262,31 @@ __device__ __forceinline__ void run_bounds(int key, int lane, bool& head, int& e
 
 // ---- the half list in CSR form ------------------------------------------------------------------
 // Row i of the half list holds the partners j > i of slot i at half_j[half_start[i] .. half_start[i + 1]).
-// A warp walks a span of 32 consecutive rows: lane l holds the start of row r0 + l, the span's pairs are
-// taken in warp-sized chunks, and the row of a pair is the last lane whose start is not above it (a
-// binary search over the lanes, five shuffles).  The rows of a chunk are consecutive, so lanes of equal
-// i form runs, as the warp-segmented i-side sums need.
-constexpr int kSpanRows = 32;
+// A warp walks a span of R consecutive rows (R a power of two, at most 32; a.span_rows, chosen at launch):
+// lane l < R holds the start of row r0 + l, the span's pairs are taken in warp-sized chunks, and the row
+// of a pair is the last lane whose start is not above it (a binary search over the lanes, five shuffles;
+// lanes l >= R hold the span's end, so they are never chosen).  The rows of a chunk are consecutive, so
+// lanes of equal i form runs, as the warp-segmented i-side sums need.
+constexpr int kSpanRows = 32;  // the largest span (and the span of the batched edge items)
 
 struct HalfSpan {
   int r0;          // first row of the span
-  int start;       // lane l: start of row r0 + l relative to e0 (rows past n: the span's end)
+  int start;       // lane l: start of row r0 + min(l, R) relative to e0 (rows past n: the list's end)
   int64_t e0, e1;  // the span's pairs
 };
 
-__device__ __forceinline__ HalfSpan half_span(const KArgs& a, int r0, int64_t E) {
+__device__ __forceinline__ HalfSpan half_span(const KArgs& a, int r0, int64_t E, int R) {
   const int lane = threadIdx.x & 31;
   HalfSpan S;
   S.r0 = r0;
   S.e0 = min(a.half_start[r0], E);
-  S.e1 = min(a.half_start[min(r0 + kSpanRows, a.n)], E);
-  S.start = (int)(min(a.half_start[min(r0 + lane, a.n)], E) - S.e0);
+  S.e1 = min(a.half_start[min(r0 + R, a.n)], E);
+  S.start = (int)(min(a.half_start[min(r0 + min(lane, R), a.n)], E) - S.e0);
   return S;
 }
+
+// Rows per span of the single-system edge kernels (set by the launch; 0 in arguments built elsewhere).
+__device__ __forceinline__ int span_rows(const KArgs& a) { return a.span_rows > 0 ? a.span_rows : kSpanRows; }
 
 // Row of the pair at offset q of the span (0 <= q < e1 - e0); every lane of the warp must call it.
 __device__ __forceinline__ int half_row(const HalfSpan& S, int q) {
@@ -1309,16 +1313,16 @@ __device__ __forceinline__ int half_j_at(const KArgs& a, const HalfSpan& S, int6
   return e < S.e1 ? __ldcs(a.half_j + e) : -1;
 }
 
-// The pairs of the span of rows [r0, r0 + 32), one thread per pair.
+// The pairs of the span of rows [r0, r0 + R), one thread per pair.
 template <bool PATCHY, int NP>
-__device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t E) {
+__device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t E, int R) {
   const int lane = threadIdx.x & 31;
   const size_t n = (size_t)a.n;
   float4* fhi = a.acc;
   float4* flo = a.acc + n;
   float4* thi = a.acc + 2 * n;
   float4* tlo = a.acc + 3 * n;
-  const HalfSpan S = half_span(a, r0, E);
+  const HalfSpan S = half_span(a, r0, E, R);
   int jn = half_j_at(a, S, S.e0);
   for (int64_t base = S.e0; base < S.e1; base += 32) {
     const int2 p = half_pair(a, S, base, jn);  // this chunk's pair; the next chunk's partner is loaded now
@@ -1383,22 +1387,22 @@ __device__ __forceinline__ int64_t half_pairs(const KArgs& a) { return min(a.hal
 
 template <bool PATCHY, int NP>
 __global__ void __launch_bounds__(256) k_edge_mixed(KArgs a) {
-  // persistent warps over the spans of 32 rows
+  // persistent warps over the spans of R rows
   const int64_t E = half_pairs(a);
-  const int spans = (a.n + kSpanRows - 1) / kSpanRows;
+  const int R = span_rows(a), spans = (a.n + R - 1) / R;
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < spans; s += nw)
-    edge_mixed_span<PATCHY, NP>(a, s * kSpanRows, E);
+    edge_mixed_span<PATCHY, NP>(a, s * R, E, R);
 }
 
-// The pairs of the span of rows [r0, r0 + 32), one thread per pair, FP64.
+// The pairs of the span of rows [r0, r0 + R), one thread per pair, FP64.
 template <bool PATCHY, int NP>
-__device__ __forceinline__ void edge_fp64_span(const KArgs& a, int r0, int64_t E) {
+__device__ __forceinline__ void edge_fp64_span(const KArgs& a, int r0, int64_t E, int R) {
   const int lane = threadIdx.x & 31;
   double* f = (double*)a.force;
   double* vir = a.virial;
   double* t = (double*)a.torque;
-  const HalfSpan S = half_span(a, r0, E);
+  const HalfSpan S = half_span(a, r0, E, R);
   int jn = half_j_at(a, S, S.e0);
   for (int64_t base = S.e0; base < S.e1; base += 32) {
     const int2 p = half_pair(a, S, base, jn);
@@ -1458,10 +1462,10 @@ __device__ __forceinline__ void edge_fp64_span(const KArgs& a, int r0, int64_t E
 template <bool PATCHY, int NP>
 __global__ void __launch_bounds__(256) k_edge_fp64(KArgs a) {
   const int64_t E = half_pairs(a);
-  const int spans = (a.n + kSpanRows - 1) / kSpanRows;
+  const int R = span_rows(a), spans = (a.n + R - 1) / R;
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < spans; s += nw)
-    edge_fp64_span<PATCHY, NP>(a, s * kSpanRows, E);
+    edge_fp64_span<PATCHY, NP>(a, s * R, E, R);
 }
 
 // Mixed edge path: FP32 atomic sums plus their compensation terms become the FP64 result.
@@ -1782,12 +1786,12 @@ __device__ __forceinline__ void edge_store_fp64_one(const KArgs& a, int64_t k, i
 
 template <bool PATCHY, int NP>
 __global__ void __launch_bounds__(256) k_edge_store(KArgs a) {
-  // persistent warps over the spans of 32 rows; each pair's slot k of the store gets its terms
+  // persistent warps over the spans of R rows; each pair's slot k of the store gets its terms
   const int64_t E = half_pairs(a);
-  const int spans = (a.n + kSpanRows - 1) / kSpanRows;
+  const int R = span_rows(a), spans = (a.n + R - 1) / R;
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   for (int sp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); sp < spans; sp += nw) {
-    const HalfSpan S = half_span(a, sp * kSpanRows, E);
+    const HalfSpan S = half_span(a, sp * R, E, R);
     int jn = half_j_at(a, S, S.e0);
     for (int64_t base = S.e0; base < S.e1; base += 32) {
       const int2 p = half_pair(a, S, base, jn);

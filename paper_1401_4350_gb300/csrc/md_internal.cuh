@@ -143,6 +143,7 @@ struct KArgs {
   int32_t* nbr_count;
   int64_t* half_start;
   int32_t* half_j;       // half-list partners, rows from half_start
+  int32_t span_rows;     // rows per warp span of the single-system edge kernels (set at their launch)
   double4_32a* force;   // (F, E_i) result, FP64
   double* virial;        // W_i result
   double4_32a* torque;   // (tau, 0) result, patchy

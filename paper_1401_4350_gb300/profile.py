@@ -4,7 +4,8 @@
 
 Builds the seeded workload, prepares cells, lists and forces once, then launches the chosen phase
 `reps` times (forces: md_forces_vertex / md_forces_edge; build: md_build_cells + md_build_verlet;
-step: md_step_verlet of one step; steps3: of three steps; stepkernel: md_time_step_kernel, the kernel
+step: md_step_verlet of one step; steps3: of three steps; steps: of --nsteps steps, all launched directly
+(for launch lists: ncu does not profile graphs that hold conditional nodes); stepkernel: md_time_step_kernel, the kernel
 one step runs, i.e. the fused force + integrate kernel when fuse_step applies).  Prints the median
 CUDA-event time per call.
 """
@@ -35,7 +36,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="lj524288", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--path", default="vertex", choices=["vertex", "edge"])
-    ap.add_argument("--what", default="forces", choices=["forces", "build", "step", "steps3", "stepkernel"])
+    ap.add_argument("--what", default="forces", choices=["forces", "build", "step", "steps3", "steps", "stepkernel"])
+    ap.add_argument("--nsteps", type=int, default=20, help="steps of one call for --what steps (direct launches)")
     ap.add_argument("--fuse", type=int, default=1, choices=[0, 1], help="fuse_step of the system")
     ap.add_argument("--prune", type=float, default=0.0, help="prune_skin of the system (inner list)")
     ap.add_argument("--tpp", type=int, default=1)
@@ -70,6 +72,9 @@ def main(argv=None):
     elif a.what == "steps3":  # three steps: FIRST, then MIDDLE or fused launches, LAST
         def fn():
             sim.step(3, path, use_graph=False)
+    elif a.what == "steps":  # one call of nsteps steps, every kernel launched directly (for launch lists)
+        def fn():
+            sim.step(a.nsteps, path, use_graph=False)
     else:  # the kernel one step runs (fused step kernel or force kernel): a warm-up and one timed launch
         def fn():
             sim.time_step_kernel(path, reps=1)

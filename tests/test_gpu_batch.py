@@ -89,7 +89,10 @@ def test_batch_steps_match_single_system(use_graph):
             assert np.array_equal(pos, pos_s) and np.array_equal(vel, vel_s), f"replica {r}"
             assert st[B.MD_STATUS_REBUILDS] == ss[B.MD_STATUS_REBUILDS]
         else:
-            assert np.abs(pos - pos_s).max() < 1e-9
+            # the edge path sums its pairs with atomics in no fixed order (and the single-system kernel
+            # groups the i-side warp sums by other spans than the batched items), so the trajectories
+            # differ at the rounding level: ~1e-7 of a pair force, a few 1e-9 in position after 60 steps
+            assert np.abs(pos - pos_s).max() < 1e-7
     bs.release()
 
 
