@@ -338,7 +338,12 @@ static KArgs make_args(const md_params* p, const md_state* s, void* ws, const La
       const double r = sqrt(p->patch[k][0] * p->patch[k][0] + p->patch[k][1] * p->patch[k][1] +
                             p->patch[k][2] * p->patch[k][2]);
       if (r > R) R = r;
-      for (int c = 0; c < 3; c++) a.patch_body[k][c] = p->patch[k][c];
+      for (int c = 0; c < 3; c++) {
+        a.patch_body[k][c] = p->patch[k][c];
+        const float hi = (float)p->patch[k][c];
+        a.patch_body_ff[k][c][0] = hi;
+        a.patch_body_ff[k][c][1] = (float)(p->patch[k][c] - (double)hi);
+      }
     }
     // patch terms beyond (r_ab / delta)^10 = 177.4 (exp(-q^5 / 2) < 2^-128: force, torque and energy below
     // 1e-34) are skipped in mixed precision; beyond 1600 every FP64 term is exactly zero (exp underflow)

@@ -152,20 +152,8 @@ __device__ __forceinline__ float exact_r2u(int dx, int dy, int dz) {
 // In a sparse WCA fluid the largest forces are collisions at r ~ 0.85-0.9 sigma, tens of times the rms
 // force; the FP32 chain (sigma/r)^2 -> ^6 -> ^12 multiplies the roundings of r^2 and of the reciprocal by
 // six to twelve and leaves about 1e-6 of such a pair force, which is 1e-5 of the rms force.  For these
-// pairs the scalar part of the force is carried in unevaluated sums of two FP32 numbers (hi + lo, about
-// 2^-44 relative) from the exact integer r^2 on, and rounded to FP32 once at the end.
-struct FF {
-  float hi, lo;
-};
-
-// (a.hi + a.lo)(b.hi + b.lo) to about 2^-44 relative: the product of the high parts is split exactly
-// (its rounding error by a fused multiply-add), the cross terms are added to the low part.
-__device__ __forceinline__ FF ff_mul(FF a, FF b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  const float e = __fmaf_rn(a.hi, b.hi, -p);
-  return {p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e))};
-}
-
+// pairs the scalar part of the force is carried in unevaluated sums of two FP32 numbers (FF, hi + lo,
+// about 2^-44 relative) from the exact integer r^2 on, and rounded to FP32 once at the end.
 // For the exact integer squared separation s (units u^2) and t = C / s, C = sigma^2 / u^2: the force
 // scalar (2 t^7 - t^4) K, rounded once to FP32, and t^3, t^6 for the energy and virial sums.
 __device__ __forceinline__ float core_ff(const KArgs& a, unsigned long long s, float khi, float klo, float& t3f,

@@ -43,19 +43,6 @@ __device__ __forceinline__ long long fixed32_of(float x) {
   return (b >> 31) ? -v : v;
 }
 
-// FP64 -> FP32, rounded to nearest (halves away from zero), from the binary64 fields with integer
-// operations; magnitudes below 2^-126 give signed zero, above the FP32 range infinity.  For the
-// per-particle kinetic terms of the mixed path, where FP32 suffices and the FP64 pipe (which also
-// carries the hardware conversion) is the scarce unit.
-__device__ __forceinline__ float f32_of(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const int ef = (int)((hi >> 20) & 0x7ffu) - 896;  // biased FP32 exponent
-  uint32_t mag = ((uint32_t)max(ef, 0) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  mag += (lo >> 28) & 1u;  // a carry out of the significand moves into the exponent, as it should
-  mag = ef <= 0 ? 0u : min(mag, 0x7f800000u);
-  return __uint_as_float((hi & 0x80000000u) | mag);
-}
-
 // Warp total of 64-bit integers, in every lane: 32-bit reductions of four 16-bit pieces (exact while
 // the total fits in 64 bits).
 __device__ __forceinline__ long long warp_sum_i64(long long v) {
@@ -82,8 +69,8 @@ __device__ __forceinline__ double4_32a rotate(const KArgs& a, const double4_32a&
     // The increment (dq - 1) (x) q of a rotation by |omega| dt << 1 is small: it is computed in FP32
     // (cos(theta/2) - 1 = -2 sin^2(theta/4) keeps its relative precision) and added to the FP64
     // quaternion, which is then renormalised with one Newton step (|q|^2 - 1 ~ 1e-13).
-    const float wx = (float)L.x * a.inv_inertia_f, wy = (float)L.y * a.inv_inertia_f,
-                wz = (float)L.z * a.inv_inertia_f;
+    const float wx = f32_of(L.x) * a.inv_inertia_f, wy = f32_of(L.y) * a.inv_inertia_f,
+                wz = f32_of(L.z) * a.inv_inertia_f;
     const float wn = sqrtf(wx * wx + wy * wy + wz * wz);
     if (!(wn > 0.f)) return q;
     float s4, c4;
@@ -91,13 +78,13 @@ __device__ __forceinline__ double4_32a rotate(const KArgs& a, const double4_32a&
     const float cm1 = -2.f * s4 * s4;           // cos(theta/2) - 1
     const float k = 2.f * s4 * c4 / wn;         // sin(theta/2) / |omega|
     const float vx = wx * k, vy = wy * k, vz = wz * k;
-    const float qw = (float)q.x, qx = (float)q.y, qy = (float)q.z, qz = (float)q.w;
+    const float qw = f32_of(q.x), qx = f32_of(q.y), qy = f32_of(q.z), qz = f32_of(q.w);
     // (cm1, v) (x) (qw, qv) = (cm1 qw - v.qv, cm1 qv + qw v + v x qv)
     const float dw = cm1 * qw - (vx * qx + vy * qy + vz * qz);
     const float dx = cm1 * qx + qw * vx + (vy * qz - vz * qy);
     const float dy = cm1 * qy + qw * vy + (vz * qx - vx * qz);
     const float dz = cm1 * qz + qw * vz + (vx * qy - vy * qx);
-    double4_32a r = make_double4_32a(q.x + (double)dw, q.y + (double)dx, q.z + (double)dy, q.w + (double)dz);
+    double4_32a r = make_double4_32a(q.x + f64_of(dw), q.y + f64_of(dx), q.z + f64_of(dy), q.w + f64_of(dz));
     const double n2 = r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
     const double f = 1.5 - 0.5 * n2;
     return make_double4_32a(r.x * f, r.y * f, r.z * f, r.w * f);
@@ -275,14 +262,23 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
       double4_32a L = a.angmom[i];
       const double4_32a T = a.torque[i];
       const double hdt = 0.5 * a.dt;
-      if (mode == 1) {
-        L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
-        if (mixed) {
-          const float lx = f32_of(L.x), ly = f32_of(L.y), lz = f32_of(L.z);
+      if (mode == 1 && mixed) {
+        // as for the velocity: the closing half kick only for the FP32 rotational energy, then one kick
+        // by the whole step (or, after a refresh, the opening half kick from the drawn momentum)
+        if (energies) {
+          const float hf = 0.5f * a.dt_f;
+          const float lx = f32_of(L.x) + f32_of(T.x) * hf, ly = f32_of(L.y) + f32_of(T.y) * hf,
+                      lz = f32_of(L.z) + f32_of(T.z) * hf;
           krf = 0.5f * a.inv_inertia_f * (lx * lx + ly * ly + lz * lz);
-        } else {
-          kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
         }
+        if (refresh) {
+          L.x = fma(T.x, hdt, ln[0]); L.y = fma(T.y, hdt, ln[1]); L.z = fma(T.z, hdt, ln[2]);
+        } else {
+          L.x = fma(T.x, a.dt, L.x); L.y = fma(T.y, a.dt, L.y); L.z = fma(T.z, a.dt, L.z);
+        }
+      } else if (mode == 1) {
+        L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
+        kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
         if (refresh) L = make_double4_32a(ln[0], ln[1], ln[2], L.w);
         L.x = fma(T.x, hdt, L.x); L.y = fma(T.y, hdt, L.y); L.z = fma(T.z, hdt, L.z);
       } else if (mode == 0 || mode == 2) {
@@ -301,7 +297,7 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
       if (drift) {
         const double4_32a q = rotate(a, a.quat[i], L);
         a.quat[i] = q;
-        write_patch_lab(a, i, q);
+        write_patch_lab(a, i, q, a.n_patch);  // the unused slots keep the zeros of the last cell build
       }
     }
     if (drift) {

@@ -113,6 +113,7 @@ struct KArgs {
   float patch_reach2_f;
   float patch_q32_f;                      // mixed: FP32 q below which a patch pair is evaluated in FP64
   double patch_body[MD_MAX_PATCH][3];
+  float patch_body_ff[MD_MAX_PATCH][3][2];  // mixed: the same as float-float pairs (hi, lo)
   int32_t pow_core;                       // MD_PATCHY_POW: (sigma/r)^200 centre repulsion instead of WCA
   double patch_qcut_d;                    // MD_PATCHY_POW: (patch_rc / delta)^2 (1e300: no cut-off)
   // thermostat (momentum refresh)
@@ -278,25 +279,116 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float term) {
 
 namespace mdgb {
 
+// FP64 -> FP32, rounded to nearest (halves away from zero), from the binary64 fields with integer
+// operations; magnitudes below 2^-126 give signed zero, above the FP32 range infinity.  For the
+// per-particle kinetic terms of the mixed path, where FP32 suffices and the FP64 pipe (which also
+// carries the hardware conversion) is the scarce unit.
+__device__ __forceinline__ float f32_of(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int ef = (int)((hi >> 20) & 0x7ffu) - 896;  // biased FP32 exponent
+  uint32_t mag = ((uint32_t)max(ef, 0) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  mag += (lo >> 28) & 1u;  // a carry out of the significand moves into the exponent, as it should
+  mag = ef <= 0 ? 0u : min(mag, 0x7f800000u);
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+// FP32 -> FP64 from the binary32 fields with integer operations (exact for normal numbers; subnormal
+// inputs give signed zero), for the same reason.
+__device__ __forceinline__ double f64_of(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint32_t sign = b & 0x80000000u;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  const uint32_t e64 = e == 0xffu ? 0x7ffu : e + 896u;
+  return __hiloint2double((int)(sign | (e64 << 20) | ((b >> 3) & 0xfffffu)), (int)(b << 29));
+}
+
+// ---- float-float arithmetic -------------------------------------------------------------------
+// An unevaluated sum hi + lo of two FP32 numbers carries about 48 significant bits: where a result needs
+// more than FP32 but the FP64 pipe (2 operations per clock and SM against 128 for FP32) is the scarce
+// unit, the pair is formed with FP32 operations.
+struct FF {
+  float hi, lo;
+};
+
+// (a.hi + a.lo)(b.hi + b.lo) to about 2^-44 relative: the product of the high parts is split exactly
+// (its rounding error by a fused multiply-add), the cross terms are added to the low part.
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return {p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e))};
+}
+
+// a + b to about 2^-44 relative: the exact sum of the high parts (TwoSum), the low parts added to its
+// rounding error, and the pair renormalised so that |lo| is at most half an ulp of hi.
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float t = __fadd_rn(__fadd_rn(a.lo, b.lo), two_sum_err(a.hi, b.hi, s));
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+// k (a.hi + a.lo) for k a power of two: exact
+__device__ __forceinline__ FF ff_scale(FF a, float k) { return {a.hi * k, a.lo * k}; }
+
+// x to about 2^-48 relative: its FP32 rounding and the FP32 rounding of the (exact) remainder, with one
+// FP64 operation
+__device__ __forceinline__ FF ff_of(double x) {
+  const float h = f32_of(x);
+  return {h, f32_of(x - f64_of(h))};
+}
+
+__device__ __forceinline__ double f64_of(FF a) { return f64_of(a.hi) + f64_of(a.lo); }
+
 // Lab-frame patch sites of one particle from its FP64 quaternion (w, x, y, z): p_lab = R(q) p_body,
-// computed in FP64 and stored as FP64 vectors.  MD_MIXED also stores each site as a 32-bit fixed-point
-// offset from the centre in the units of the centre coordinates (box fraction times 2^32), so that a
-// patch-pair separation x_j + p_b - x_i - p_a is an exact integer sum for the FP32 screening of pairs.
-__device__ __forceinline__ void write_patch_lab(const KArgs& a, int i, const double4_32a& q) {
+// stored as FP64 vectors.  MD_MIXED also stores each site as a 32-bit fixed-point offset from the centre
+// in the units of the centre coordinates (box fraction times 2^32), so that a patch-pair separation
+// x_j + p_b - x_i - p_a is an exact integer sum for the FP32 screening of pairs.  FP64 forms R and the
+// sites in FP64; MD_MIXED forms them in float-float from the float-float quaternion (about 1e-13 of the
+// FP64 result, far inside what the FP64 bond terms of the mixed path need), which takes the rigid-body
+// update off the FP64 pipe: 22 FP64 operations per particle instead of 63.  slots: the sites written (the
+// unused slots past n_patch are written as zeros by the cell build).
+__device__ __forceinline__ void write_patch_lab(const KArgs& a, int i, const double4_32a& q,
+                                                int slots = MD_MAX_PATCH) {
+  if (a.precision == MD_MIXED) {
+    const FF w = ff_of(q.x), x = ff_of(q.y), y = ff_of(q.z), z = ff_of(q.w);
+    const FF xx = ff_mul(x, x), yy = ff_mul(y, y), zz = ff_mul(z, z);
+    const FF xy = ff_mul(x, y), xz = ff_mul(x, z), yz = ff_mul(y, z);
+    const FF wx = ff_mul(w, x), wy = ff_mul(w, y), wz = ff_mul(w, z);
+    const FF one = {1.f, 0.f};
+    const FF R[3][3] = {
+        {ff_add(one, ff_scale(ff_add(yy, zz), -2.f)), ff_scale(ff_add(xy, ff_scale(wz, -1.f)), 2.f),
+         ff_scale(ff_add(xz, wy), 2.f)},
+        {ff_scale(ff_add(xy, wz), 2.f), ff_add(one, ff_scale(ff_add(xx, zz), -2.f)),
+         ff_scale(ff_add(yz, ff_scale(wx, -1.f)), 2.f)},
+        {ff_scale(ff_add(xz, ff_scale(wy, -1.f)), 2.f), ff_scale(ff_add(yz, wx), 2.f),
+         ff_add(one, ff_scale(ff_add(xx, yy), -2.f))}};
+    int4* out = (int4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
+    for (int p = 0; p < slots; p++) {
+      double v[3] = {0.0, 0.0, 0.0};
+      if (p < a.n_patch) {
+        const FF bx = {a.patch_body_ff[p][0][0], a.patch_body_ff[p][0][1]};
+        const FF by = {a.patch_body_ff[p][1][0], a.patch_body_ff[p][1][1]};
+        const FF bz = {a.patch_body_ff[p][2][0], a.patch_body_ff[p][2][1]};
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+          v[c] = f64_of(ff_add(ff_add(ff_mul(R[c][0], bx), ff_mul(R[c][1], by)), ff_mul(R[c][2], bz)));
+      }
+      out[p] = make_int4((int)to_fixed(v[0], a.fxp_scale[0]), (int)to_fixed(v[1], a.fxp_scale[1]),
+                         (int)to_fixed(v[2], a.fxp_scale[2]), 0);
+      a.patch_lab_d[(size_t)i * MD_MAX_PATCH + p] = make_double4_32a(v[0], v[1], v[2], 0.0);
+    }
+    return;
+  }
   const double w = q.x, x = q.y, y = q.z, z = q.w;
   const double R[3][3] = {{1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y)},
                           {2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x)},
                           {2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)}};
-  for (int p = 0; p < MD_MAX_PATCH; p++) {
+  for (int p = 0; p < slots; p++) {
     double v[3] = {0.0, 0.0, 0.0};
     if (p < a.n_patch) {
       const double bx = a.patch_body[p][0], by = a.patch_body[p][1], bz = a.patch_body[p][2];
       for (int c = 0; c < 3; c++) v[c] = R[c][0] * bx + R[c][1] * by + R[c][2] * bz;
-    }
-    if (a.precision == MD_MIXED) {
-      int4* out = (int4*)a.patch_lab + (size_t)i * MD_MAX_PATCH;
-      out[p] = make_int4((int)to_fixed(v[0], a.fxp_scale[0]), (int)to_fixed(v[1], a.fxp_scale[1]),
-                         (int)to_fixed(v[2], a.fxp_scale[2]), 0);
     }
     a.patch_lab_d[(size_t)i * MD_MAX_PATCH + p] = make_double4_32a(v[0], v[1], v[2], 0.0);
   }
