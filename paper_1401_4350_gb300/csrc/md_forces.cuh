@@ -404,8 +404,8 @@ __device__ __forceinline__ PairOut<float> patchy_pair_mixed(const KArgs& a, cons
     }
   }
   if (any) {
-    o.F = {(float)((double)Fc.x + P.F.x), (float)((double)Fc.y + P.F.y), (float)((double)Fc.z + P.F.z)};
-    o.e = (float)((double)ec + P.e);
+    o.F = {f32_of(f64_of(Fc.x) + P.F.x), f32_of(f64_of(Fc.y) + P.F.y), f32_of(f64_of(Fc.z) + P.F.z)};
+    o.e = f32_of(f64_of(ec) + P.e);
     o.ti = {(float)P.ti.x, (float)P.ti.y, (float)P.ti.z};
     if (WANT_TJ) o.tj = {(float)P.tj.x, (float)P.tj.y, (float)P.tj.z};
   } else {
@@ -537,12 +537,12 @@ __device__ __forceinline__ void vertex_mixed_body(const KArgs& a, int gt) {
   group_reduce<TPP>(F, T, e, w);
   if (valid && l == 0) {
     // the compensated FP32 sums end here: sum + compensation, once per particle, in FP64
-    a.force[i] = make_double4_32a((double)F.s[0] + (double)F.lo[0], (double)F.s[1] + (double)F.lo[1],
-                                  (double)F.s[2] + (double)F.lo[2], 0.5 * (double)e);
-    a.virial[i] = 0.5 * (double)w;
+    a.force[i] = make_double4_32a(f64_of(F.s[0]) + f64_of(F.lo[0]), f64_of(F.s[1]) + f64_of(F.lo[1]),
+                                  f64_of(F.s[2]) + f64_of(F.lo[2]), 0.5 * f64_of(e));
+    a.virial[i] = 0.5 * f64_of(w);
     if (PATCHY)
-      a.torque[i] = make_double4_32a((double)T.s[0] + (double)T.lo[0], (double)T.s[1] + (double)T.lo[1],
-                                     (double)T.s[2] + (double)T.lo[2], 0.0);
+      a.torque[i] = make_double4_32a(f64_of(T.s[0]) + f64_of(T.lo[0]), f64_of(T.s[1]) + f64_of(T.lo[1]),
+                                     f64_of(T.s[2]) + f64_of(T.lo[2]), 0.0);
   }
 }
 
@@ -1460,13 +1460,13 @@ __global__ void __launch_bounds__(256) k_edge_fp64(KArgs a) {
 __device__ __forceinline__ void edge_finalize_one(const KArgs& a, int i) {
   const size_t n = (size_t)a.n;
   const float4 hi = a.acc[i], lo = a.acc[n + i];
-  a.force[i] = make_double4_32a((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y,
-                                (double)hi.z + (double)lo.z, (double)hi.w);
-  a.virial[i] = (double)lo.w;
+  a.force[i] = make_double4_32a(f64_of(hi.x) + f64_of(lo.x), f64_of(hi.y) + f64_of(lo.y),
+                                f64_of(hi.z) + f64_of(lo.z), f64_of(hi.w));
+  a.virial[i] = f64_of(lo.w);
   if (is_patchy(a.model)) {
     const float4 th = a.acc[2 * n + i], tl = a.acc[3 * n + i];
-    a.torque[i] = make_double4_32a((double)th.x + (double)tl.x, (double)th.y + (double)tl.y,
-                                   (double)th.z + (double)tl.z, 0.0);
+    a.torque[i] = make_double4_32a(f64_of(th.x) + f64_of(tl.x), f64_of(th.y) + f64_of(tl.y),
+                                   f64_of(th.z) + f64_of(tl.z), 0.0);
   }
 }
 
@@ -1546,12 +1546,12 @@ __device__ __forceinline__ void vertex_newton_mixed_body(const KArgs& a, int i) 
     }
     cur = nxt;
   }
-  a.force[i] = make_double4_32a((double)F.s[0] + (double)F.lo[0], (double)F.s[1] + (double)F.lo[1],
-                                (double)F.s[2] + (double)F.lo[2], (double)e);
-  a.virial[i] = (double)w;
+  a.force[i] = make_double4_32a(f64_of(F.s[0]) + f64_of(F.lo[0]), f64_of(F.s[1]) + f64_of(F.lo[1]),
+                                f64_of(F.s[2]) + f64_of(F.lo[2]), f64_of(e));
+  a.virial[i] = f64_of(w);
   if (PATCHY)
-    a.torque[i] = make_double4_32a((double)T.s[0] + (double)T.lo[0], (double)T.s[1] + (double)T.lo[1],
-                                   (double)T.s[2] + (double)T.lo[2], 0.0);
+    a.torque[i] = make_double4_32a(f64_of(T.s[0]) + f64_of(T.lo[0]), f64_of(T.s[1]) + f64_of(T.lo[1]),
+                                   f64_of(T.s[2]) + f64_of(T.lo[2]), 0.0);
 }
 
 template <bool PATCHY, int NP>
@@ -1824,12 +1824,12 @@ __device__ __forceinline__ void edge_store_reduce_one(const KArgs& a, int i) {
       e += 0.5f * x.w;
       w += 0.5f * y.w;
     }
-    a.force[i] = make_double4_32a((double)F.s[0] + (double)F.lo[0], (double)F.s[1] + (double)F.lo[1],
-                                  (double)F.s[2] + (double)F.lo[2], (double)e);
-    a.virial[i] = (double)w;
+    a.force[i] = make_double4_32a(f64_of(F.s[0]) + f64_of(F.lo[0]), f64_of(F.s[1]) + f64_of(F.lo[1]),
+                                  f64_of(F.s[2]) + f64_of(F.lo[2]), f64_of(e));
+    a.virial[i] = f64_of(w);
     if (patchy)
-      a.torque[i] = make_double4_32a((double)T.s[0] + (double)T.lo[0], (double)T.s[1] + (double)T.lo[1],
-                                     (double)T.s[2] + (double)T.lo[2], 0.0);
+      a.torque[i] = make_double4_32a(f64_of(T.s[0]) + f64_of(T.lo[0]), f64_of(T.s[1]) + f64_of(T.lo[1]),
+                                     f64_of(T.s[2]) + f64_of(T.lo[2]), 0.0);
   } else {
     const double4_32a* A = (const double4_32a*)a.estore;
     const double4_32a* Bk = A + a.max_pairs;
