@@ -738,13 +738,15 @@ __device__ __forceinline__ void gather4(const KArgs& a, const Rows& R, const int
   sj[3] = R.coords(a, (unsigned)cur.w);
 }
 
-// One group of four list entries of particle si, from their gathered coordinates sj.  LIVE: some entries
-// may lie past the count.  keep (PRUNE): the entries closer than rc + prune_skin, as bits 0..3.  ACC: the
-// pairs inside the cut-off go through the accurate core instead of the packed FP32 arithmetic (WCA).
-template <bool LIVE, bool PRUNE = false, bool ACC = false>
-__device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, const uint4 sj[4], int lim,
-                                            IsoAcc& A, unsigned* keep = nullptr) {
-  float r2[4], dx[4], dy[4], dz[4];
+// One group of four list entries of particle si, in two stages.  prep turns the gathered coordinates sj into
+// the separations (the exact integer r^2 shifted into FP32, and the components as FP32 values of the integer
+// differences); after it the coordinate registers are free, and the walk gathers the next group into them.
+// LIVE: some entries may lie past the count (lim).  PRUNE: returns the entries closer than rc + prune_skin
+// as bits 0..3.
+template <bool LIVE, bool PRUNE>
+__device__ __forceinline__ unsigned iso_group_prep(const KArgs& a, const uint4& si, const uint4 sj[4], int lim,
+                                                   float r2[4], float dx[4], float dy[4], float dz[4]) {
+  unsigned keep = 0u;
 #pragma unroll
   for (int u = 0; u < 4; u++) {
     const int ix = (int)(sj[u].x - si.x), iy = (int)(sj[u].y - si.y), iz = (int)(sj[u].z - si.z);
@@ -752,13 +754,17 @@ __device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, con
     dx[u] = (float)ix;
     dy[u] = (float)iy;
     dz[u] = (float)iz;
+    if (PRUNE) keep |= ((!LIVE || u < lim) && r2[u] < a.rin2_s) ? (1u << u) : 0u;
   }
-  if (PRUNE) {
-    unsigned k = 0u;
-#pragma unroll
-    for (int u = 0; u < 4; u++) k |= ((!LIVE || u < lim) && r2[u] < a.rin2_s) ? (1u << u) : 0u;
-    *keep = k;
-  }
+  return keep;
+}
+
+// The packed FP32 arithmetic of a prepared group: pairs inside the cut-off add to the Kahan sums, the
+// (sigma/r)^12 and (sigma/r)^6 sums and the pair count.  ACC: the packed path takes no pair (the accurate
+// core adds them), but still tracks the band around rc^2.
+template <bool LIVE, bool ACC = false>
+__device__ __forceinline__ void iso_group_math(const KArgs& a, const float r2[4], const float dx[4], const float dy[4],
+                                               const float dz[4], int lim, IsoAcc& A) {
   const float2 thr2 = make_float2(-a.rwca2_s, -a.rwca2_s);
   float2 gx, gy, gz;
 #pragma unroll
@@ -794,6 +800,17 @@ __device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, con
   kahan_add2(A.fx, A.cx, gx);
   kahan_add2(A.fy, A.cy, gy);
   kahan_add2(A.fz, A.cz, gz);
+}
+
+// Both stages of a group whose coordinates stay in sj.  ACC: the pairs inside the cut-off go through the
+// accurate core instead of the packed FP32 arithmetic (WCA).
+template <bool LIVE, bool PRUNE = false, bool ACC = false>
+__device__ __forceinline__ void iso_group_c(const KArgs& a, const uint4& si, const uint4 sj[4], int lim,
+                                            IsoAcc& A, unsigned* keep = nullptr) {
+  float r2[4], dx[4], dy[4], dz[4];
+  const unsigned k = iso_group_prep<LIVE, PRUNE>(a, si, sj, lim, r2, dx, dy, dz);
+  if (PRUNE) *keep = k;
+  iso_group_math<LIVE, ACC>(a, r2, dx, dy, dz, lim, A);
   if (ACC) {
 #pragma unroll
     for (int u = 0; u < 4; u++) {
@@ -839,6 +856,7 @@ __device__ __forceinline__ void store_iso(const KArgs& a, int gt, int tpp, const
 template <int TPP, class Rows, class Sink = NoPrune, bool AHEAD = true, bool ACC = false>
 __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, const Rows& R, IsoResult& res,
                                                       Sink* sink = nullptr) {
+  static_assert(!(AHEAD && ACC), "the accurate core re-reads the coordinates of its group: no gathers ahead");
   const int i = gt / TPP, l = gt % TPP;
   const bool valid = i < a.n;
   const size_t n = (size_t)a.n;
@@ -858,27 +876,28 @@ __device__ __forceinline__ void vertex_iso_cubic_rows(const KArgs& a, int gt, co
 #pragma unroll
     for (int d = 2; d < kListPrefetch; d++)
       if (l + d * TPP < ng) R.prefetch(l + d * TPP, n);
-    // the gathers of each group are issued one group ahead, so that their latency overlaps the
-    // arithmetic of the group before
+    // AHEAD: the gathers of each group are issued one group ahead, so that their latency overlaps the
+    // arithmetic of the group before.  Each group is first reduced to its separations, which frees the
+    // coordinate registers; the next group's gathers then go into the same registers (no second buffer,
+    // no copies between them) and are in flight during the group's arithmetic.
     int g = l;
     uint4 sj[4];
     if (AHEAD) gather4(a, R, cur, sj);
     for (; g < nfull; g += TPP) {  // groups of four entries that are all in the list
       const int4 nxt = R.group(g + TPP, ng, n);
       if (g + kListPrefetch * TPP < ng) R.prefetch(g + kListPrefetch * TPP, n);
-      uint4 sn[4];
-      if (AHEAD)
-        gather4(a, R, nxt, sn);  // the next group's coordinates are in flight during this group's arithmetic
-      else
-        gather4(a, R, cur, sj);
       unsigned keep = 0u;
-      iso_group_c<false, Sink::kPrune, ACC>(a, si, sj, 4, A, &keep);
+      if (AHEAD) {
+        float r2[4], dx[4], dy[4], dz[4];
+        keep = iso_group_prep<false, Sink::kPrune>(a, si, sj, 4, r2, dx, dy, dz);
+        gather4(a, R, nxt, sj);
+        iso_group_math<false, ACC>(a, r2, dx, dy, dz, 4, A);
+      } else {
+        gather4(a, R, cur, sj);
+        iso_group_c<false, Sink::kPrune, ACC>(a, si, sj, 4, A, &keep);
+      }
       if (Sink::kPrune) sink->take(a, cur, keep);
       cur = nxt;
-      if (AHEAD) {
-#pragma unroll
-        for (int u = 0; u < 4; u++) sj[u] = sn[u];
-      }
     }
     if (g < ng) {  // the partial last group
       if (!AHEAD) gather4(a, R, cur, sj);
