@@ -21,9 +21,9 @@
 // positions as 32-bit fixed-point fractions of the box, so that the difference of two
 // coordinates taken in 32-bit integer arithmetic is the minimum image (wrap-around is the
 // periodic boundary) and converts to FP32 with a relative error of 2^-24 of the separation.
-// Per-particle sums are FP32 with a Kahan compensation term (vertex) or FP32 atomics whose
-// rounding error is recovered with TwoSum from the returned old value and accumulated in a
-// second array (edge).
+// Per-particle sums are FP32 with a Kahan compensation term (vertex) or, for atomics, two FP32
+// reductions per contribution: its part on a 2^-8 grid, which sums exactly, and the remainder, in a
+// second array (edge, and the reactions of the Newton vertex path).
 #include "md_forces.cuh"
 
 namespace mdgb {

@@ -1208,35 +1208,32 @@ __global__ void __launch_bounds__(256) k_vertex_fp64(KArgs a) {
 // Edge-based kernels
 // ------------------------------------------------------------------------------------------------
 
-__device__ __forceinline__ float4 atom_add_v4(float4* addr, float4 v) {
-  float4 old;
-  asm volatile("atom.global.add.v4.f32 {%0,%1,%2,%3}, [%4], {%5,%6,%7,%8};"
-               : "=f"(old.x), "=f"(old.y), "=f"(old.z), "=f"(old.w)
-               : "l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-               : "memory");
-  return old;
-}
-
 __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
   asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                : "memory");
 }
 
-// The second half of comp_atomic: from the value `old` an atomic hi += v returned, the rounding errors of
-// the three force components go to lo.xyz, and `extra` to lo.w (the per-particle virial).
-__device__ __forceinline__ void comp_finish(float4* lo, float4 old, float4 v, float extra) {
-  float4 err;
-  err.x = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
-  err.y = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
-  err.z = two_sum_err(old.z, v.z, __fadd_rn(old.z, v.z));
-  err.w = extra;
-  if (err.x != 0.f || err.y != 0.f || err.z != 0.f || err.w != 0.f) red_add_v4(lo, err);
+// Compensated FP32 accumulation with non-returning reductions.  Each force (or torque) component t is
+// split into q, t rounded to a multiple of 2^-8, and its exact remainder t - q (|t - q| <= 2^-9).  Sums of
+// multiples of 2^-8 are exact in FP32 while they stay below 2^16 in magnitude, so the hi accumulator holds
+// an exact partial sum whatever the order of the additions; lo sums the remainders, whose own rounding
+// is below 2^-28 per addition while that sum stays below 1 (about 2^-33 at the typical 0.05).  Rounding to
+// 2^-8 is t + 1.5 * 2^15 - 1.5 * 2^15 (two FP32 additions, exact for |t| < 2^14; larger components go to
+// hi whole, where they round at 2^-24 of the sum).  No old value is waited for, which the TwoSum
+// compensation of an atomic's returned value would need.
+constexpr float kSplitMagic = 49152.0f;  // 1.5 * 2^23 * 2^-8
+constexpr float kSplitMax = 16384.0f;    // 2^22 * 2^-8
+__device__ __forceinline__ float split_hi(float t) {
+  return fabsf(t) < kSplitMax ? __fsub_rn(__fadd_rn(t, kSplitMagic), kSplitMagic) : t;
 }
 
-// hi += (v.xyz, v.w); the rounding errors of the three force components go to lo.xyz, and `extra`
-// is added to lo.w (the per-particle virial).
-__device__ __forceinline__ void comp_atomic(float4* hi, float4* lo, float4 v, float extra) {
-  comp_finish(lo, atom_add_v4(hi, v), v, extra);
+// hi += (q(v.xyz), v.w), lo += (v.xyz - q(v.xyz), extra); the .w words (half pair energies in hi, half
+// pair virials in lo) are plain FP32 sums.  A reduction whose four words are zero is not issued.
+__device__ __forceinline__ void split_red(float4* hi, float4* lo, float4 v, float extra) {
+  const float qx = split_hi(v.x), qy = split_hi(v.y), qz = split_hi(v.z);
+  const float rx = __fsub_rn(v.x, qx), ry = __fsub_rn(v.y, qy), rz = __fsub_rn(v.z, qz);
+  if (qx != 0.f || qy != 0.f || qz != 0.f || v.w != 0.f) red_add_v4(hi, make_float4(qx, qy, qz, v.w));
+  if (rx != 0.f || ry != 0.f || rz != 0.f || extra != 0.f) red_add_v4(lo, make_float4(rx, ry, rz, extra));
 }
 
 // Segmented suffix sum over lanes with equal key: after the call the first lane of each run holds
@@ -1358,13 +1355,10 @@ __device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t 
     const bool nz = o.F.x != 0.f || o.F.y != 0.f || o.F.z != 0.f || eh != 0.f || wh != 0.f ||
                     (PATCHY && (o.ti.x != 0.f || o.ti.y != 0.f || o.ti.z != 0.f || o.tj.x != 0.f ||
                                 o.tj.y != 0.f || o.tj.z != 0.f));
-    // j side: one atomic per contributing pair.  Its returned old value (for the compensation) is used only
-    // after the i side's warp sums, so that their shuffles overlap the atomic's round trip to L2.
-    const float4 vj = make_float4(-o.F.x, -o.F.y, -o.F.z, eh), tvj = make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f);
-    float4 oldj = make_float4(0.f, 0.f, 0.f, 0.f), toldj = oldj;
+    // j side: the split reductions of every contributing pair
     if (nz) {
-      oldj = atom_add_v4(fhi + p.y, vj);
-      if (PATCHY) toldj = atom_add_v4(thi + p.y, tvj);
+      split_red(fhi + p.y, flo + p.y, make_float4(-o.F.x, -o.F.y, -o.F.z, eh), wh);
+      if (PATCHY) split_red(thi + p.y, tlo + p.y, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f), 0.f);
     }
     // i side: one atomic per run of equal i within the warp
     bool head;
@@ -1379,13 +1373,9 @@ __device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t 
       // a run contributes iff one of its lanes does
       const unsigned run_mask = (end == 32 ? 0xffffffffu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
       if (head && p.x >= 0 && (any_nz & run_mask)) {
-        comp_atomic(fhi + p.x, flo + p.x, make_float4(fx, fy, fz, es), ws);
-        if (PATCHY) comp_atomic(thi + p.x, tlo + p.x, make_float4(tx, ty, tz, 0.f), 0.f);
+        split_red(fhi + p.x, flo + p.x, make_float4(fx, fy, fz, es), ws);
+        if (PATCHY) split_red(thi + p.x, tlo + p.x, make_float4(tx, ty, tz, 0.f), 0.f);
       }
-    }
-    if (nz) {
-      comp_finish(flo + p.y, oldj, vj, wh);
-      if (PATCHY) comp_finish(tlo + p.y, toldj, tvj, 0.f);
     }
   }
 }
@@ -1555,9 +1545,9 @@ __device__ __forceinline__ void vertex_newton_mixed_body(const KArgs& a, int i) 
                       (PATCHY && (o.ti.x != 0.f || o.ti.y != 0.f || o.ti.z != 0.f || o.tj.x != 0.f ||
                                   o.tj.y != 0.f || o.tj.z != 0.f));
       if (!nz) continue;  // no interaction, no memory traffic
-      comp_atomic(fhi + j, flo + j, make_float4(-o.F.x, -o.F.y, -o.F.z, eh), wh);
+      split_red(fhi + j, flo + j, make_float4(-o.F.x, -o.F.y, -o.F.z, eh), wh);
       if (PATCHY)
-        comp_atomic(newton_copy(a, 2, c) + j, newton_copy(a, 3, c) + j, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f), 0.f);
+        split_red(newton_copy(a, 2, c) + j, newton_copy(a, 3, c) + j, make_float4(o.tj.x, o.tj.y, o.tj.z, 0.f), 0.f);
       comp_add(F, o.F);
       if (PATCHY) comp_add(T, o.ti);
       e += eh;
