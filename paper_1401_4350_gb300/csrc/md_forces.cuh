@@ -670,27 +670,21 @@ struct NoPrune {
 
 struct InnerPrune {
   static constexpr bool kPrune = true;
-  int i;               // the slot
-  int cnt;             // entries kept so far (the last cnt % 4 of them still in b0..b3)
-  int b0, b1, b2, b3;  // the group being filled
-  __device__ __forceinline__ void push(const KArgs& a, int j) {
-    const int k = cnt & 3;
-    b0 = k == 0 ? j : b0;
-    b1 = k == 1 ? j : b1;
-    b2 = k == 2 ? j : b2;
-    b3 = k == 3 ? j : b3;
-    if (++cnt & 3) return;
-    ((int4*)a.nbr_in)[(size_t)((cnt >> 2) - 1) * (size_t)a.n + i] = make_int4(b0, b1, b2, b3);
-  }
+  int i;    // the slot
+  int cnt;  // entries kept so far
+  // each kept entry goes straight to its place in the slot's inner-list row (entry k at group k / 4)
   __device__ __forceinline__ void take(const KArgs& a, const int4& cur, unsigned keep) {
-    if (keep & 1u) push(a, cur.x);
-    if (keep & 2u) push(a, cur.y);
-    if (keep & 4u) push(a, cur.z);
-    if (keep & 8u) push(a, cur.w);
+    int32_t* col = a.nbr_in + (size_t)i * 4;
+    const int v[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (keep & (1u << u)) {
+        col[(size_t)(cnt >> 2) * (size_t)a.n * 4 + (cnt & 3)] = v[u];
+        cnt++;
+      }
   }
   // the row is never longer than the Verlet-list row it comes from, so it fits the same capacity
   __device__ __forceinline__ void finish(const KArgs& a, const uint4& si) {
-    if (cnt & 3) ((int4*)a.nbr_in)[(size_t)(cnt >> 2) * (size_t)a.n + i] = make_int4(b0, b1, b2, b3);
     a.nbr_in_count[i] = cnt;
     a.fxp_prune[i] = si;
   }
@@ -989,7 +983,6 @@ __device__ __forceinline__ void vertex_iso_inner_eval(const KArgs& a, int i, boo
     InnerPrune S;
     S.i = i;
     S.cnt = 0;
-    S.b0 = S.b1 = S.b2 = S.b3 = 0;
     vertex_iso_cubic_rows<1, GlobalRows, InnerPrune, !ACC, ACC>(a, i, R, res, &S);
   } else {
     const GlobalRows R = global_rows(a, i, true);
