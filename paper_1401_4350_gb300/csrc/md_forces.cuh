@@ -1330,18 +1330,20 @@ __device__ __forceinline__ void edge_mixed_span(const KArgs& a, int r0, int64_t 
     o.e = o.w = 0.f;
     if (ok) {
       const uint4 si = __ldg(a.fxp + p.x), sj = __ldg(a.fxp + p.y);
-      const Vec3<float> d = sep_mixed(si, sj, a);
-      const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-      if (PATCHY) {
-        if (r2 < a.rc2_f) {
-          const IPatches<(PATCHY ? NP : 1)> Pi = load_ipatches<(PATCHY ? NP : 1)>(a, p.x);
-          const int3 ds = make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z));
-          o = patchy_pair_mixed<(PATCHY ? NP : 1), true>(a, ds, d, r2, Pi, p.x, p.y);
-        }
-      } else if (a.cubic) {
-        o = iso_pair_cubic(a, make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z)), p.x, p.y);
+      const int3 ds = make_int3((int)(sj.x - si.x), (int)(sj.y - si.y), (int)(sj.z - si.z));
+      if (!PATCHY && a.cubic) {
+        o = iso_pair_cubic(a, ds, p.x, p.y);  // from the integer separation alone
       } else {
-        o = iso_pair<float>(a, d, r2, p.x, p.y);
+        const Vec3<float> d = sep_mixed(si, sj, a);
+        const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        if (PATCHY) {
+          if (r2 < a.rc2_f) {
+            const IPatches<(PATCHY ? NP : 1)> Pi = load_ipatches<(PATCHY ? NP : 1)>(a, p.x);
+            o = patchy_pair_mixed<(PATCHY ? NP : 1), true>(a, ds, d, r2, Pi, p.x, p.y);
+          }
+        } else {
+          o = iso_pair<float>(a, d, r2, p.x, p.y);
+        }
       }
     }
     const float eh = 0.5f * o.e, wh = 0.5f * o.w;
