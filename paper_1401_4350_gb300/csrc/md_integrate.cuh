@@ -55,6 +55,14 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
          (long long)p0;
 }
 
+// x^2 + y^2 + z^2 and k (x^2 + y^2 + z^2) in FP32 with every rounding fixed (no contraction left to the
+// compiler), so that kernels compiled apart (the fused step and the separate integrate kernel) give the same
+// kinetic terms and displacement decisions bit for bit.
+__device__ __forceinline__ float sq3(float x, float y, float z) {
+  return __fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)));
+}
+__device__ __forceinline__ float kin3(float k, float x, float y, float z) { return __fmul_rn(k, sq3(x, y, z)); }
+
 // Quaternion product a (x) b, (w, x, y, z) stored as double4_32a (x=w, y=x, z=y, w=z).
 __device__ __forceinline__ double4_32a qmul(const double4_32a& a, const double4_32a& b) {
   return make_double4_32a(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
@@ -213,9 +221,10 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
       // closing half kick of the finished step (energies from v_n) and opening half kick of the next
       if (mixed) {
         if (energies) {
-          const float vx = f32_of(v.x) + f32_of(F.x) * a.half_dt_over_m_f, vy = f32_of(v.y) + f32_of(F.y) * a.half_dt_over_m_f,
-                      vz = f32_of(v.z) + f32_of(F.z) * a.half_dt_over_m_f;
-          ktf = a.half_mass_f * (vx * vx + vy * vy + vz * vz);
+          const float vx = __fmaf_rn(f32_of(F.x), a.half_dt_over_m_f, f32_of(v.x)),
+                      vy = __fmaf_rn(f32_of(F.y), a.half_dt_over_m_f, f32_of(v.y)),
+                      vz = __fmaf_rn(f32_of(F.z), a.half_dt_over_m_f, f32_of(v.z));
+          ktf = kin3(a.half_mass_f, vx, vy, vz);
         }
         if (refresh) {  // the refreshed velocity replaces v_n; then the opening half kick
           v.x = fma(F.x, a.half_dt_over_m, vn[0]);
@@ -251,8 +260,7 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
     }
     if (mode == 2 || mode == 3) {
       if (mixed) {
-        const float vx = f32_of(v.x), vy = f32_of(v.y), vz = f32_of(v.z);
-        ktf = a.half_mass_f * (vx * vx + vy * vy + vz * vz);
+        ktf = kin3(a.half_mass_f, f32_of(v.x), f32_of(v.y), f32_of(v.z));
       } else {
         kt = 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
       }
@@ -267,9 +275,9 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
         // by the whole step (or, after a refresh, the opening half kick from the drawn momentum)
         if (energies) {
           const float hf = 0.5f * a.dt_f;
-          const float lx = f32_of(L.x) + f32_of(T.x) * hf, ly = f32_of(L.y) + f32_of(T.y) * hf,
-                      lz = f32_of(L.z) + f32_of(T.z) * hf;
-          krf = 0.5f * a.inv_inertia_f * (lx * lx + ly * ly + lz * lz);
+          const float lx = __fmaf_rn(f32_of(T.x), hf, f32_of(L.x)), ly = __fmaf_rn(f32_of(T.y), hf, f32_of(L.y)),
+                      lz = __fmaf_rn(f32_of(T.z), hf, f32_of(L.z));
+          krf = kin3(__fmul_rn(0.5f, a.inv_inertia_f), lx, ly, lz);
         }
         if (refresh) {
           L.x = fma(T.x, hdt, ln[0]); L.y = fma(T.y, hdt, ln[1]); L.z = fma(T.z, hdt, ln[2]);
@@ -287,8 +295,7 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
       }
       if (mode == 2 || mode == 3) {
         if (mixed) {
-          const float lx = f32_of(L.x), ly = f32_of(L.y), lz = f32_of(L.z);
-          krf = 0.5f * a.inv_inertia_f * (lx * lx + ly * ly + lz * lz);
+          krf = kin3(__fmul_rn(0.5f, a.inv_inertia_f), f32_of(L.x), f32_of(L.y), f32_of(L.z));
         } else {
           kr = 0.5 * a.inv_inertia * (L.x * L.x + L.y * L.y + L.z * L.z);
         }
@@ -313,14 +320,14 @@ __device__ __forceinline__ void integrate_core(const KArgs& a, int mode, int i, 
       const float dx = (float)(int)(f.x - b.x) * a.fxp_unit[0];
       const float dy = (float)(int)(f.y - b.y) * a.fxp_unit[1];
       const float dz = (float)(int)(f.z - b.z) * a.fxp_unit[2];
-      disp2 = dx * dx + dy * dy + dz * dz;
+      disp2 = sq3(dx, dy, dz);
       if (!(disp2 == disp2)) disp2 = 3.0e38f;  // NaN: force a rebuild (and the error is recorded)
       if (a.inner) {
         const uint4 q = a.fxp_prune[i];
         const float px = (float)(int)(f.x - q.x) * a.fxp_unit[0];
         const float py = (float)(int)(f.y - q.y) * a.fxp_unit[1];
         const float pz = (float)(int)(f.z - q.z) * a.fxp_unit[2];
-        disp2p = px * px + py * py + pz * pz;
+        disp2p = sq3(px, py, pz);
         if (!(disp2p == disp2p)) disp2p = 3.0e38f;
       }
     }
