@@ -211,8 +211,9 @@ typedef struct md_ws_layout {
   size_t force;          /* double[n][4] (Fx, Fy, Fz, E_i): the force result of either precision */
   size_t virial;         /* double[n] W_i: half of each pair virial -r_ij.F_ij                  */
   size_t torque;         /* double[n][4] (tx, ty, tz, 0), patchy                                */
-  size_t acc;            /* mixed edge path: float[4][n][4] FP32 atomic accumulators and their
-                            compensation terms (force hi, force lo, torque hi, torque lo)          */
+  size_t acc;            /* mixed edge path: float[4][n][4] FP32 reduction accumulators: the
+                            2^-8-grid parts and the remainders (force hi, force lo, torque hi,
+                            torque lo)                                                              */
   size_t copies;         /* MD_VERTEX_NEWTON reaction-force copies (force_copies > 0), zero between
                             calls.  Mixed: float[2 or 4][m][n][4] as in acc, one block of n per copy;
                             FP64: double[m][n][4] forces + double[m][n] virials + double[m][n][4]
@@ -303,7 +304,11 @@ int md_forces_vertex(const md_params* p, md_state* s, void* ws, void* stream);
  * thread per pair of the half list computes F_ij and, only when it is not
  * zero, adds it to i and -F_ij to j (Newton's third law) with atomics; the
  * contributions to a run of pairs with the same i are first summed within the
- * warp.  Needs MD_LIST_HALF.  The accumulation order is not deterministic.
+ * warp.  Needs MD_LIST_HALF.  MD_MIXED: each force or torque component goes to
+ * two FP32 accumulators, its value rounded to a multiple of 2^-8 (whose sums are
+ * exact, so independent of order, below 2^16) and the exact remainder, by
+ * non-returning reductions; only the remainders' rounding depends on the order
+ * of the additions, which is not deterministic.
  */
 int md_forces_edge(const md_params* p, md_state* s, void* ws, void* stream);
 
@@ -421,7 +426,7 @@ int md_prepare(const md_params* p, md_state* s, void* ws, int32_t path, void* st
  * Copies the current forces into FP64 device arrays in slot order:
  * force_out [n][4] = (Fx, Fy, Fz, E_i), torque_out [n][4] = (tx, ty, tz, W_i)
  * (torque_out may be NULL).  Mixed-precision values are the FP64 sums of the
- * FP32 accumulator and its compensation term.
+ * FP32 accumulator and its compensation (or remainder) term.
  */
 int md_get_forces(const md_params* p, const void* ws, double* force_out, double* torque_out, void* stream);
 
