@@ -761,25 +761,27 @@ def cpu_baseline(system, max_seconds=25.0):
 
 
 def run_reference(args):
-    """The oracle timed as it stands, bounded: at most ~60 s of host time."""
+    """The oracle timed as it stands, on one host thread: W warm-up steps, then K steps, or as many as fit in
+    about 120 s of host time."""
     import oracle
     oracle.build()
     system = make_system(0)
     m = oracle.Model(oracle.LJ, tuple(system.box), system.rc)
     t0 = time.perf_counter()
-    pos, vel, _, _, _ = oracle.run_nve(system.pos, system.vel, m, system.dt, 1, use_cells=True)
-    per = (time.perf_counter() - t0) / 2.0
-    k = max(1, min(args.steps, int(60.0 / max(per, 1e-3)) - 1))
+    pos, vel, _, _, _ = oracle.run_nve(system.pos, system.vel, m, system.dt, args.warmup, use_cells=True)
+    per = (time.perf_counter() - t0) / (args.warmup + 1.0)  # the warm-up steps and the initial force evaluation
+    k = max(1, min(args.steps, int(120.0 / max(per, 1e-3))))
     t1 = time.perf_counter()
     oracle.run_nve(pos, vel, m, system.dt, k, use_cells=True)
     el = time.perf_counter() - t1
     value = k / el
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1, "steps": k,
-            "requested_steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * el / k, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "requested_steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / k,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": system.n, "implementation": "FP64 cell-list C oracle"},
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{k} steps of the {system.n}-particle workload, one host thread"},
+                             "sample": f"{k} steps of the {system.n}-particle workload after {args.warmup} warm-up "
+                                       f"steps, one host thread"},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
